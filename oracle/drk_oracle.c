@@ -1,0 +1,780 @@
+/*
+ * drk_oracle.c -- plain FP64 CPU oracle for Deformable Radial Kernel (DRK)
+ * splatting.  TEST INFRASTRUCTURE ONLY: it exists to check the CUDA path and
+ * is called from the test-suite, the smoke check and the benchmark's CPU
+ * baseline leg, never from the product path.  It shares no code, header or
+ * constant table with the CUDA library.
+ *
+ * What it computes (per pixel, brute force over every primitive, no culling,
+ * no tiles, no cache):
+ *   1. ray of the pixel centre, ray-plane intersection and local (u, v)
+ *      coordinates                                           -- Eq. 4, Eq. 5
+ *   2. polar angle, sector k, relative angle, radial L2 term -- Eq. 6
+ *   3. L1 norm through the inverse endpoint matrix           -- Eq. 7
+ *   4. L1/L2 blend and exponential                           -- Eq. 8
+ *   5. sharpening Psi                                        -- Eq. 9
+ *   6. view-dependent low-pass filter (max)                  -- Eq. 10
+ *   7. contributors sorted by ray depth r_t                  -- Eq. 13
+ *   8. front-to-back alpha compositing                       -- Eq. 1
+ * and the exact reverse-mode derivative of that image, evaluated
+ * back-to-front over each pixel's sorted contributor list.
+ *
+ * Readings where the paper is silent or garbled (each one is stated where it
+ * is used below):
+ *   R1  the polar angle is atan2(v, u) on the full circle (Sec. 4.1 writes
+ *       arccos, which only covers half of it); K angles theta_0..theta_{K-1}
+ *       ascending with span < 2 pi, the last sector wraps to theta_0 + 2 pi
+ *       with scale s_0; a point on theta_{k+1} belongs to sector k.
+ *   R2  R_x, R_y, R_z are the columns of R(q) (Eq. 5 speaks of rows of R,
+ *       i.e. the rows of R^T); q = (w, x, y, z) is normalised first.
+ *   R3  camera: pinhole, x right / y down / z forward, pixel centres at +0.5;
+ *       the ray direction has unit camera-space z, so r_t of Eq. 13 is the
+ *       view-space depth of the intersection.  Skip a pair when the
+ *       normalised ray is within 1e-7 of parallel to the plane or r_t <= near.
+ *   R4  low-pass filter: r_d in Eq. 10 is normalised; Delta p is measured
+ *       from the pinhole projection of mu (only when mu lies beyond the near
+ *       plane); s_l is an option (0 = filter off); the max is taken after Psi.
+ *   R5  alpha_tilde = min(max(alpha, filter), alpha_max); a pair contributes
+ *       iff alpha_tilde >= alpha_min; compositing stops before the first
+ *       contributor whose T (1 - alpha_tilde) would fall below T_min.
+ *   R6  contributors are ordered by (r_t, primitive index).
+ *   R7  colour: plain RGB, or real spherical harmonics of degree <= 3 in the
+ *       view direction camera centre -> mu, plus 0.5, clamped below at 0.
+ *   R8  background colour bg is added with the final transmittance.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORD_PI 3.14159265358979323846
+#define ORD_TWO_PI (2.0 * ORD_PI)
+#define ORD_MAXK 64
+
+typedef struct {
+    int64_t n;
+    int K;
+    int sh_degree;          /* -1: plain RGB */
+    const double *mu;       /* n x 3 */
+    const double *quat;     /* n x 4 (w, x, y, z) */
+    const double *scale;    /* n x K */
+    const double *theta;    /* n x K ascending */
+    const double *eta;      /* n */
+    const double *tau;      /* n */
+    const double *opacity;  /* n */
+    const double *color;    /* n x 3 or n x (deg+1)^2 x 3 */
+} ord_params;
+
+typedef struct {
+    double *mu, *quat, *scale, *theta, *eta, *tau, *opacity, *color;
+} ord_grads;
+
+typedef struct {
+    int width, height;
+    double fx, fy, cx, cy;
+    double w2c[12];         /* row-major 3 x 4 [R | t] */
+} ord_camera;
+
+typedef struct {
+    double alpha_min, T_min, alpha_max, lowpass_sl, near_plane;
+    double bg[3];
+} ord_options;
+
+/* parity flags written per pixel by ord_render */
+#define ORD_FLAG_ALPHA_MIN 1   /* some alpha_tilde within 1e-4 (rel) of alpha_min (informational) */
+#define ORD_FLAG_T_MIN     2   /* a stop decision within FP32 margin and with visible effect */
+#define ORD_FLAG_DEPTH_TIE 4   /* two contributors with near-equal depth and visible order effect */
+
+/* ------------------------------------------------------------------------ */
+/* Sharpening, Eq. 9, and its inverse (used by tests and by the culling
+ * radius of Eq. 11).                                                        */
+
+double ord_psi(double g, double tau)
+{
+    if (g < (1.0 + tau) / 4.0) return (1.0 - tau) / (1.0 + tau) * g;
+    if (g < (3.0 - tau) / 4.0) return (1.0 + tau) / (1.0 - tau) * g - tau / (1.0 - tau);
+    return (1.0 - tau) / (1.0 + tau) * g + 2.0 * tau / (1.0 + tau);
+}
+
+/* derivative of Psi with respect to g and to tau on the piece containing g */
+static void psi_grad(double g, double tau, double *dg, double *dtau)
+{
+    double p = 1.0 + tau, m = 1.0 - tau;
+    if (g < p / 4.0) {
+        *dg = m / p;
+        *dtau = -2.0 * g / (p * p);
+    } else if (g < (3.0 - tau) / 4.0) {
+        *dg = p / m;
+        *dtau = 2.0 * g / (m * m) - 1.0 / (m * m);
+    } else {
+        *dg = m / p;
+        *dtau = -2.0 * g / (p * p) + 2.0 / (p * p);
+    }
+}
+
+/* inverse of Psi on [0, 1] (Psi is continuous and strictly increasing) */
+double ord_psi_inv(double y, double tau)
+{
+    if (y < (1.0 - tau) / 4.0) return y * (1.0 + tau) / (1.0 - tau);
+    if (y < (3.0 + tau) / 4.0) return (y * (1.0 - tau) + tau) / (1.0 + tau);
+    return ((1.0 + tau) * y - 2.0 * tau) / (1.0 - tau);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Rotation from a quaternion (w, x, y, z), normalised first.  R is
+ * row-major; its columns are R_x, R_y, R_z (reading R2).                   */
+
+void ord_rotation(const double *q, double *R)
+{
+    double nrm = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    double w = q[0] / nrm, x = q[1] / nrm, y = q[2] / nrm, z = q[3] / nrm;
+    R[0] = 1.0 - 2.0 * (y * y + z * z);
+    R[1] = 2.0 * (x * y - w * z);
+    R[2] = 2.0 * (x * z + w * y);
+    R[3] = 2.0 * (x * y + w * z);
+    R[4] = 1.0 - 2.0 * (x * x + z * z);
+    R[5] = 2.0 * (y * z - w * x);
+    R[6] = 2.0 * (x * z - w * y);
+    R[7] = 2.0 * (y * z + w * x);
+    R[8] = 1.0 - 2.0 * (x * x + y * y);
+}
+
+/* gradient of a loss with respect to the (unnormalised) quaternion, given
+ * its gradient with respect to the row-major R */
+static void rotation_backward(const double *q, const double *dR, double *dq)
+{
+    double nrm = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    double w = q[0] / nrm, x = q[1] / nrm, y = q[2] / nrm, z = q[3] / nrm;
+    double gw = 0, gx = 0, gy = 0, gz = 0;
+    /* R00 */ gy += -4 * y * dR[0]; gz += -4 * z * dR[0];
+    /* R01 */ gw += -2 * z * dR[1]; gx += 2 * y * dR[1]; gy += 2 * x * dR[1]; gz += -2 * w * dR[1];
+    /* R02 */ gw += 2 * y * dR[2]; gx += 2 * z * dR[2]; gy += 2 * w * dR[2]; gz += 2 * x * dR[2];
+    /* R10 */ gw += 2 * z * dR[3]; gx += 2 * y * dR[3]; gy += 2 * x * dR[3]; gz += 2 * w * dR[3];
+    /* R11 */ gx += -4 * x * dR[4]; gz += -4 * z * dR[4];
+    /* R12 */ gw += -2 * x * dR[5]; gx += -2 * w * dR[5]; gy += 2 * z * dR[5]; gz += 2 * y * dR[5];
+    /* R20 */ gw += -2 * y * dR[6]; gx += 2 * z * dR[6]; gy += -2 * w * dR[6]; gz += 2 * x * dR[6];
+    /* R21 */ gw += 2 * x * dR[7]; gx += 2 * w * dR[7]; gy += 2 * z * dR[7]; gz += 2 * y * dR[7];
+    /* R22 */ gx += -4 * x * dR[8]; gy += -4 * y * dR[8];
+    double dotp = w * gw + x * gx + y * gy + z * gz;
+    dq[0] = (gw - w * dotp) / nrm;
+    dq[1] = (gx - x * dotp) / nrm;
+    dq[2] = (gy - y * dotp) / nrm;
+    dq[3] = (gz - z * dotp) / nrm;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Real spherical harmonics up to degree 3 (reading R7), written as
+ * polynomials in the unit direction (x, y, z).  Index l*l + l + m,
+ * m = -l..l.  Convention: y_lm = sqrt(2) Im Y_l^|m| (m < 0), Y_l^0 (m = 0),
+ * sqrt(2) Re Y_l^m (m > 0), with Y_l^m carrying the Condon-Shortley phase.
+ * Normalisation constants are written in closed form.                      */
+
+void ord_sh_basis(int degree, const double *d, double *Y)
+{
+    double x = d[0], y = d[1], z = d[2];
+    Y[0] = 0.5 * sqrt(1.0 / ORD_PI);
+    if (degree < 1) return;
+    double c1 = sqrt(3.0 / (4.0 * ORD_PI));
+    Y[1] = -c1 * y;
+    Y[2] = c1 * z;
+    Y[3] = -c1 * x;
+    if (degree < 2) return;
+    double a = 0.5 * sqrt(15.0 / ORD_PI), b = 0.25 * sqrt(5.0 / ORD_PI), c = 0.25 * sqrt(15.0 / ORD_PI);
+    Y[4] = a * x * y;
+    Y[5] = -a * y * z;
+    Y[6] = b * (2.0 * z * z - x * x - y * y);
+    Y[7] = -a * x * z;
+    Y[8] = c * (x * x - y * y);
+    if (degree < 3) return;
+    double e = 0.25 * sqrt(35.0 / (2.0 * ORD_PI)), f = 0.5 * sqrt(105.0 / ORD_PI);
+    double h = 0.25 * sqrt(21.0 / (2.0 * ORD_PI)), k = 0.25 * sqrt(7.0 / ORD_PI), l = 0.25 * sqrt(105.0 / ORD_PI);
+    Y[9] = -e * y * (3.0 * x * x - y * y);
+    Y[10] = f * x * y * z;
+    Y[11] = -h * y * (4.0 * z * z - x * x - y * y);
+    Y[12] = k * z * (2.0 * z * z - 3.0 * x * x - 3.0 * y * y);
+    Y[13] = -h * x * (4.0 * z * z - x * x - y * y);
+    Y[14] = l * z * (x * x - y * y);
+    Y[15] = -e * x * (x * x - 3.0 * y * y);
+}
+
+/* gradient of each basis polynomial with respect to (x, y, z): G[3*j + c] */
+static void sh_basis_grad(int degree, const double *d, double *G)
+{
+    double x = d[0], y = d[1], z = d[2];
+    memset(G, 0, sizeof(double) * 48);
+    if (degree < 1) return;
+    double c1 = sqrt(3.0 / (4.0 * ORD_PI));
+    G[3 * 1 + 1] = -c1;
+    G[3 * 2 + 2] = c1;
+    G[3 * 3 + 0] = -c1;
+    if (degree < 2) return;
+    double a = 0.5 * sqrt(15.0 / ORD_PI), b = 0.25 * sqrt(5.0 / ORD_PI), c = 0.25 * sqrt(15.0 / ORD_PI);
+    G[3 * 4 + 0] = a * y;  G[3 * 4 + 1] = a * x;
+    G[3 * 5 + 1] = -a * z; G[3 * 5 + 2] = -a * y;
+    G[3 * 6 + 0] = -2.0 * b * x; G[3 * 6 + 1] = -2.0 * b * y; G[3 * 6 + 2] = 4.0 * b * z;
+    G[3 * 7 + 0] = -a * z; G[3 * 7 + 2] = -a * x;
+    G[3 * 8 + 0] = 2.0 * c * x; G[3 * 8 + 1] = -2.0 * c * y;
+    if (degree < 3) return;
+    double e = 0.25 * sqrt(35.0 / (2.0 * ORD_PI)), f = 0.5 * sqrt(105.0 / ORD_PI);
+    double h = 0.25 * sqrt(21.0 / (2.0 * ORD_PI)), k = 0.25 * sqrt(7.0 / ORD_PI), l = 0.25 * sqrt(105.0 / ORD_PI);
+    /* Y9 = -e (3 x^2 y - y^3) */
+    G[3 * 9 + 0] = -e * 6.0 * x * y; G[3 * 9 + 1] = -e * (3.0 * x * x - 3.0 * y * y);
+    /* Y10 = f x y z */
+    G[3 * 10 + 0] = f * y * z; G[3 * 10 + 1] = f * x * z; G[3 * 10 + 2] = f * x * y;
+    /* Y11 = -h (4 y z^2 - x^2 y - y^3) */
+    G[3 * 11 + 0] = -h * (-2.0 * x * y);
+    G[3 * 11 + 1] = -h * (4.0 * z * z - x * x - 3.0 * y * y);
+    G[3 * 11 + 2] = -h * (8.0 * y * z);
+    /* Y12 = k (2 z^3 - 3 x^2 z - 3 y^2 z) */
+    G[3 * 12 + 0] = k * (-6.0 * x * z); G[3 * 12 + 1] = k * (-6.0 * y * z);
+    G[3 * 12 + 2] = k * (6.0 * z * z - 3.0 * x * x - 3.0 * y * y);
+    /* Y13 = -h (4 x z^2 - x^3 - x y^2) */
+    G[3 * 13 + 0] = -h * (4.0 * z * z - 3.0 * x * x - y * y);
+    G[3 * 13 + 1] = -h * (-2.0 * x * y);
+    G[3 * 13 + 2] = -h * (8.0 * x * z);
+    /* Y14 = l (x^2 z - y^2 z) */
+    G[3 * 14 + 0] = l * 2.0 * x * z; G[3 * 14 + 1] = -l * 2.0 * y * z; G[3 * 14 + 2] = l * (x * x - y * y);
+    /* Y15 = -e (x^3 - 3 x y^2) */
+    G[3 * 15 + 0] = -e * (3.0 * x * x - 3.0 * y * y); G[3 * 15 + 1] = -e * (-6.0 * x * y);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Camera helpers (reading R3). */
+
+static void cam_center(const ord_camera *c, double *o)
+{
+    const double *M = c->w2c;
+    /* o = -R^T t */
+    for (int i = 0; i < 3; i++)
+        o[i] = -(M[0 * 4 + i] * M[3] + M[1 * 4 + i] * M[7] + M[2 * 4 + i] * M[11]);
+}
+
+/* world-space ray direction of pixel (px, py); camera-space z component 1 */
+static void cam_ray(const ord_camera *c, int px, int py, double *d)
+{
+    const double *M = c->w2c;
+    double dc[3] = {(px + 0.5 - c->cx) / c->fx, (py + 0.5 - c->cy) / c->fy, 1.0};
+    for (int i = 0; i < 3; i++)
+        d[i] = M[0 * 4 + i] * dc[0] + M[1 * 4 + i] * dc[1] + M[2 * 4 + i] * dc[2];
+}
+
+static double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+/* ------------------------------------------------------------------------ */
+/* Kernel function in local (u, v) coordinates: Eq. 6 - Eq. 9.  Everything
+ * the derivative needs is kept in this record.                             */
+
+typedef struct {
+    int k, k1;                  /* sector (k, k+1 mod K) */
+    double r2sq, phi, th_k, th_k1, gap, dtheta, c, Q;
+    double a, b, r1, E, g, psi, alpha;
+    double Minv[4];             /* inverse of [e_k e_{k+1}], row-major */
+} kernel_eval;
+
+static void kernel_uv(int K, const double *s, const double *th, double eta, double tau, double o,
+                      double u, double v, kernel_eval *ke)
+{
+    ke->r2sq = u * u + v * v;
+    /* reading R1: full-circle polar angle reduced into [theta_0, theta_0 + 2 pi) */
+    double phi = atan2(v, u);
+    double rel = fmod(phi - th[0], ORD_TWO_PI);
+    if (rel < 0.0) rel += ORD_TWO_PI;
+    phi = th[0] + rel;
+    int k = 0;
+    for (int j = 1; j < K; j++)
+        if (th[j] < phi) k = j;
+    int k1 = (k + 1) % K;
+    double th_k = th[k];
+    double th_k1 = (k + 1 < K) ? th[k + 1] : th[0] + ORD_TWO_PI;
+    ke->k = k; ke->k1 = k1; ke->phi = phi; ke->th_k = th_k; ke->th_k1 = th_k1;
+    ke->gap = th_k1 - th_k;
+    /* Eq. 6: relative angle and cosine-weighted inverse squared radius */
+    ke->dtheta = (phi - th_k) * ORD_PI / ke->gap;
+    ke->c = cos(ke->dtheta);
+    ke->Q = (1.0 + ke->c) / (2.0 * s[k] * s[k]) + (1.0 - ke->c) / (2.0 * s[k1] * s[k1]);
+    /* Eq. 7: L1 norm of the coordinates in the basis of the two endpoints */
+    double e0x = s[k] * cos(th_k), e0y = s[k] * sin(th_k);
+    double e1x = s[k1] * cos(th_k1), e1y = s[k1] * sin(th_k1);
+    double det = e0x * e1y - e1x * e0y;
+    ke->Minv[0] = e1y / det;  ke->Minv[1] = -e1x / det;
+    ke->Minv[2] = -e0y / det; ke->Minv[3] = e0x / det;
+    ke->a = ke->Minv[0] * u + ke->Minv[1] * v;
+    ke->b = ke->Minv[2] * u + ke->Minv[3] * v;
+    ke->r1 = fabs(ke->a) + fabs(ke->b);
+    /* Eq. 8: blend and exponential */
+    ke->E = eta * ke->r1 * ke->r1 + (1.0 - eta) * ke->r2sq * ke->Q;
+    ke->g = exp(-0.5 * ke->E);
+    /* Eq. 9 */
+    ke->psi = ord_psi(ke->g, tau);
+    ke->alpha = o * ke->psi;
+}
+
+double ord_kernel_uv(int K, const double *s, const double *th, double eta, double tau, double o,
+                     double u, double v)
+{
+    kernel_eval ke;
+    kernel_uv(K, s, th, eta, tau, o, u, v, &ke);
+    return ke.alpha;
+}
+
+double ord_l1_norm(int K, const double *s, const double *th, double u, double v)
+{
+    kernel_eval ke;
+    kernel_uv(K, s, th, 0.0, 0.0, 1.0, u, v, &ke);
+    return ke.r1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One (pixel, primitive) pair: geometry (Eq. 4, 5), kernel (Eq. 6-9),
+ * filter (Eq. 10), clamp and threshold (reading R5).                       */
+
+typedef struct {
+    int valid;                  /* ray meets the plane in front of the near plane */
+    double t, u, v;
+    double R[9], m[3], d[3], dn, p[3];
+    kernel_eval ke;
+    int filt_on;                /* filter evaluated */
+    double filt, dpx, dpy, cosv, dp2, muc[3];
+    int use_filter;             /* alpha_tilde taken from the filter */
+    int clamped;                /* alpha_tilde clamped to alpha_max */
+    double alpha_tilde;
+} pair_eval;
+
+static void eval_pair(const ord_params *P, int64_t i, const ord_camera *cam, const ord_options *opt,
+                      const double *ocam, int px, int py, pair_eval *pe)
+{
+    memset(pe, 0, sizeof(*pe));
+    int K = P->K;
+    ord_rotation(P->quat + 4 * i, pe->R);
+    const double *mu = P->mu + 3 * i;
+    double Rx[3] = {pe->R[0], pe->R[3], pe->R[6]};
+    double Ry[3] = {pe->R[1], pe->R[4], pe->R[7]};
+    double Rz[3] = {pe->R[2], pe->R[5], pe->R[8]};
+    cam_ray(cam, px, py, pe->d);
+    for (int c = 0; c < 3; c++) pe->m[c] = mu[c] - ocam[c];
+    pe->dn = dot3(pe->d, Rz);
+    double dnorm = sqrt(dot3(pe->d, pe->d));
+    if (fabs(pe->dn) < 1e-7 * dnorm) return;                 /* reading R3 */
+    /* Eq. 4 (ray depth r_t of Eq. 13) */
+    pe->t = dot3(pe->m, Rz) / pe->dn;
+    if (!(pe->t > opt->near_plane)) return;
+    pe->valid = 1;
+    /* Eq. 5: p = i - mu with i = o + t d */
+    for (int c = 0; c < 3; c++) pe->p[c] = pe->t * pe->d[c] - pe->m[c];
+    pe->u = dot3(Rx, pe->p);
+    pe->v = dot3(Ry, pe->p);
+    double o = P->opacity[i];
+    kernel_uv(K, P->scale + (int64_t)K * i, P->theta + (int64_t)K * i, P->eta[i], P->tau[i], o,
+              pe->u, pe->v, &pe->ke);
+    double at = pe->ke.alpha;
+    /* Eq. 10 (reading R4) */
+    const double *M = cam->w2c;
+    for (int r = 0; r < 3; r++)
+        pe->muc[r] = M[r * 4 + 0] * mu[0] + M[r * 4 + 1] * mu[1] + M[r * 4 + 2] * mu[2] + M[r * 4 + 3];
+    if (opt->lowpass_sl > 0.0 && pe->muc[2] > opt->near_plane) {
+        pe->filt_on = 1;
+        double prx = cam->fx * pe->muc[0] / pe->muc[2] + cam->cx;
+        double pry = cam->fy * pe->muc[1] / pe->muc[2] + cam->cy;
+        pe->dpx = px + 0.5 - prx;
+        pe->dpy = py + 0.5 - pry;
+        pe->dp2 = pe->dpx * pe->dpx + pe->dpy * pe->dpy;
+        pe->cosv = fabs(pe->dn) / dnorm;
+        double sl = opt->lowpass_sl;
+        pe->filt = o * exp(-pe->dp2 / (2.0 * pe->cosv * pe->cosv * sl * sl));
+        if (pe->filt > at) { at = pe->filt; pe->use_filter = 1; }
+    }
+    if (at > opt->alpha_max) { at = opt->alpha_max; pe->clamped = 1; }
+    pe->alpha_tilde = at;
+}
+
+int ord_pair(const ord_params *P, int64_t i, const ord_camera *cam, const ord_options *opt,
+             int px, int py, double *alpha_tilde, double *t)
+{
+    double ocam[3];
+    cam_center(cam, ocam);
+    pair_eval pe;
+    eval_pair(P, i, cam, opt, ocam, px, py, &pe);
+    *alpha_tilde = pe.valid ? pe.alpha_tilde : 0.0;
+    *t = pe.t;
+    return pe.valid;
+}
+
+/* colour of primitive i seen from the camera centre (reading R7) */
+static int ncoef_of(int deg) { return deg < 0 ? 1 : (deg + 1) * (deg + 1); }
+
+static void prim_color(const ord_params *P, int64_t i, const double *ocam, double *rgb, int *clamped)
+{
+    if (P->sh_degree < 0) {
+        for (int c = 0; c < 3; c++) { rgb[c] = P->color[3 * i + c]; clamped[c] = 0; }
+        return;
+    }
+    int nc = ncoef_of(P->sh_degree);
+    const double *sh = P->color + (int64_t)3 * nc * i;
+    double dir[3];
+    for (int c = 0; c < 3; c++) dir[c] = P->mu[3 * i + c] - ocam[c];
+    double nr = sqrt(dot3(dir, dir));
+    for (int c = 0; c < 3; c++) dir[c] /= nr;
+    double Y[16];
+    ord_sh_basis(P->sh_degree, dir, Y);
+    for (int c = 0; c < 3; c++) {
+        double acc = 0.5;
+        for (int j = 0; j < nc; j++) acc += sh[3 * j + c] * Y[j];
+        clamped[c] = acc < 0.0;
+        rgb[c] = acc < 0.0 ? 0.0 : acc;
+    }
+}
+
+void ord_color(const ord_params *P, int64_t i, const ord_camera *cam, double *rgb)
+{
+    double ocam[3];
+    int cl[3];
+    cam_center(cam, ocam);
+    prim_color(P, i, ocam, rgb, cl);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Per-pixel contributor list, sorted by (r_t, index) -- Eq. 13, reading R6 */
+
+typedef struct { double t; int64_t idx; double alpha; } contrib;
+
+static int contrib_cmp(const void *pa, const void *pb)
+{
+    const contrib *a = (const contrib *)pa, *b = (const contrib *)pb;
+    if (a->t < b->t) return -1;
+    if (a->t > b->t) return 1;
+    return (a->idx > b->idx) - (a->idx < b->idx);
+}
+
+static int64_t gather_contributors(const ord_params *P, const ord_camera *cam, const ord_options *opt,
+                                   const double *ocam, int px, int py, contrib *buf, int *near_amin)
+{
+    int64_t cnt = 0;
+    *near_amin = 0;
+    for (int64_t i = 0; i < P->n; i++) {
+        pair_eval pe;
+        eval_pair(P, i, cam, opt, ocam, px, py, &pe);
+        if (!pe.valid) continue;
+        if (fabs(pe.alpha_tilde / opt->alpha_min - 1.0) < 1e-4) *near_amin = 1;
+        if (pe.alpha_tilde >= opt->alpha_min) {
+            buf[cnt].t = pe.t;
+            buf[cnt].idx = i;
+            buf[cnt].alpha = pe.alpha_tilde;
+            cnt++;
+        }
+    }
+    qsort(buf, (size_t)cnt, sizeof(contrib), contrib_cmp);
+    return cnt;
+}
+
+/* number of contributors composited before the T_min stop (reading R5) */
+static int64_t composite_count(const contrib *buf, int64_t cnt, double T_min)
+{
+    double T = 1.0;
+    for (int64_t j = 0; j < cnt; j++) {
+        double Tn = T * (1.0 - buf[j].alpha);
+        if (Tn < T_min) return j;
+        T = Tn;
+    }
+    return cnt;
+}
+
+static double max_abs_diff3(const double *a, const double *b)
+{
+    double m = 0.0;
+    for (int c = 0; c < 3; c++) {
+        double d = fabs(a[c] - b[c]);
+        if (d > m) m = d;
+    }
+    return m;
+}
+
+/* Render the listed pixels.  pix: npix x 2 (x, y).  Outputs per pixel:
+ * rgb (npix x 3, includes T_final * bg), T_final, number of composited
+ * contributors, parity flags.  Returns 0, or -1 on allocation failure.    */
+int ord_render(const ord_params *P, const ord_camera *cam, const ord_options *opt, int64_t npix,
+               const int32_t *pix, double *rgb, double *T_final, int32_t *n_contrib, int32_t *flags)
+{
+    double ocam[3];
+    cam_center(cam, ocam);
+    int fail = 0;
+#pragma omp parallel
+    {
+        contrib *buf = (contrib *)malloc(sizeof(contrib) * (size_t)(P->n > 0 ? P->n : 1));
+        if (!buf) {
+#pragma omp atomic write
+            fail = 1;
+        }
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t q = 0; q < npix; q++) {
+            if (!buf) continue;
+            int px = pix[2 * q], py = pix[2 * q + 1];
+            int near_amin;
+            int64_t cnt = gather_contributors(P, cam, opt, ocam, px, py, buf, &near_amin);
+            int64_t nc = composite_count(buf, cnt, opt->T_min);
+            double C[3] = {0, 0, 0}, T = 1.0;
+            int flag = near_amin ? ORD_FLAG_ALPHA_MIN : 0;
+            for (int64_t j = 0; j <= nc && j < cnt; j++) {
+                double cj[3];
+                int cl[3];
+                prim_color(P, buf[j].idx, ocam, cj, cl);
+                double a = buf[j].alpha;
+                /* stop decision within FP32 margin with an effect above 5e-5 */
+                double rel = fabs(T * (1.0 - a) / opt->T_min - 1.0);
+                if (opt->T_min > 0.0 && rel < 2e-4 * (1.0 + a / (1.0 - a)) &&
+                    T * a * max_abs_diff3(cj, opt->bg) > 5e-5)
+                    flag |= ORD_FLAG_T_MIN;
+                if (j == nc) break;
+                /* near-equal depths whose swap is visible */
+                for (int64_t l = j + 1; l < cnt && buf[l].t - buf[j].t <= 1e-5 * buf[l].t; l++) {
+                    double cl_rgb[3];
+                    int cl2[3];
+                    prim_color(P, buf[l].idx, ocam, cl_rgb, cl2);
+                    if (T * a * buf[l].alpha * max_abs_diff3(cj, cl_rgb) > 5e-5) flag |= ORD_FLAG_DEPTH_TIE;
+                }
+                for (int c = 0; c < 3; c++) C[c] += T * a * cj[c];
+                T *= 1.0 - a;
+            }
+            for (int c = 0; c < 3; c++) rgb[3 * q + c] = C[c] + T * opt->bg[c];
+            if (T_final) T_final[q] = T;
+            if (n_contrib) n_contrib[q] = (int32_t)nc;
+            if (flags) flags[q] = flag;
+        }
+        free(buf);
+    }
+    return fail ? -1 : 0;
+}
+
+/* Sorted contributor list of one pixel (for inspection by tests).
+ * Writes up to cap entries; returns the total count; *n_composited gets the
+ * number composited before the stop.                                        */
+int64_t ord_contributors(const ord_params *P, const ord_camera *cam, const ord_options *opt, int px, int py,
+                         int64_t cap, int64_t *idx, double *t, double *alpha, int64_t *n_composited)
+{
+    double ocam[3];
+    cam_center(cam, ocam);
+    contrib *buf = (contrib *)malloc(sizeof(contrib) * (size_t)(P->n > 0 ? P->n : 1));
+    if (!buf) return -1;
+    int near_amin;
+    int64_t cnt = gather_contributors(P, cam, opt, ocam, px, py, buf, &near_amin);
+    for (int64_t j = 0; j < cnt && j < cap; j++) {
+        idx[j] = buf[j].idx;
+        t[j] = buf[j].t;
+        alpha[j] = buf[j].alpha;
+    }
+    *n_composited = composite_count(buf, cnt, opt->T_min);
+    free(buf);
+    return cnt;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Reverse mode.  For one pair, given dL/d(alpha_tilde), accumulate the
+ * gradient with respect to every DRK parameter of primitive i.  The chain
+ * follows the forward steps above in reverse order.                        */
+
+static void acc(double *dst, double v)
+{
+#pragma omp atomic update
+    *dst += v;
+}
+
+static void pair_backward(const ord_params *P, int64_t i, const ord_camera *cam, const ord_options *opt,
+                          const double *ocam, int px, int py, double g_at, ord_grads *G)
+{
+    pair_eval pe;
+    eval_pair(P, i, cam, opt, ocam, px, py, &pe);
+    if (!pe.valid || pe.clamped) return;
+    int K = P->K;
+    const double *s = P->scale + (int64_t)K * i;
+    double o = P->opacity[i];
+    double tau = P->tau[i], eta = P->eta[i];
+    double dmu[3] = {0, 0, 0}, dR[9] = {0};
+    const double *M = cam->w2c;
+
+    if (pe.use_filter) {
+        /* f = o exp(-dp2 / (2 cosv^2 sl^2)) */
+        double sl = opt->lowpass_sl, f = pe.filt;
+        acc(&G->opacity[i], g_at * f / o);
+        double dQf = -g_at * f;                                  /* dL/dQf */
+        double d_dp2 = dQf / (2.0 * pe.cosv * pe.cosv * sl * sl);
+        double d_cos = dQf * (-pe.dp2 / (pe.cosv * pe.cosv * pe.cosv * sl * sl));
+        /* projection of mu */
+        double z = pe.muc[2];
+        double dprx = -2.0 * pe.dpx * d_dp2, dpry = -2.0 * pe.dpy * d_dp2;
+        double dmuc[3] = {dprx * cam->fx / z, dpry * cam->fy / z,
+                          -dprx * cam->fx * pe.muc[0] / (z * z) - dpry * cam->fy * pe.muc[1] / (z * z)};
+        for (int c = 0; c < 3; c++)
+            dmu[c] += M[0 * 4 + c] * dmuc[0] + M[1 * 4 + c] * dmuc[1] + M[2 * 4 + c] * dmuc[2];
+        /* cosv = |d . Rz| / |d| */
+        double dnorm = sqrt(dot3(pe.d, pe.d));
+        double sg = pe.dn >= 0.0 ? 1.0 : -1.0;
+        for (int c = 0; c < 3; c++) dR[3 * c + 2] += d_cos * sg * pe.d[c] / dnorm;
+    } else {
+        kernel_eval *ke = &pe.ke;
+        double dpsi_dg, dpsi_dtau;
+        psi_grad(ke->g, tau, &dpsi_dg, &dpsi_dtau);
+        acc(&G->opacity[i], g_at * ke->psi);
+        acc(&G->tau[i], g_at * o * dpsi_dtau);
+        double dE = -0.5 * ke->g * g_at * o * dpsi_dg;
+        acc(&G->eta[i], dE * (ke->r1 * ke->r1 - ke->r2sq * ke->Q));
+        double d_r1 = dE * 2.0 * eta * ke->r1;
+        double d_r2sq = dE * (1.0 - eta) * ke->Q;
+        double d_Q = dE * (1.0 - eta) * ke->r2sq;
+        int k = ke->k, k1 = ke->k1;
+        double *ds = G->scale + (int64_t)K * i, *dth = G->theta + (int64_t)K * i;
+        /* Q = (1 + c)/(2 s_k^2) + (1 - c)/(2 s_k1^2) */
+        double d_c = d_Q * (1.0 / (2.0 * s[k] * s[k]) - 1.0 / (2.0 * s[k1] * s[k1]));
+        acc(&ds[k], d_Q * (1.0 + ke->c) * (-1.0 / (s[k] * s[k] * s[k])));
+        acc(&ds[k1], d_Q * (1.0 - ke->c) * (-1.0 / (s[k1] * s[k1] * s[k1])));
+        /* c = cos(dtheta), dtheta = (phi - th_k) pi / gap */
+        double d_dth = -sin(ke->dtheta) * d_c;
+        double gap = ke->gap;
+        double d_phi = d_dth * ORD_PI / gap;
+        acc(&dth[k], d_dth * ORD_PI * (ke->phi - ke->th_k1) / (gap * gap));
+        acc(&dth[k1], d_dth * (-(ke->phi - ke->th_k) * ORD_PI / (gap * gap)));
+        double du = 0.0, dv = 0.0;
+        if (ke->r2sq > 0.0) {
+            du += d_phi * (-pe.v / ke->r2sq);
+            dv += d_phi * (pe.u / ke->r2sq);
+        }
+        du += d_r2sq * 2.0 * pe.u;
+        dv += d_r2sq * 2.0 * pe.v;
+        /* r1 = |a| + |b|, (a, b) = Minv (u, v) */
+        double sa = ke->a > 0.0 ? 1.0 : (ke->a < 0.0 ? -1.0 : 0.0);
+        double sb = ke->b > 0.0 ? 1.0 : (ke->b < 0.0 ? -1.0 : 0.0);
+        double wx = ke->Minv[0] * sa + ke->Minv[2] * sb;   /* Minv^T (sa, sb) */
+        double wy = ke->Minv[1] * sa + ke->Minv[3] * sb;
+        du += d_r1 * wx;
+        dv += d_r1 * wy;
+        double ck = cos(ke->th_k), sk = sin(ke->th_k), ck1 = cos(ke->th_k1), sk1 = sin(ke->th_k1);
+        acc(&ds[k], d_r1 * (-ke->a) * (wx * ck + wy * sk));
+        acc(&dth[k], d_r1 * (-ke->a) * s[k] * (-wx * sk + wy * ck));
+        acc(&ds[k1], d_r1 * (-ke->b) * (wx * ck1 + wy * sk1));
+        acc(&dth[k1], d_r1 * (-ke->b) * s[k1] * (-wx * sk1 + wy * ck1));
+        /* geometry: u = Rx . p, v = Ry . p, p = t d - m, t = (m . Rz)/(d . Rz) */
+        double dp[3];
+        for (int c = 0; c < 3; c++) {
+            dR[3 * c + 0] += du * pe.p[c];
+            dR[3 * c + 1] += dv * pe.p[c];
+            dp[c] = du * pe.R[3 * c + 0] + dv * pe.R[3 * c + 1];
+        }
+        double dt = dot3(dp, pe.d);
+        for (int c = 0; c < 3; c++) {
+            double dm = -dp[c] + dt * pe.R[3 * c + 2] / pe.dn;
+            dmu[c] += dm;
+            dR[3 * c + 2] += -dt * pe.p[c] / pe.dn;
+        }
+    }
+    for (int c = 0; c < 3; c++) acc(&G->mu[3 * i + c], dmu[c]);
+    double dq[4];
+    rotation_backward(P->quat + 4 * i, dR, dq);
+    for (int c = 0; c < 4; c++) acc(&G->quat[4 * i + c], dq[c]);
+}
+
+static void color_backward(const ord_params *P, int64_t i, const double *ocam, const double *gc, ord_grads *G)
+{
+    if (P->sh_degree < 0) {
+        for (int c = 0; c < 3; c++) acc(&G->color[3 * i + c], gc[c]);
+        return;
+    }
+    int nc = ncoef_of(P->sh_degree);
+    const double *sh = P->color + (int64_t)3 * nc * i;
+    double dir[3];
+    for (int c = 0; c < 3; c++) dir[c] = P->mu[3 * i + c] - ocam[c];
+    double nr = sqrt(dot3(dir, dir));
+    for (int c = 0; c < 3; c++) dir[c] /= nr;
+    double Y[16], Gy[48];
+    ord_sh_basis(P->sh_degree, dir, Y);
+    sh_basis_grad(P->sh_degree, dir, Gy);
+    double rgb_pre[3];
+    for (int c = 0; c < 3; c++) {
+        rgb_pre[c] = 0.5;
+        for (int j = 0; j < nc; j++) rgb_pre[c] += sh[3 * j + c] * Y[j];
+    }
+    double ddir[3] = {0, 0, 0};
+    for (int c = 0; c < 3; c++) {
+        if (rgb_pre[c] < 0.0) continue;       /* clamped channel */
+        for (int j = 0; j < nc; j++) {
+            acc(&G->color[(int64_t)3 * nc * i + 3 * j + c], gc[c] * Y[j]);
+            for (int a = 0; a < 3; a++) ddir[a] += gc[c] * sh[3 * j + c] * Gy[3 * j + a];
+        }
+    }
+    double proj = dot3(ddir, dir);
+    for (int a = 0; a < 3; a++) acc(&G->mu[3 * i + a], (ddir[a] - dir[a] * proj) / nr);
+}
+
+/* Gradient of L = sum_q dL_drgb[q] . rgb[q] over the listed pixels with
+ * respect to every parameter (accumulated into G, which the caller zeroes).
+ * Back-to-front over each pixel's composited contributors:
+ *   dC/dc_j = T_j alpha_j,   dC/dalpha_j = T_j (c_j - B_j),
+ * where B_j is the colour composited behind contributor j (bg behind the
+ * last).  Returns 0, or -1 on allocation failure.                           */
+int ord_render_backward(const ord_params *P, const ord_camera *cam, const ord_options *opt, int64_t npix,
+                        const int32_t *pix, const double *dL_drgb, ord_grads *G)
+{
+    double ocam[3];
+    cam_center(cam, ocam);
+    int fail = 0;
+#pragma omp parallel
+    {
+        contrib *buf = (contrib *)malloc(sizeof(contrib) * (size_t)(P->n > 0 ? P->n : 1));
+        double *Tj = (double *)malloc(sizeof(double) * (size_t)(P->n > 0 ? P->n : 1));
+        double *cj = (double *)malloc(sizeof(double) * 3 * (size_t)(P->n > 0 ? P->n : 1));
+        if (!buf || !Tj || !cj) {
+#pragma omp atomic write
+            fail = 1;
+        }
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t q = 0; q < npix; q++) {
+            if (!buf || !Tj || !cj) continue;
+            int px = pix[2 * q], py = pix[2 * q + 1];
+            const double *gC = dL_drgb + 3 * q;
+            int near_amin;
+            int64_t cnt = gather_contributors(P, cam, opt, ocam, px, py, buf, &near_amin);
+            int64_t nc = composite_count(buf, cnt, opt->T_min);
+            double T = 1.0;
+            for (int64_t j = 0; j < nc; j++) {
+                int cl[3];
+                Tj[j] = T;
+                prim_color(P, buf[j].idx, ocam, cj + 3 * j, cl);
+                T *= 1.0 - buf[j].alpha;
+            }
+            double B[3] = {opt->bg[0], opt->bg[1], opt->bg[2]};
+            for (int64_t j = nc - 1; j >= 0; j--) {
+                double a = buf[j].alpha;
+                double gc[3], ga = 0.0;
+                for (int c = 0; c < 3; c++) {
+                    gc[c] = gC[c] * Tj[j] * a;
+                    ga += gC[c] * Tj[j] * (cj[3 * j + c] - B[c]);
+                }
+                color_backward(P, buf[j].idx, ocam, gc, G);
+                pair_backward(P, buf[j].idx, cam, opt, ocam, px, py, ga, G);
+                for (int c = 0; c < 3; c++) B[c] = a * cj[3 * j + c] + (1.0 - a) * B[c];
+            }
+        }
+        free(buf);
+        free(Tj);
+        free(cj);
+    }
+    return fail ? -1 : 0;
+}
+
+int ord_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void ord_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
