@@ -1,0 +1,324 @@
+#!/usr/bin/env python
+"""Throughput of the DRK splatting hot path on GB300: Mpix/s of one
+forward + backward render (Sec. 4.4 pipeline and its reverse mode) of a
+100k-primitive, K = 8, SH-degree-3 scene at 1920 x 1080, synthetic data.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl drk|reference]
+
+One process per GPU (torchrun for N > 1).  The path does not shard: every
+rank renders its own replica of the workload ("replicas only"), value =
+pixels of all ranks / max-over-ranks step time.  Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2412_11752_gb300 import synth  # noqa: E402
+
+METRIC = "Mpix/s fwd+bwd at 1080p/100k DRK"
+WORKLOAD = "clustered-100k-1080p"
+
+# Algorithmic FP32 operations per (pixel, primitive) evaluation of Eq. 4 -
+# Eq. 10 on the FMA/ALU pipes (one per add, mul, fma, compare, select; the
+# atan2 polynomial counted as 16; transcendental MUFU ops not included).
+OPS_PER_EVAL = 66
+# extra operations per composited contributor in the backward (Eq. 1
+# gradient, chain through Eq. 10 - Eq. 4 to the record quantities)
+OPS_PER_EMIT_BWD = 190
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("drk", "reference"), default="drk")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-pixels", type=int, default=1024, help="oracle sample size (pixels, fwd+bwd)")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu_id}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except Exception:
+        return {}
+
+
+def dist_setup():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+def oracle_rate(scene, cam, pixels: int, seed: int = 7) -> tuple[float, dict]:
+    """Oracle (FP64 CPU) forward + backward over a seeded pixel sample: Mpix/s."""
+    from oracle import drk_oracle as O
+    opt = O.Options(alpha_min=float(np.float32(np.exp(-9.0))), T_min=float(np.float32(1e-4)),
+                    alpha_max=float(np.float32(0.99)), lowpass_sl=float(np.float32(0.70710678)),
+                    near=float(np.float32(0.2)))
+    pix = synth.pixel_sample(cam.width, cam.height, pixels, seed=seed)
+    g = np.random.default_rng(seed).standard_normal((pix.shape[0], 3))
+    t0 = time.perf_counter()
+    O.render_pixels(scene, cam, opt, pix)
+    O.render_backward_pixels(scene, cam, opt, pix, g)
+    dt = time.perf_counter() - t0
+    info = {"cores": O.max_threads(),
+            "sample": f"{pix.shape[0]} seeded pixels of the {cam.width}x{cam.height} frame, forward + backward "
+                      f"(brute force over all {scene.n} primitives per pixel, FP64)",
+            "seconds": dt}
+    return pix.shape[0] / dt / 1e6, info
+
+
+def run_reference(args):
+    rank, world, local = dist_setup()
+    if rank != 0:
+        return 0
+    sc_f, cam_f = synth.WORKLOADS[args.workload]
+    scene, cam = sc_f(), cam_f()
+    px = max(16, args.cpu_pixels // 4)
+    for _ in range(max(0, args.warmup)):
+        oracle_rate(scene, cam, 16, seed=1)
+    rates, infos = [], []
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        r, info = oracle_rate(scene, cam, px, seed=100 + k)
+        rates.append(r)
+        infos.append(info)
+    wall = time.perf_counter() - t0
+    value = args.steps * px / sum(i["seconds"] for i in infos) / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "pixels_per_step": px, "parallelism": "host threads"},
+            "cpu_baseline": {"value": value, "unit": "Mpix/s", "cores": infos[0]["cores"], "kind": "oracle",
+                             "sample": infos[0]["sample"].replace(f"{px} seeded", f"{px} seeded (per step)")},
+            "e2e": {"value": value, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+def run_drk(args):
+    import torch
+    rank, world, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2412_11752_gb300 import drk
+
+    sc_f, cam_f = synth.WORKLOADS[args.workload]
+    scene, cam = sc_f(), cam_f()
+    H, W = cam.height, cam.width
+    ds = drk.DeviceScene.from_scene(scene, dev)
+    target = torch.from_numpy(synth.target_image(H, W)).to(dev)
+    opt = drk.Options()
+    ctx = drk.Context(local)
+    out = dict(rgb=torch.empty((3, H, W), device=dev), T=None, n=None)
+    inv_n = 1.0 / float(3 * H * W)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+
+    def step(scene_dev):
+        rgb, _, _, st = drk.drk_render(scene_dev, cam, opt, ctx=ctx, need_state=True, out=out)
+        dL = torch.sign(rgb - target).mul_(inv_n)      # d(mean |C - target|)/dC
+        g = drk.drk_render_backward(scene_dev, cam, opt, st, dL, ctx=ctx)
+        st.free()
+        return rgb, g
+
+    for _ in range(args.warmup):
+        step(ds)
+    torch.cuda.synchronize()
+
+    # ---- device-timed region
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = getattr(props, "uuid", None)
+    gpu_id = f"GPU-{gpu_id}" if gpu_id is not None and not str(gpu_id).startswith("GPU-") else (gpu_id or str(local))
+    sampler = ClockSampler(str(gpu_id))
+    ctx.timing_enable(True)
+    l0 = drk.launch_count()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    sampler.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()                                  # evict L2 between steps (untimed)
+        starts[k].record()
+        step(ds)
+        ends[k].record()
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    launches = drk.launch_count() - l0
+    stage = ctx.timing_read()
+    ctx.timing_enable(False)
+    stats = ctx.stats()
+    ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms_step = max_over_ranks(float(np.mean(ms)), world, dev)
+    value = world * H * W / (ms_step / 1e3) / 1e6
+
+    # ---- roofline of the dominant kernel (FP32 ALU bound)
+    peaks = measured_peaks()
+    sms = props.multi_processor_count
+    smax = float(peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0)
+    peak_tops = sms * 128 * smax * 1e6 / 1e12
+    fwd_ms = stage["raster"][0] / max(1, stage["raster"][1])
+    bwd_ms = stage["raster_bwd"][0] / max(1, stage["raster_bwd"][1])
+    if fwd_ms >= bwd_ms:
+        dom, dom_ms, ops = "raster_fwd", fwd_ms, stats["n_evals"] * OPS_PER_EVAL
+    else:
+        dom, dom_ms, ops = "raster_bwd", bwd_ms, stats["n_evals"] * OPS_PER_EVAL + stats["n_emitted"] * OPS_PER_EMIT_BWD
+    achieved = ops / (dom_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tops, "unit": "Top/s",
+                "frac": achieved / peak_tops, "traffic": None,
+                "peak_basis": f"{sms} SMs x 128 FP32 lanes x {smax:.0f} MHz (max SM clock, MEASURED_PEAKS.json)"}
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        host_params = {k: torch.from_numpy(np.ascontiguousarray(getattr(scene, k), np.float32)).pin_memory()
+                       for k in drk.PARAM_NAMES}
+        host_rgb = torch.empty((3, H, W), dtype=torch.float32).pin_memory()
+        host_grads = {k: torch.empty_like(v).pin_memory() for k, v in host_params.items()}
+        dev_params = {k: torch.empty(v.shape, dtype=torch.float32, device=dev) for k, v in host_params.items()}
+        h2d = sum(v.numel() * 4 for v in host_params.values())
+        d2h = host_rgb.numel() * 4 + sum(v.numel() * 4 for v in host_grads.values())
+        e_steps = max(3, args.steps // 2)
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e_steps):
+            for k in drk.PARAM_NAMES:
+                dev_params[k].copy_(host_params[k], non_blocking=True)
+            sd = drk.DeviceScene(**dev_params, sh_degree=scene.sh_degree)
+            rgb, g = step(sd)
+            host_rgb.copy_(rgb, non_blocking=True)
+            for k in drk.PARAM_NAMES:
+                host_grads[k].copy_(g[k], non_blocking=True)
+            torch.cuda.synchronize()
+        wall = max_over_ranks(time.perf_counter() - t0, world, dev)
+        e2e = {"value": world * e_steps * H * W / wall / 1e6, "unit": "Mpix/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r, info = oracle_rate(scene, cam, args.cpu_pixels)
+        cpu = {"value": r, "unit": "Mpix/s", "cores": info["cores"], "kind": "oracle", "sample": info["sample"]}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": args.workload, "primitives": scene.n, "K": scene.K,
+                           "sh_degree": scene.sh_degree, "width": W, "height": H, "tile": 16,
+                           "cull_level": opt.cull_level, "kbuf_capacity": opt.kbuf_capacity,
+                           "step": "render + L1-loss gradient + backward to all parameters",
+                           "l2": "flushed between timed steps (256 MiB write)",
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clocks,
+                "stages_ms": {k: v[0] / max(1, v[1]) for k, v in stage.items() if v[1]},
+                "counters": {k: stats[k] for k in ("n_pairs", "n_evals", "n_emitted", "n_extra_passes", "n_visible")}}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_drk(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

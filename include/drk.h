@@ -1,0 +1,211 @@
+/*
+ * drk.h -- C ABI of libdrk, the GB300 (sm_103a) hot path of Deformable
+ * Radial Kernel (DRK) splatting.
+ *
+ * The library renders planar DRK primitives (Sec. 4: centre mu, rotation q,
+ * K radial bases (s_k, theta_k), L1/L2 blend eta, sharpness tau, opacity o,
+ * colour) through a tile-based rasterizer (Sec. 4.4, "Kernel Culling" and
+ * "Cache Sorting"): per-primitive preprocess with a conservative K-basis
+ * screen bound, per-(primitive, tile) pair emission with tile culling, a
+ * device radix sort on tile|depth keys, and a per-tile rasterizer that
+ * intersects each pixel ray with the primitive plane (Eq. 4, Eq. 5),
+ * evaluates the kernel (Eq. 6 - Eq. 10), and composites front to back in
+ * exact per-pixel ray-depth order (Eq. 1, Eq. 13).  The derivative of the
+ * rendered image with respect to every primitive parameter is available
+ * through drk_render_backward (the paper trains through its renderer,
+ * Sec. 1 and the supplementary "Tensor Graph"; the backward visits each
+ * pixel's contributors front to back as the supplementary "Cache-Sorting"
+ * paragraph requires).
+ *
+ * Conventions (the paper leaves these open):
+ *   - Pinhole camera, OpenCV axes (x right, y down, z forward); pixel (x, y)
+ *     has its centre at (x + 0.5, y + 0.5); world_to_cam is the row-major
+ *     3 x 4 [R | t] with x_cam = R x_world + t, R orthonormal.
+ *   - R_x, R_y, R_z of Eq. 4 / Eq. 5 are the columns of R(q), q = (w, x, y, z)
+ *     normalised by the library.
+ *   - The polar angle is atan2(v, u) over the full circle; angles
+ *     theta_0 < ... < theta_{K-1} with theta_{K-1} - theta_0 < 2 pi and every
+ *     cyclic gap below pi; the last sector wraps to theta_0 + 2 pi with s_0.
+ *   - r_t (Eq. 13) is the view-space depth of the ray-plane intersection;
+ *     pairs with r_t <= near_plane are skipped.
+ *   - alpha_tilde = min(max(o Psi(g), filter), alpha_max) (Eq. 9, Eq. 10);
+ *     a pair contributes iff alpha_tilde >= alpha_min; compositing stops
+ *     before the first contributor with T (1 - alpha_tilde) < T_min;
+ *     contributors are composited in (r_t, primitive index) order.
+ *   - Colour: plain RGB (sh_degree = -1) or real spherical harmonics of
+ *     degree 0..3 evaluated in the direction camera centre -> mu, plus 0.5,
+ *     clamped below at 0.  bg is added with the final transmittance.
+ *
+ * Memory: every pointer argument that refers to per-primitive or per-pixel
+ * data is a DEVICE pointer owned by the caller, unless a field says
+ * otherwise.  Structures themselves are passed by host pointer and read
+ * during the call only.  All calls with a `stream` argument are
+ * asynchronous on that stream (a cudaStream_t passed as void*, NULL = the
+ * legacy default stream) unless stated; they never call
+ * cudaDeviceSynchronize.  Errors detected on the host are returned before
+ * anything is launched; errors detected on the device (capacity) are
+ * recorded in the context and returned by the next synchronising call.
+ * drk_last_error() gives a message for the last failure on the calling
+ * thread.  No call traps or asserts on the device.
+ */
+#ifndef DRK_H
+#define DRK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DRK_OK = 0,
+    DRK_ERR_INVALID_ARG = 1,  /* rejected on the host before any launch */
+    DRK_ERR_OOM = 2,          /* device allocation failed or over budget */
+    DRK_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+    DRK_ERR_CAPACITY = 4,     /* a fixed-capacity buffer was too small */
+    DRK_ERR_TIMEOUT = 5,      /* a bounded wait expired */
+    DRK_ERR_BUSY = 6,         /* no free slot; retry later */
+    DRK_ERR_NOT_FOUND = 7     /* unknown ticket or scene */
+} drk_status_t;
+
+/* Activated DRK parameters (Sec. 4), structure of arrays, float32, device.
+ *   mu       n x 3           centre
+ *   quat     n x 4           rotation (w, x, y, z), any non-zero norm
+ *   scale    n x K           radial lengths s_k > 0
+ *   theta    n x K           polar angles, ascending (see conventions)
+ *   eta      n               L1/L2 blend in [0, 1] (Eq. 8)
+ *   tau      n               sharpness in (-1, 1) (Eq. 9)
+ *   opacity  n               o in (0, 1]
+ *   color    n x 3           plain RGB when sh_degree = -1, else
+ *            n x (d+1)^2 x 3 SH coefficients, coefficient-major, RGB inner
+ * 3 <= K <= 16, -1 <= sh_degree <= 3, 0 <= n < 2^31. */
+typedef struct {
+    int64_t n;
+    int32_t K;
+    int32_t sh_degree;
+    const float *mu, *quat, *scale, *theta, *eta, *tau, *opacity, *color;
+} drk_params_t;
+
+/* Gradients, same shapes as drk_params_t; written (not accumulated) by
+ * drk_render_backward. */
+typedef struct {
+    float *mu, *quat, *scale, *theta, *eta, *tau, *opacity, *color;
+} drk_params_grad_t;
+
+typedef struct {
+    int32_t width, height;      /* 1 .. 16384 */
+    float fx, fy, cx, cy;       /* pixels */
+    float world_to_cam[12];     /* host values, row-major 3 x 4 */
+} drk_camera_t;
+
+/* Tile culling levels (Sec. 4.4, "Kernel Culling").  All three give the
+ * same image bit for bit: culling only removes pairs that cannot reach
+ * alpha_min. */
+enum {
+    DRK_CULL_NONE = 0,   /* every primitive is paired with every tile */
+    DRK_CULL_RECT = 1,   /* tiles of the screen rectangle of the K-basis bound */
+    DRK_CULL_TILE = 2    /* plus a per-tile test against the per-sector radii */
+};
+
+typedef struct {
+    float alpha_min;      /* contribution threshold; default exp(-9) (Eq. 11) */
+    float T_min;          /* early-termination transmittance; default 1e-4 */
+    float alpha_max;      /* alpha clamp; default 0.99 */
+    float lowpass_sl;     /* low-pass filter radius s_l of Eq. 10 in pixels; 0 = off */
+    float near_plane;     /* default 0.2 */
+    float bg[3];          /* background colour */
+    int32_t cull_level;   /* DRK_CULL_*; default DRK_CULL_TILE */
+    int32_t kbuf_capacity;/* per-pixel depth-order buffer entries: 8 or 16 */
+    int32_t reserved[6];  /* must be zero */
+} drk_options_t;
+
+/* Fills *opt with the defaults listed above. */
+void drk_options_default(drk_options_t *opt);
+
+/* Output image, device, float32 planar. */
+typedef struct {
+    float *rgb;           /* 3 x H x W, includes T_final * bg */
+    float *T_final;       /* H x W final transmittance, may be NULL */
+    int32_t *n_emitted;   /* H x W number of composited contributors, may be NULL */
+} drk_image_t;
+
+/* Counters of the last render on a context (device-side counts). */
+typedef struct {
+    int64_t n_visible;    /* primitives with a non-empty bound */
+    int64_t n_pairs;      /* (primitive, tile) pairs after culling */
+    int64_t n_evals;      /* kernel evaluations (pixel, primitive) */
+    int64_t n_emitted;    /* composited contributions */
+    int64_t n_extra_passes;/* extra list passes taken by pixels whose depth
+                             buffer filled (exactness is kept) */
+    int64_t n_tiles;
+    int32_t key_bits_depth;
+    int32_t status;       /* device-side drk_status_t of the last render */
+} drk_stats_t;
+
+typedef struct drk_ctx drk_ctx_t;
+typedef struct drk_state drk_state_t;
+
+/* A context owns device scratch memory (grown on demand from a
+ * stream-ordered pool) and the counters of its last render.  One context
+ * may be used from one host thread at a time.  `device` is the CUDA
+ * ordinal. */
+drk_status_t drk_ctx_create(int device, drk_ctx_t **out);
+void drk_ctx_destroy(drk_ctx_t *ctx);
+
+/* Forward render (Sec. 4.4 pipeline).  params, cam, opt: host structs whose
+ * array fields are device pointers.  out: device image buffers of the
+ * camera's size.  If state != NULL, *state receives a library-owned object
+ * holding what drk_render_backward needs (free it with drk_state_free).
+ * The call reads the pair count back to the host once (a stream sync) to
+ * size the sort; everything else is asynchronous.  Returns
+ * DRK_ERR_INVALID_ARG for bad sizes or options, DRK_ERR_OOM if scratch
+ * cannot grow, DRK_ERR_CUDA on a launch failure. */
+drk_status_t drk_render(drk_ctx_t *ctx, const drk_params_t *params, const drk_camera_t *cam,
+                        const drk_options_t *opt, const drk_image_t *out, drk_state_t **state,
+                        void *stream);
+
+/* Reverse mode of drk_render for the same params, cam and opt and the
+ * state it produced: grads <- d(sum dL_drgb * rgb)/d(params).  dL_drgb is a
+ * device 3 x H x W array.  grads arrays are overwritten.  Asynchronous. */
+drk_status_t drk_render_backward(drk_ctx_t *ctx, const drk_params_t *params, const drk_camera_t *cam,
+                                 const drk_options_t *opt, const drk_state_t *state,
+                                 const float *dL_drgb, const drk_params_grad_t *grads, void *stream);
+
+void drk_state_free(drk_state_t *state);
+
+/* Stable ascending sort of n (key, value) pairs by the low key_bits bits of
+ * the keys (1..32), in place, on device arrays -- the LSD radix sort the
+ * render uses for its (tile | depth) keys (Sec. 4.4).  Scratch comes from
+ * the context's pool.  Asynchronous.  n < 2^32. */
+drk_status_t drk_sort_pairs(drk_ctx_t *ctx, uint32_t *keys, uint32_t *vals, int64_t n, int key_bits, void *stream);
+
+/* Synchronises the stream of the last render and copies its counters. */
+drk_status_t drk_get_stats(drk_ctx_t *ctx, drk_stats_t *out);
+
+/* Stage timing with CUDA events recorded on the caller's stream around each
+ * stage of drk_render / drk_render_backward.  Stages: 0 preprocess (bounds,
+ * culling count, scan), 1 pair emission, 2 radix sort and tile ranges,
+ * 3 raster forward, 4 raster backward, 5 preprocess backward (6, 7
+ * unused).  drk_timing_enable resets the accumulators and switches timing
+ * on (enable != 0) or off.  drk_timing_read waits for the recorded events
+ * and returns, per stage, the summed milliseconds and the number of timed
+ * launches (host arrays of 8). */
+drk_status_t drk_timing_enable(drk_ctx_t *ctx, int enable);
+drk_status_t drk_timing_read(drk_ctx_t *ctx, double *ms, int64_t *launches);
+
+/* Number of kernel launches the library has issued so far, process-wide
+ * (host counter). */
+int64_t drk_launch_count(void);
+
+/* Message for the last failure on the calling thread ("" if none). */
+const char *drk_last_error(void);
+
+/* Library version string. */
+const char *drk_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DRK_H */

@@ -1,0 +1,574 @@
+// api.cu -- C ABI of libdrk: contexts, forward render, backward, counters.
+//
+// Pipeline of drk_render (Sec. 4.4):
+//   K1 preprocess (per primitive)  -> raster records, colours, bounds
+//   K2 count (per-tile culling)    -> pairs per primitive; exclusive scan
+//      host reads the pair total back once (sizes the sort)
+//   K2 emit                        -> (tile | depth) keys, primitive values
+//   K3 radix sort                  -> pairs grouped by tile, by depth bound
+//   K4 tile ranges
+//   K5 raster                      -> image, final transmittance, counts
+// drk_render_backward replays K5 (K6) and then runs the per-primitive
+// backward (K7).
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "drk_internal.h"
+
+using namespace drk;
+
+namespace {
+std::atomic<long long> g_launches{0};
+}
+namespace drk {
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace drk
+
+// CUDA-event timing of the pipeline stages (off unless enabled)
+enum { ST_PREPROCESS = 0, ST_EMIT, ST_SORT, ST_RASTER, ST_RASTER_BWD, ST_PREPROCESS_BWD, ST_COUNT = 8 };
+struct StageTimer {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    struct Pending { int stage; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    double ms[ST_COUNT] = {0};
+    long long cnt[ST_COUNT] = {0};
+    cudaEvent_t get() {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    cudaEvent_t begin(cudaStream_t st) {
+        if (!on) return nullptr;
+        cudaEvent_t a = get();
+        cudaEventRecord(a, st);
+        return a;
+    }
+    void end(int stage, cudaEvent_t a, cudaStream_t st) {
+        if (!on || !a) return;
+        cudaEvent_t b = get();
+        cudaEventRecord(b, st);
+        pending.push_back({stage, a, b});
+    }
+    void collect() {
+        for (auto& p : pending) {
+            float t = 0.f;
+            cudaEventSynchronize(p.b);
+            cudaEventElapsedTime(&t, p.a, p.b);
+            ms[p.stage] += t;
+            cnt[p.stage] += 1;
+            pool.push_back(p.a);
+            pool.push_back(p.b);
+        }
+        pending.clear();
+    }
+    void destroy() {
+        collect();
+        for (auto e : pool) cudaEventDestroy(e);
+        pool.clear();
+    }
+};
+
+struct drk_ctx {
+    StageTimer timer;
+    int device = 0;
+    cudaMemPool_t pool = nullptr;
+    cudaStream_t last_stream = nullptr;
+    unsigned long long* counters = nullptr;   // evals, emitted, extra passes, visible
+    int* zmax_bits = nullptr;                 // counters[4] holds the device status bits
+    DepthQuant* dq = nullptr;
+    uint64_t* h_total = nullptr;              // pinned
+    drk_stats_t last{};
+};
+
+struct drk_state {
+    drk_ctx* ctx = nullptr;
+    cudaStream_t stream = nullptr;
+    int64_t n = 0, pairs = 0;
+    int K = 0, kmax = 0, cap = 0, sh_degree = 0, width = 0, height = 0;
+    FrameConst fc{};
+    float* rec = nullptr;
+    float* rgb = nullptr;
+    uint32_t* keys = nullptr;
+    uint32_t* vals = nullptr;
+    uint2* ranges = nullptr;
+    DepthQuant* dq = nullptr;
+    float* Cfin = nullptr;
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+drk_status_t fail(drk_status_t s, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+#define DRK_CUDA(call)                                                                     \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(DRK_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));     \
+    } while (0)
+
+// stream-ordered allocations of one call; freed together unless kept
+struct Allocs {
+    cudaMemPool_t pool;
+    cudaStream_t st;
+    std::vector<void*> ptrs;
+    bool keep = false;
+    Allocs(cudaMemPool_t p, cudaStream_t s) : pool(p), st(s) {}
+    ~Allocs() {
+        if (!keep)
+            for (void* q : ptrs) cudaFreeAsync(q, st);
+    }
+    template <typename T>
+    drk_status_t get(T** out, size_t count) {
+        void* q = nullptr;
+        const size_t bytes = count * sizeof(T) > 0 ? count * sizeof(T) : 16;
+        const cudaError_t e = cudaMallocFromPoolAsync(&q, bytes, pool, st);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(DRK_ERR_OOM, "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+        }
+        ptrs.push_back(q);
+        *out = reinterpret_cast<T*>(q);
+        return DRK_OK;
+    }
+};
+
+bool finite_pos(float v) { return std::isfinite(v) && v > 0.f; }
+
+drk_status_t validate(const drk_params_t* p, const drk_camera_t* cam, const drk_options_t* opt) {
+    if (!p || !cam || !opt) return fail(DRK_ERR_INVALID_ARG, "null params, camera or options");
+    if (p->n < 0 || p->n >= (int64_t(1) << 31)) return fail(DRK_ERR_INVALID_ARG, "n = %lld out of range", (long long)p->n);
+    if (p->K < 3 || p->K > 16) return fail(DRK_ERR_INVALID_ARG, "K = %d not in [3, 16]", p->K);
+    if (p->sh_degree < -1 || p->sh_degree > 3)
+        return fail(DRK_ERR_INVALID_ARG, "sh_degree = %d not in [-1, 3]", p->sh_degree);
+    if (p->n > 0 && (!p->mu || !p->quat || !p->scale || !p->theta || !p->eta || !p->tau || !p->opacity || !p->color))
+        return fail(DRK_ERR_INVALID_ARG, "null parameter array");
+    if (cam->width < 1 || cam->height < 1 || cam->width > 16384 || cam->height > 16384)
+        return fail(DRK_ERR_INVALID_ARG, "image size %d x %d out of range", cam->width, cam->height);
+    if (!finite_pos(cam->fx) || !finite_pos(cam->fy) || !std::isfinite(cam->cx) || !std::isfinite(cam->cy))
+        return fail(DRK_ERR_INVALID_ARG, "bad intrinsics");
+    for (int i = 0; i < 12; i++)
+        if (!std::isfinite(cam->world_to_cam[i])) return fail(DRK_ERR_INVALID_ARG, "non-finite world_to_cam");
+    if (!(opt->alpha_min > 0.f && opt->alpha_min < 1.f)) return fail(DRK_ERR_INVALID_ARG, "alpha_min not in (0, 1)");
+    if (!(opt->alpha_max >= opt->alpha_min && opt->alpha_max < 1.f))
+        return fail(DRK_ERR_INVALID_ARG, "alpha_max not in [alpha_min, 1)");
+    if (!(opt->T_min >= 0.f && opt->T_min < 1.f)) return fail(DRK_ERR_INVALID_ARG, "T_min not in [0, 1)");
+    if (!(opt->lowpass_sl >= 0.f) || !std::isfinite(opt->lowpass_sl)) return fail(DRK_ERR_INVALID_ARG, "bad lowpass_sl");
+    if (!finite_pos(opt->near_plane)) return fail(DRK_ERR_INVALID_ARG, "near_plane must be > 0");
+    if (opt->cull_level < 0 || opt->cull_level > 2) return fail(DRK_ERR_INVALID_ARG, "cull_level not in 0..2");
+    if (opt->kbuf_capacity != 8 && opt->kbuf_capacity != 16)
+        return fail(DRK_ERR_INVALID_ARG, "kbuf_capacity must be 8 or 16");
+    for (int i = 0; i < 6; i++)
+        if (opt->reserved[i] != 0) return fail(DRK_ERR_INVALID_ARG, "reserved option fields must be zero");
+    for (int i = 0; i < 3; i++)
+        if (!std::isfinite(opt->bg[i])) return fail(DRK_ERR_INVALID_ARG, "non-finite bg");
+    return DRK_OK;
+}
+
+struct Frame {
+    FrameConst fc;
+    CamDev cam;
+    float center[3];
+    int n_tiles, tile_bits, depth_bits, kmax;
+};
+
+Frame make_frame(const drk_params_t* p, const drk_camera_t* cam, const drk_options_t* opt) {
+    Frame F;
+    FrameConst& fc = F.fc;
+    fc.width = cam->width;
+    fc.height = cam->height;
+    fc.tiles_x = (cam->width + kTile - 1) / kTile;
+    fc.tiles_y = (cam->height + kTile - 1) / kTile;
+    fc.ifx = (float)(1.0 / cam->fx);
+    fc.ify = (float)(1.0 / cam->fy);
+    fc.ox = (float)((0.5 - (double)cam->cx) / cam->fx);
+    fc.oy = (float)((0.5 - (double)cam->cy) / cam->fy);
+    fc.near_plane = opt->near_plane;
+    fc.alpha_min = opt->alpha_min;
+    fc.alpha_max = opt->alpha_max;
+    fc.T_min = opt->T_min;
+    for (int c = 0; c < 3; c++) fc.bg[c] = opt->bg[c];
+    F.cam.fx = cam->fx; F.cam.fy = cam->fy; F.cam.cx = cam->cx; F.cam.cy = cam->cy;
+    for (int i = 0; i < 12; i++) F.cam.w2c[i] = cam->world_to_cam[i];
+    const float* M = cam->world_to_cam;
+    for (int i = 0; i < 3; i++)
+        F.center[i] = (float)(-((double)M[i] * M[3] + (double)M[4 + i] * M[7] + (double)M[8 + i] * M[11]));
+    F.n_tiles = fc.tiles_x * fc.tiles_y;
+    int tb = 1;
+    while ((1 << tb) < F.n_tiles + 1) tb++;   // one spare id for sentinel keys
+    F.tile_bits = tb;
+    F.depth_bits = 32 - tb;
+    F.kmax = p->K <= 8 ? 8 : 16;
+    return F;
+}
+
+size_t rec_floats(int kmax) { return kmax == 8 ? Rec<8>::STRIDE : Rec<16>::STRIDE; }
+size_t bnd_floats(int kmax) { return kmax == 8 ? Bnd<8>::STRIDE : Bnd<16>::STRIDE; }
+
+drk_status_t check_launch() {
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(DRK_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+    return DRK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void drk_options_default(drk_options_t* opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->alpha_min = expf(-9.0f);
+    opt->T_min = 1e-4f;
+    opt->alpha_max = 0.99f;
+    opt->lowpass_sl = 0.70710678f;
+    opt->near_plane = 0.2f;
+    opt->cull_level = DRK_CULL_TILE;
+    opt->kbuf_capacity = 16;
+}
+
+const char* drk_last_error(void) { return g_err; }
+
+const char* drk_version(void) { return "libdrk 0.1 (sm_103a)"; }
+
+drk_status_t drk_ctx_create(int device, drk_ctx_t** out) {
+    if (!out) return fail(DRK_ERR_INVALID_ARG, "null out");
+    *out = nullptr;
+    int ndev = 0;
+    DRK_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(DRK_ERR_INVALID_ARG, "device %d of %d", device, ndev);
+    DRK_CUDA(cudaSetDevice(device));
+    drk_ctx* c = new (std::nothrow) drk_ctx();
+    if (!c) return fail(DRK_ERR_OOM, "host allocation failed");
+    c->device = device;
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    cudaError_t e = cudaMemPoolCreate(&c->pool, &props);
+    if (e != cudaSuccess) {
+        delete c;
+        return fail(DRK_ERR_CUDA, "cudaMemPoolCreate: %s", cudaGetErrorString(e));
+    }
+    uint64_t thr = ~0ull;
+    cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    if (cudaMalloc(&c->counters, 8 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&c->zmax_bits, sizeof(int)) != cudaSuccess || cudaMalloc(&c->dq, sizeof(DepthQuant)) != cudaSuccess ||
+        cudaMallocHost(&c->h_total, 2 * sizeof(uint64_t)) != cudaSuccess) {
+        cudaGetLastError();
+        drk_ctx_destroy(c);
+        return fail(DRK_ERR_OOM, "context buffers");
+    }
+    *out = c;
+    return DRK_OK;
+}
+
+void drk_ctx_destroy(drk_ctx_t* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->last_stream) cudaStreamSynchronize(c->last_stream);
+    cudaFree(c->counters);
+    cudaFree(c->zmax_bits);
+    cudaFree(c->dq);
+    if (c->h_total) cudaFreeHost(c->h_total);
+    c->timer.destroy();
+    if (c->pool) cudaMemPoolDestroy(c->pool);
+    delete c;
+}
+
+drk_status_t drk_render(drk_ctx_t* ctx, const drk_params_t* params, const drk_camera_t* cam, const drk_options_t* opt,
+                        const drk_image_t* out, drk_state_t** state, void* stream) {
+    if (!ctx) return fail(DRK_ERR_INVALID_ARG, "null context");
+    if (state) *state = nullptr;
+    drk_status_t s = validate(params, cam, opt);
+    if (s != DRK_OK) return s;
+    if (!out || !out->rgb) return fail(DRK_ERR_INVALID_ARG, "null output image");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    DRK_CUDA(cudaSetDevice(ctx->device));
+    ctx->last_stream = st;
+    const Frame F = make_frame(params, cam, opt);
+    const int64_t n = params->n;
+    Allocs al(ctx->pool, st);
+
+    PreArgs A;
+    std::memset(&A, 0, sizeof(A));
+    A.p = *params;
+    A.cam = F.cam;
+    for (int c = 0; c < 3; c++) A.cam_center[c] = F.center[c];
+    A.fc = F.fc;
+    A.sl = opt->lowpass_sl;
+    A.cull_level = opt->cull_level;
+    A.depth_bits = F.depth_bits;
+    A.zmax_bits = ctx->zmax_bits;
+    A.counters = ctx->counters;
+    A.status = reinterpret_cast<int*>(ctx->counters + 4);
+    if ((s = al.get(&A.rec, (size_t)n * rec_floats(F.kmax))) != DRK_OK) return s;
+    if ((s = al.get(&A.bnd, (size_t)n * bnd_floats(F.kmax))) != DRK_OK) return s;
+    if ((s = al.get(&A.rgb, (size_t)n * 3)) != DRK_OK) return s;
+    if ((s = al.get(&A.count, (size_t)n + 1)) != DRK_OK) return s;
+    if ((s = al.get(&A.offsets, (size_t)n + 1)) != DRK_OK) return s;
+    void* scan_scr = nullptr;
+    if ((s = al.get(reinterpret_cast<uint8_t**>(&scan_scr), scan_scratch_bytes(n + 1))) != DRK_OK) return s;
+    DepthQuant* dq = nullptr;
+    if ((s = al.get(&dq, 1)) != DRK_OK) return s;
+    A.dq = dq;
+
+    const float near_bits_f = opt->near_plane;
+    int near_bits;
+    std::memcpy(&near_bits, &near_bits_f, sizeof(int));
+    DRK_CUDA(cudaMemcpyAsync(ctx->zmax_bits, &near_bits, sizeof(int), cudaMemcpyHostToDevice, st));
+    DRK_CUDA(cudaMemsetAsync(ctx->counters, 0, 8 * sizeof(unsigned long long), st));
+
+    StageTimer& tm = ctx->timer;
+    cudaEvent_t ev = tm.begin(st);
+    if (F.kmax == 8) launch_preprocess<8>(A, st); else launch_preprocess<16>(A, st);
+    if (opt->cull_level >= 2) {
+        if (F.kmax == 8) launch_count<8>(A, st); else launch_count<16>(A, st);
+    }
+    if ((s = check_launch()) != DRK_OK) return s;
+    exclusive_scan_u32_u64(A.count, A.offsets, n, scan_scr, st);
+    launch_depth_quant(A, st);
+    tm.end(ST_PREPROCESS, ev, st);
+    DRK_CUDA(cudaMemcpyAsync(ctx->h_total, A.offsets + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    DRK_CUDA(cudaStreamSynchronize(st));
+    const int64_t P = (int64_t)ctx->h_total[0];
+    if (P >= (int64_t(1) << 32) - 1)
+        return fail(DRK_ERR_CAPACITY, "%lld pairs exceed the 2^32 - 1 limit of one render", (long long)P);
+
+    uint32_t *kalt = nullptr, *valt = nullptr;
+    uint2* ranges = nullptr;
+    void* sort_scr = nullptr;
+    if ((s = al.get(&A.keys, (size_t)P)) != DRK_OK) return s;
+    if ((s = al.get(&A.vals, (size_t)P)) != DRK_OK) return s;
+    if ((s = al.get(&kalt, (size_t)P)) != DRK_OK) return s;
+    if ((s = al.get(&valt, (size_t)P)) != DRK_OK) return s;
+    if ((s = al.get(&ranges, (size_t)F.n_tiles)) != DRK_OK) return s;
+    if ((s = al.get(reinterpret_cast<uint8_t**>(&sort_scr), radix_sort_scratch_bytes(P))) != DRK_OK) return s;
+
+    ev = tm.begin(st);
+    if (F.kmax == 8) launch_emit<8>(A, st); else launch_emit<16>(A, st);
+    tm.end(ST_EMIT, ev, st);
+    ev = tm.begin(st);
+    radix_sort_pairs(A.keys, A.vals, kalt, valt, P, 32, sort_scr, st);
+    launch_tile_ranges(A.keys, P, F.depth_bits, ranges, F.n_tiles, st);
+    tm.end(ST_SORT, ev, st);
+
+    RasterArgs R;
+    std::memset(&R, 0, sizeof(R));
+    R.fc = F.fc;
+    R.K = params->K;
+    R.rec = A.rec;
+    R.rgb = A.rgb;
+    R.keys = A.keys;
+    R.vals = A.vals;
+    R.ranges = ranges;
+    R.dq = dq;
+    R.counters = ctx->counters;
+    R.status = reinterpret_cast<int*>(ctx->counters + 4);
+    R.out_rgb = out->rgb;
+    R.out_T = out->T_final;
+    R.out_n = out->n_emitted;
+    R.p = *params;
+    ev = tm.begin(st);
+    launch_raster(R, F.kmax, opt->kbuf_capacity, false, st);
+    tm.end(ST_RASTER, ev, st);
+    if ((s = check_launch()) != DRK_OK) return s;
+
+    ctx->last = drk_stats_t{};
+    ctx->last.n_pairs = P;
+    ctx->last.n_tiles = F.n_tiles;
+    ctx->last.key_bits_depth = F.depth_bits;
+
+    if (state) {
+        drk_state* S = new (std::nothrow) drk_state();
+        if (!S) return fail(DRK_ERR_OOM, "host allocation failed");
+        S->ctx = ctx;
+        S->stream = st;
+        S->n = n;
+        S->pairs = P;
+        S->K = params->K;
+        S->kmax = F.kmax;
+        S->cap = opt->kbuf_capacity;
+        S->sh_degree = params->sh_degree;
+        S->width = cam->width;
+        S->height = cam->height;
+        S->fc = F.fc;
+        S->rec = A.rec;
+        S->rgb = A.rgb;
+        S->keys = A.keys;
+        S->vals = A.vals;
+        S->ranges = ranges;
+        S->dq = dq;
+        const size_t npix = (size_t)cam->width * cam->height;
+        float* cf = nullptr;
+        if ((s = al.get(&cf, 3 * npix)) != DRK_OK) {
+            delete S;
+            return s;
+        }
+        DRK_CUDA(cudaMemcpyAsync(cf, out->rgb, 3 * npix * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        S->Cfin = cf;
+        S->allocs = al.ptrs;
+        al.keep = true;
+        *state = S;
+    }
+    return DRK_OK;
+}
+
+drk_status_t drk_render_backward(drk_ctx_t* ctx, const drk_params_t* params, const drk_camera_t* cam,
+                                 const drk_options_t* opt, const drk_state_t* state, const float* dL_drgb,
+                                 const drk_params_grad_t* grads, void* stream) {
+    if (!ctx || !state || !dL_drgb || !grads) return fail(DRK_ERR_INVALID_ARG, "null argument");
+    drk_status_t s = validate(params, cam, opt);
+    if (s != DRK_OK) return s;
+    if (params->n != state->n || params->K != state->K || cam->width != state->width || cam->height != state->height ||
+        params->sh_degree != state->sh_degree || opt->kbuf_capacity != state->cap)
+        return fail(DRK_ERR_INVALID_ARG, "backward arguments do not match the forward state");
+    const int64_t n = params->n;
+    if (n > 0 && (!grads->mu || !grads->quat || !grads->scale || !grads->theta || !grads->eta || !grads->tau ||
+                  !grads->opacity || !grads->color))
+        return fail(DRK_ERR_INVALID_ARG, "null gradient array");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    DRK_CUDA(cudaSetDevice(ctx->device));
+    ctx->last_stream = st;
+    const Frame F = make_frame(params, cam, opt);
+    const int K = params->K;
+    const int ncoef = params->sh_degree < 0 ? 1 : (params->sh_degree + 1) * (params->sh_degree + 1);
+    if (n == 0) return DRK_OK;
+    DRK_CUDA(cudaMemsetAsync(grads->mu, 0, (size_t)n * 3 * sizeof(float), st));
+    DRK_CUDA(cudaMemsetAsync(grads->quat, 0, (size_t)n * 4 * sizeof(float), st));
+    DRK_CUDA(cudaMemsetAsync(grads->scale, 0, (size_t)n * K * sizeof(float), st));
+    DRK_CUDA(cudaMemsetAsync(grads->theta, 0, (size_t)n * K * sizeof(float), st));
+    DRK_CUDA(cudaMemsetAsync(grads->eta, 0, (size_t)n * sizeof(float), st));
+    DRK_CUDA(cudaMemsetAsync(grads->tau, 0, (size_t)n * sizeof(float), st));
+    DRK_CUDA(cudaMemsetAsync(grads->opacity, 0, (size_t)n * sizeof(float), st));
+    DRK_CUDA(cudaMemsetAsync(grads->color, 0, (size_t)n * 3 * ncoef * sizeof(float), st));
+    Allocs al(ctx->pool, st);
+    float* gtmp = nullptr;
+    if ((s = al.get(&gtmp, (size_t)n * G_STRIDE)) != DRK_OK) return s;
+    DRK_CUDA(cudaMemsetAsync(gtmp, 0, (size_t)n * G_STRIDE * sizeof(float), st));
+
+    RasterArgs R;
+    std::memset(&R, 0, sizeof(R));
+    R.fc = F.fc;
+    R.K = K;
+    R.rec = state->rec;
+    R.rgb = state->rgb;
+    R.keys = state->keys;
+    R.vals = state->vals;
+    R.ranges = state->ranges;
+    R.dq = state->dq;
+    R.counters = nullptr;
+    R.p = *params;
+    R.dL = dL_drgb;
+    R.Cfin = state->Cfin;
+    R.gtmp = gtmp;
+    R.grads = *grads;
+    StageTimer& tm = ctx->timer;
+    cudaEvent_t ev = tm.begin(st);
+    launch_raster(R, F.kmax, state->cap, true, st);
+    tm.end(ST_RASTER_BWD, ev, st);
+
+    PreArgs A;
+    std::memset(&A, 0, sizeof(A));
+    A.p = *params;
+    A.cam = F.cam;
+    for (int c = 0; c < 3; c++) A.cam_center[c] = F.center[c];
+    A.fc = F.fc;
+    A.sl = opt->lowpass_sl;
+    ev = tm.begin(st);
+    if (F.kmax == 8) launch_preprocess_backward<8>(A, gtmp, *grads, st);
+    else launch_preprocess_backward<16>(A, gtmp, *grads, st);
+    tm.end(ST_PREPROCESS_BWD, ev, st);
+    return check_launch();
+}
+
+drk_status_t drk_timing_enable(drk_ctx_t* ctx, int enable) {
+    if (!ctx) return fail(DRK_ERR_INVALID_ARG, "null context");
+    DRK_CUDA(cudaSetDevice(ctx->device));
+    ctx->timer.collect();
+    for (int i = 0; i < ST_COUNT; i++) {
+        ctx->timer.ms[i] = 0.0;
+        ctx->timer.cnt[i] = 0;
+    }
+    ctx->timer.on = enable != 0;
+    return DRK_OK;
+}
+
+drk_status_t drk_timing_read(drk_ctx_t* ctx, double* ms, int64_t* launches) {
+    if (!ctx || !ms || !launches) return fail(DRK_ERR_INVALID_ARG, "null argument");
+    DRK_CUDA(cudaSetDevice(ctx->device));
+    ctx->timer.collect();
+    for (int i = 0; i < ST_COUNT; i++) {
+        ms[i] = ctx->timer.ms[i];
+        launches[i] = ctx->timer.cnt[i];
+    }
+    return DRK_OK;
+}
+
+int64_t drk_launch_count(void) { return g_launches.load(); }
+
+void drk_state_free(drk_state_t* S) {
+    if (!S) return;
+    cudaSetDevice(S->ctx->device);
+    for (void* q : S->allocs) cudaFreeAsync(q, S->stream);
+    delete S;
+}
+
+drk_status_t drk_sort_pairs(drk_ctx_t* ctx, uint32_t* keys, uint32_t* vals, int64_t n, int key_bits, void* stream) {
+    if (!ctx) return fail(DRK_ERR_INVALID_ARG, "null context");
+    if (n < 0 || n >= (int64_t(1) << 32)) return fail(DRK_ERR_INVALID_ARG, "n = %lld out of range", (long long)n);
+    if (key_bits < 1 || key_bits > 32) return fail(DRK_ERR_INVALID_ARG, "key_bits = %d not in [1, 32]", key_bits);
+    if (n > 0 && (!keys || !vals)) return fail(DRK_ERR_INVALID_ARG, "null keys or values");
+    if (n <= 1) return DRK_OK;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    DRK_CUDA(cudaSetDevice(ctx->device));
+    Allocs al(ctx->pool, st);
+    drk_status_t s;
+    uint32_t *kalt = nullptr, *valt = nullptr;
+    uint8_t* scr = nullptr;
+    if ((s = al.get(&kalt, (size_t)n)) != DRK_OK) return s;
+    if ((s = al.get(&valt, (size_t)n)) != DRK_OK) return s;
+    if ((s = al.get(&scr, radix_sort_scratch_bytes(n))) != DRK_OK) return s;
+    radix_sort_pairs(keys, vals, kalt, valt, n, key_bits, scr, st);
+    return check_launch();
+}
+
+drk_status_t drk_get_stats(drk_ctx_t* ctx, drk_stats_t* out) {
+    if (!ctx || !out) return fail(DRK_ERR_INVALID_ARG, "null argument");
+    DRK_CUDA(cudaSetDevice(ctx->device));
+    unsigned long long c[8];
+    DRK_CUDA(cudaMemcpyAsync(c, ctx->counters, sizeof(c), cudaMemcpyDeviceToHost, ctx->last_stream));
+    DRK_CUDA(cudaStreamSynchronize(ctx->last_stream));
+    *out = ctx->last;
+    out->n_evals = (int64_t)c[0];
+    out->n_emitted = (int64_t)c[1];
+    out->n_extra_passes = (int64_t)c[2];
+    out->n_visible = (int64_t)c[3];
+    const int bits = (int)(c[4] & 0xffffffffu);
+    out->status = DRK_OK;
+    for (int b = 1; b < 8; b++)
+        if (bits & (1 << b)) { out->status = b; break; }
+    return DRK_OK;
+}
+
+}  // extern "C"

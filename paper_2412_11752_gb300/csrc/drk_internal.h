@@ -1,0 +1,85 @@
+// drk_internal.h -- host/device interfaces between the translation units of
+// libdrk.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/drk.h"
+#include "drk_common.cuh"
+
+namespace drk {
+
+struct CamDev {
+    float fx, fy, cx, cy;
+    float w2c[12];
+};
+
+// arguments of the per-primitive kernels (preprocess, culling, emission,
+// preprocess backward)
+struct PreArgs {
+    drk_params_t p;
+    CamDev cam;
+    float cam_center[3];
+    FrameConst fc;
+    float sl;               // low-pass filter radius s_l (pixels), 0 = off
+    int cull_level;
+    int depth_bits;
+    float* rec;             // n x Rec<KMAX>::STRIDE
+    float* bnd;             // n x Bnd<KMAX>::STRIDE
+    float* rgb;             // n x 3 view-dependent colour
+    uint32_t* count;        // n pairs per primitive
+    uint64_t* offsets;      // n + 1 exclusive scan of count
+    int* zmax_bits;         // max ray depth of any bound (float bits)
+    DepthQuant* dq;         // device
+    uint32_t* keys;         // pair keys
+    uint32_t* vals;         // pair values (primitive index)
+    unsigned long long* counters;  // [3]: primitives with at least one pair
+    int* status;                   // device status bits (1 << drk_status_t)
+};
+
+// arguments of the raster kernels
+struct RasterArgs {
+    FrameConst fc;
+    int K;
+    const float* rec;
+    const float* rgb;
+    const uint32_t* keys;
+    const uint32_t* vals;
+    const uint2* ranges;
+    const DepthQuant* dq;
+    unsigned long long* counters;   // evals, emitted, extra passes (may be null)
+    int* status;                     // device status bits (may be null)
+    // forward outputs
+    float* out_rgb;
+    float* out_T;
+    int32_t* out_n;
+    // backward
+    drk_params_t p;
+    const float* dL;
+    const float* Cfin;
+    float* gtmp;                     // n x G_STRIDE
+    drk_params_grad_t grads;
+};
+
+// host-side count of kernel launches made by the library (all threads)
+void note_launch();
+
+template <int KMAX> void launch_preprocess(const PreArgs& A, cudaStream_t st);
+template <int KMAX> void launch_count(const PreArgs& A, cudaStream_t st);
+template <int KMAX> void launch_emit(const PreArgs& A, cudaStream_t st);
+template <int KMAX>
+void launch_preprocess_backward(const PreArgs& A, const float* gtmp, const drk_params_grad_t& g, cudaStream_t st);
+void launch_depth_quant(const PreArgs& A, cudaStream_t st);
+
+size_t scan_scratch_bytes(int64_t n);
+void exclusive_scan_u32_u64(const uint32_t* in, uint64_t* out, int64_t n, void* scratch, cudaStream_t st);
+size_t radix_sort_scratch_bytes(int64_t n);
+void radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, int64_t n, int bits,
+                      void* scratch, cudaStream_t st);
+void launch_tile_ranges(const uint32_t* keys, int64_t n, int depth_bits, uint2* ranges, int n_tiles,
+                        cudaStream_t st);
+void launch_raster(const RasterArgs& A, int kmax, int cap, bool bwd, cudaStream_t st);
+
+}  // namespace drk

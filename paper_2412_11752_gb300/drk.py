@@ -1,0 +1,337 @@
+"""ctypes binding of libdrk (include/drk.h).
+
+Argument marshalling only: every step of the rendering path runs in the
+library's CUDA kernels.  Torch tensors provide device memory and streams.
+If the library is not built, every entry point raises; there is no
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field, fields
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+DRK_OK = 0
+STATUS = {0: "DRK_OK", 1: "DRK_ERR_INVALID_ARG", 2: "DRK_ERR_OOM", 3: "DRK_ERR_CUDA", 4: "DRK_ERR_CAPACITY",
+          5: "DRK_ERR_TIMEOUT", 6: "DRK_ERR_BUSY", 7: "DRK_ERR_NOT_FOUND"}
+CULL_NONE, CULL_RECT, CULL_TILE = 0, 1, 2
+PARAM_NAMES = ("mu", "quat", "scale", "theta", "eta", "tau", "opacity", "color")
+
+
+class DrkError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_fp = C.POINTER(C.c_float)
+
+
+class drk_params_t(C.Structure):
+    _fields_ = [("n", C.c_int64), ("K", C.c_int32), ("sh_degree", C.c_int32)] + [(k, _fp) for k in PARAM_NAMES]
+
+
+class drk_params_grad_t(C.Structure):
+    _fields_ = [(k, _fp) for k in PARAM_NAMES]
+
+
+class drk_camera_t(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("world_to_cam", C.c_float * 12)]
+
+
+class drk_options_t(C.Structure):
+    _fields_ = [("alpha_min", C.c_float), ("T_min", C.c_float), ("alpha_max", C.c_float),
+                ("lowpass_sl", C.c_float), ("near_plane", C.c_float), ("bg", C.c_float * 3),
+                ("cull_level", C.c_int32), ("kbuf_capacity", C.c_int32), ("reserved", C.c_int32 * 6)]
+
+
+class drk_image_t(C.Structure):
+    _fields_ = [("rgb", _fp), ("T_final", _fp), ("n_emitted", C.POINTER(C.c_int32))]
+
+
+class drk_stats_t(C.Structure):
+    _fields_ = [("n_visible", C.c_int64), ("n_pairs", C.c_int64), ("n_evals", C.c_int64), ("n_emitted", C.c_int64),
+                ("n_extra_passes", C.c_int64), ("n_tiles", C.c_int64), ("key_bits_depth", C.c_int32),
+                ("status", C.c_int32)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libdrk.so (built in-tree by build()).  Raises if it is missing."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libdrk is not built ({path} missing); call __graft_entry__.build()")
+        L = C.CDLL(path)
+        vp = C.c_void_p
+        L.drk_options_default.argtypes = [C.POINTER(drk_options_t)]
+        L.drk_options_default.restype = None
+        L.drk_last_error.restype = C.c_char_p
+        L.drk_version.restype = C.c_char_p
+        L.drk_ctx_create.argtypes = [C.c_int, C.POINTER(vp)]
+        L.drk_ctx_destroy.argtypes = [vp]
+        L.drk_ctx_destroy.restype = None
+        L.drk_render.argtypes = [vp, C.POINTER(drk_params_t), C.POINTER(drk_camera_t), C.POINTER(drk_options_t),
+                                 C.POINTER(drk_image_t), C.POINTER(vp), vp]
+        L.drk_render_backward.argtypes = [vp, C.POINTER(drk_params_t), C.POINTER(drk_camera_t),
+                                          C.POINTER(drk_options_t), vp, _fp, C.POINTER(drk_params_grad_t), vp]
+        L.drk_state_free.argtypes = [vp]
+        L.drk_state_free.restype = None
+        L.drk_get_stats.argtypes = [vp, C.POINTER(drk_stats_t)]
+        L.drk_sort_pairs.argtypes = [vp, vp, vp, C.c_int64, C.c_int, vp]
+        L.drk_timing_enable.argtypes = [vp, C.c_int]
+        L.drk_timing_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+        L.drk_launch_count.restype = C.c_int64
+        for f in ("drk_ctx_create", "drk_render", "drk_render_backward", "drk_get_stats", "drk_sort_pairs",
+                  "drk_timing_enable", "drk_timing_read"):
+            getattr(L, f).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(code: int):
+    if code != DRK_OK:
+        raise DrkError(code, lib().drk_last_error().decode())
+
+
+# ---------------------------------------------------------------------------
+@dataclass
+class Options:
+    alpha_min: float = float(np.float32(np.exp(-9.0)))
+    T_min: float = 1e-4
+    alpha_max: float = 0.99
+    lowpass_sl: float = 0.70710678
+    near_plane: float = 0.2
+    bg: tuple = (0.0, 0.0, 0.0)
+    cull_level: int = CULL_TILE
+    kbuf_capacity: int = 16
+
+    def to_c(self) -> drk_options_t:
+        o = drk_options_t()
+        o.alpha_min, o.T_min, o.alpha_max = self.alpha_min, self.T_min, self.alpha_max
+        o.lowpass_sl, o.near_plane = self.lowpass_sl, self.near_plane
+        for i in range(3):
+            o.bg[i] = float(self.bg[i])
+        o.cull_level, o.kbuf_capacity = int(self.cull_level), int(self.kbuf_capacity)
+        return o
+
+
+def default_options() -> drk_options_t:
+    o = drk_options_t()
+    lib().drk_options_default(C.byref(o))
+    return o
+
+
+def camera_c(cam) -> drk_camera_t:
+    c = drk_camera_t()
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    w = np.asarray(cam.world_to_cam, np.float32).reshape(12)
+    for i in range(12):
+        c.world_to_cam[i] = float(w[i])
+    return c
+
+
+def _fptr(t: torch.Tensor | None):
+    if t is None:
+        return None
+    assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+    return C.cast(C.c_void_p(t.data_ptr()), _fp)
+
+
+def _stream_ptr(stream) -> C.c_void_p:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+class Context:
+    """drk_ctx_t: device scratch pool and counters of the last render."""
+
+    def __init__(self, device: int = 0):
+        h = C.c_void_p()
+        _check(lib().drk_ctx_create(int(device), C.byref(h)))
+        self.handle = h
+        self.device = int(device)
+
+    def close(self):
+        if self.handle:
+            lib().drk_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def stats(self) -> dict:
+        s = drk_stats_t()
+        _check(lib().drk_get_stats(self.handle, C.byref(s)))
+        return {f: getattr(s, f) for f, _ in drk_stats_t._fields_}
+
+    def timing_enable(self, on: bool = True) -> None:
+        _check(lib().drk_timing_enable(self.handle, 1 if on else 0))
+
+    def timing_read(self) -> dict:
+        ms = (C.c_double * 8)()
+        cnt = (C.c_int64 * 8)()
+        _check(lib().drk_timing_read(self.handle, ms, cnt))
+        return {name: (ms[i], cnt[i]) for i, name in enumerate(STAGES)}
+
+
+STAGES = ("preprocess", "emit", "sort", "raster", "raster_bwd", "preprocess_bwd", "unused6", "unused7")
+
+
+def launch_count() -> int:
+    return int(lib().drk_launch_count())
+
+
+_default_ctx = {}
+
+
+def default_context(device: int = 0) -> Context:
+    if device not in _default_ctx:
+        _default_ctx[device] = Context(device)
+    return _default_ctx[device]
+
+
+@dataclass
+class DeviceScene:
+    """Activated DRK parameters as contiguous float32 CUDA tensors."""
+    mu: torch.Tensor
+    quat: torch.Tensor
+    scale: torch.Tensor
+    theta: torch.Tensor
+    eta: torch.Tensor
+    tau: torch.Tensor
+    opacity: torch.Tensor
+    color: torch.Tensor
+    sh_degree: int = -1
+
+    @property
+    def n(self) -> int:
+        return int(self.mu.shape[0])
+
+    @property
+    def K(self) -> int:
+        return int(self.scale.shape[1])
+
+    @staticmethod
+    def from_scene(scene, device="cuda") -> "DeviceScene":
+        t = {k: torch.as_tensor(np.ascontiguousarray(getattr(scene, k), np.float32)).to(device).contiguous()
+             for k in PARAM_NAMES}
+        return DeviceScene(**t, sh_degree=int(scene.sh_degree))
+
+    def tensors(self) -> dict:
+        return {k: getattr(self, k) for k in PARAM_NAMES}
+
+    def to_c(self) -> drk_params_t:
+        p = drk_params_t()
+        p.n, p.K, p.sh_degree = self.n, self.K, int(self.sh_degree)
+        for k in PARAM_NAMES:
+            setattr(p, k, _fptr(getattr(self, k)))
+        return p
+
+
+class State:
+    """drk_state_t of one forward render (needed by the backward)."""
+
+    def __init__(self, handle, ctx: Context):
+        self.handle = handle
+        self.ctx = ctx   # the context's pool owns the state's memory
+
+    def free(self):
+        if self.handle:
+            lib().drk_state_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def drk_render(scene: DeviceScene, cam, opt: Options | None = None, ctx: Context | None = None,
+               need_state: bool = False, stream=None, out: dict | None = None):
+    """Forward render.  Returns (rgb (3, H, W), T_final (H, W), n_emitted (H, W), state|None)."""
+    opt = opt or Options()
+    ctx = ctx or default_context(scene.mu.device.index or 0)
+    H, W = int(cam.height), int(cam.width)
+    dev = scene.mu.device
+    if out is None:
+        out = dict(rgb=torch.empty((3, H, W), device=dev), T=torch.empty((H, W), device=dev),
+                   n=torch.empty((H, W), device=dev, dtype=torch.int32))
+    img = drk_image_t()
+    img.rgb = _fptr(out["rgb"])
+    img.T_final = _fptr(out.get("T"))
+    img.n_emitted = C.cast(C.c_void_p(out["n"].data_ptr()), C.POINTER(C.c_int32)) if out.get("n") is not None else None
+    p, cc, oc = scene.to_c(), camera_c(cam), opt.to_c()
+    h = C.c_void_p()
+    _check(lib().drk_render(ctx.handle, C.byref(p), C.byref(cc), C.byref(oc), C.byref(img),
+                            C.byref(h) if need_state else None, _stream_ptr(stream)))
+    st = State(h, ctx) if need_state else None
+    return out["rgb"], out.get("T"), out.get("n"), st
+
+
+def drk_render_backward(scene: DeviceScene, cam, opt: Options | None, state: State, dL_drgb: torch.Tensor,
+                        ctx: Context | None = None, stream=None) -> dict:
+    """Reverse mode: gradients of sum(dL_drgb * rgb) for every parameter array."""
+    opt = opt or Options()
+    ctx = ctx or state.ctx
+    grads = {k: torch.empty_like(getattr(scene, k)) for k in PARAM_NAMES}
+    g = drk_params_grad_t()
+    for k in PARAM_NAMES:
+        setattr(g, k, _fptr(grads[k]))
+    p, cc, oc = scene.to_c(), camera_c(cam), opt.to_c()
+    dL = dL_drgb.contiguous().float()
+    _check(lib().drk_render_backward(ctx.handle, C.byref(p), C.byref(cc), C.byref(oc), state.handle, _fptr(dL),
+                                     C.byref(g), _stream_ptr(stream)))
+    return grads
+
+
+def drk_sort_pairs(keys: torch.Tensor, vals: torch.Tensor, key_bits: int = 32, ctx: Context | None = None,
+                   stream=None) -> None:
+    """In-place stable sort of uint32 (stored as int32) keys with their values."""
+    assert keys.is_cuda and keys.dtype == torch.int32 and vals.dtype == torch.int32
+    assert keys.is_contiguous() and vals.is_contiguous() and keys.numel() == vals.numel()
+    ctx = ctx or default_context(keys.device.index or 0)
+    _check(lib().drk_sort_pairs(ctx.handle, C.c_void_p(keys.data_ptr()), C.c_void_p(vals.data_ptr()),
+                                keys.numel(), int(key_bits), _stream_ptr(stream)))
+
+
+class DRKRender(torch.autograd.Function):
+    """Differentiable render: (mu, quat, scale, theta, eta, tau, opacity, color) -> rgb (3, H, W).
+
+    Gradients are with respect to the activated parameters."""
+
+    @staticmethod
+    def forward(fctx, cam, opt, sh_degree, mu, quat, scale, theta, eta, tau, opacity, color):
+        scene = DeviceScene(*(t.detach().contiguous() for t in (mu, quat, scale, theta, eta, tau, opacity, color)),
+                            sh_degree=sh_degree)
+        rgb, _, _, st = drk_render(scene, cam, opt, need_state=True)
+        fctx.scene, fctx.cam, fctx.opt, fctx.state = scene, cam, opt, st
+        return rgb
+
+    @staticmethod
+    def backward(fctx, dL):
+        g = drk_render_backward(fctx.scene, fctx.cam, fctx.opt, fctx.state, dL)
+        fctx.state.free()
+        return (None, None, None) + tuple(g[k] for k in PARAM_NAMES)
+
+
+def render_autograd(params: dict, cam, opt: Options | None = None, sh_degree: int = -1) -> torch.Tensor:
+    return DRKRender.apply(cam, opt or Options(), sh_degree, *(params[k] for k in PARAM_NAMES))

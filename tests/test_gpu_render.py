@@ -1,0 +1,177 @@
+"""GPU forward parity: the CUDA path through the C ABI against the FP64 oracle."""
+import math
+
+import numpy as np
+import pytest
+
+from helpers import TOL_IMAGE, image_error, oracle_options
+from oracle import drk_oracle as O
+from paper_2412_11752_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def drk():
+    from paper_2412_11752_gb300 import drk as D
+    D.lib()
+    return D
+
+
+def render_gpu(drk, scene, cam, opt, **kw):
+    ds = drk.DeviceScene.from_scene(scene, "cuda")
+    rgb, T, n, st = drk.drk_render(ds, cam, opt, **kw)
+    torch.cuda.synchronize()
+    return rgb.cpu().numpy(), T.cpu().numpy(), n.cpu().numpy(), st
+
+
+def check_full(drk, scene, cam, opt, max_excluded_frac=1e-3):
+    rgb, T, n, _ = render_gpu(drk, scene, cam, opt)
+    ref = O.render(scene, cam, oracle_options(opt))
+    err, nex = image_error(rgb, ref["rgb"], ref["flags"])
+    assert err <= TOL_IMAGE, f"max abs error {err:.3e} ({nex} pixels excluded)"
+    assert nex <= max(2, max_excluded_frac * cam.npix), f"{nex} pixels excluded"
+    keep = (ref["flags"] & (O.FLAG_T_MIN | O.FLAG_DEPTH_TIE)) == 0
+    assert np.abs(T - ref["T"])[keep].max() <= TOL_IMAGE
+    return rgb, ref
+
+
+def test_plain_2k_128_full_image(drk):
+    scene = synth.scene_plain(2000, 8, seed=1000)
+    cam = synth.camera_front(128, 128)
+    opt = drk.Options()
+    rgb, ref = check_full(drk, scene, cam, opt)
+    assert rgb.max() > 0.1          # the image is not empty
+
+
+def test_cull_levels_bitwise_identical(drk):
+    scene = synth.scene_plain(2000, 8, seed=1000)
+    cam = synth.camera_front(128, 128)
+    outs = []
+    for lvl in (drk.CULL_NONE, drk.CULL_RECT, drk.CULL_TILE):
+        rgb, T, n, _ = render_gpu(drk, scene, cam, drk.Options(cull_level=lvl))
+        outs.append((rgb, T, n, drk.default_context().stats()))
+    for rgb, T, n, _ in outs[1:]:
+        assert np.array_equal(rgb, outs[0][0]) and np.array_equal(T, outs[0][1]) and np.array_equal(n, outs[0][2])
+    pairs = [s["n_pairs"] for *_, s in outs]
+    assert pairs[0] > pairs[1] > pairs[2] > 0, pairs
+
+
+def test_buffer_capacity_does_not_change_the_image(drk):
+    # the depth-order buffer is exact for any capacity: a small one takes
+    # extra passes over the list, never a different order
+    scene = synth.scene_clustered(4000, 8, seed=2100, n_clusters=8)
+    cam = synth.camera_front(96, 64)
+    r8, T8, n8, _ = render_gpu(drk, scene, cam, drk.Options(kbuf_capacity=8))
+    s8 = drk.default_context().stats()
+    r16, T16, n16, _ = render_gpu(drk, scene, cam, drk.Options(kbuf_capacity=16))
+    assert np.array_equal(r8, r16) and np.array_equal(T8, T16) and np.array_equal(n8, n16)
+    assert s8["n_extra_passes"] > 0
+
+
+def test_gaussian_special_case_k4(drk):
+    # K = 4 right angles, eta = 0, tau = 0: planar anisotropic Gaussians (Eq. 3)
+    sc = synth.scene_plain(400, 4, seed=41)
+    sc.theta[:] = np.float32([0, math.pi / 2, math.pi, 3 * math.pi / 2])
+    sc.scale[:, 2] = sc.scale[:, 0]
+    sc.scale[:, 3] = sc.scale[:, 1]
+    sc.eta[:] = 0
+    sc.tau[:] = 0
+    check_full(drk, sc, synth.camera_front(64, 64), drk.Options())
+
+
+@pytest.mark.parametrize("K", [3, 5, 12, 16])
+def test_other_basis_counts(drk, K):
+    scene = synth.scene_plain(600, K, seed=50 + K)
+    check_full(drk, scene, synth.camera_front(80, 72), drk.Options())
+
+
+@pytest.mark.parametrize("wh", [(37, 23), (100, 61), (1, 1), (17, 16)])
+def test_ragged_image_sizes(drk, wh):
+    scene = synth.scene_plain(500, 8, seed=60)
+    check_full(drk, scene, synth.camera_front(*wh), drk.Options())
+
+
+def test_sh_colour_and_background(drk):
+    scene = synth.scene_clustered(3000, 8, seed=70, n_clusters=6)
+    cam = synth.camera_lookat(96, 64, eye=(1.9, 0.3, -0.8), target=(0.5, 0.5, 0.5))
+    check_full(drk, scene, cam, drk.Options(bg=(0.2, 0.5, 0.1)))
+
+
+def test_filter_off_and_sharp_edges(drk):
+    scene = synth.scene_slab(3000, 16, seed=80)
+    check_full(drk, scene, synth.camera_front(64, 64), drk.Options(lowpass_sl=0.0))
+
+
+def test_empty_scene(drk):
+    scene = synth.scene_plain(0, 8, seed=1)
+    rgb, T, n, _ = render_gpu(drk, scene, synth.camera_front(40, 30), drk.Options(bg=(0.25, 0.5, 1.0)))
+    assert np.all(rgb[0] == np.float32(0.25)) and np.all(rgb[2] == 1.0)
+    assert np.all(T == 1.0) and np.all(n == 0)
+
+
+def test_deterministic(drk):
+    scene = synth.scene_plain(2000, 8, seed=1000)
+    cam = synth.camera_front(128, 128)
+    a = render_gpu(drk, scene, cam, drk.Options())[0]
+    b = render_gpu(drk, scene, cam, drk.Options())[0]
+    assert np.array_equal(a, b)
+
+
+def test_invalid_arguments_rejected_on_host(drk):
+    scene = synth.scene_plain(10, 8, seed=1)
+    ds = drk.DeviceScene.from_scene(scene, "cuda")
+    cam = synth.camera_front(16, 16)
+    with pytest.raises(drk.DrkError) as e:
+        drk.drk_render(ds, cam, drk.Options(kbuf_capacity=12))
+    assert e.value.code == 1
+    with pytest.raises(drk.DrkError):
+        drk.drk_render(ds, cam, drk.Options(alpha_max=1.0))
+    t = ds.tensors()
+    t["scale"] = t["scale"][:, :2].contiguous()
+    t["theta"] = t["theta"][:, :2].contiguous()
+    with pytest.raises(drk.DrkError):                      # K = 2 < 3
+        drk.drk_render(drk.DeviceScene(**t, sh_degree=-1), cam, drk.Options())
+
+
+@pytest.mark.parametrize("n,bits", [(0, 32), (1, 32), (2, 8), (10007, 32), (1 << 20, 32), (300000, 20), (4096, 13)])
+def test_sort_pairs_matches_stable_sort(drk, n, bits):
+    rng = np.random.default_rng(n + bits)
+    keys = rng.integers(0, 2 ** bits, size=n, dtype=np.uint64).astype(np.uint32)
+    if n > 100:
+        keys[: n // 3] = keys[0]          # many equal keys: stability matters
+    vals = np.arange(n, dtype=np.uint32)
+    k_t = torch.from_numpy(keys.view(np.int32).copy()).cuda()
+    v_t = torch.from_numpy(vals.view(np.int32).copy()).cuda()
+    drk.drk_sort_pairs(k_t, v_t, bits)
+    torch.cuda.synchronize()
+    order = np.argsort(keys, kind="stable")
+    assert np.array_equal(k_t.cpu().numpy().view(np.uint32), keys[order])
+    assert np.array_equal(v_t.cpu().numpy().view(np.uint32), vals[order])
+
+
+def test_clustered_100k_1080p_sampled_pixels(drk):
+    # full-size workload, checked on seeded pixels plus whole tiles (corner,
+    # centre, the tile with most projected centres, a ragged bottom tile)
+    scene = synth.scene_clustered(100_000, 8, seed=2000)
+    cam = synth.camera_front(1920, 1080)
+    opt = drk.Options()
+    rgb, T, n, _ = render_gpu(drk, scene, cam, opt)
+    # densest tile by projected centres (plain projection, test side)
+    M = cam.world_to_cam.astype(np.float64)
+    pc = scene.mu.astype(np.float64) @ M[:, :3].T + M[:, 3]
+    px = cam.fx * pc[:, 0] / pc[:, 2] + cam.cx
+    py = cam.fy * pc[:, 1] / pc[:, 2] + cam.cy
+    ok = (px >= 0) & (px < cam.width) & (py >= 0) & (py < cam.height)
+    tid = (py[ok] // 16).astype(int) * 120 + (px[ok] // 16).astype(int)
+    dense = int(np.bincount(tid).argmax())
+    tiles = [(0, 0), (60, 33), (dense % 120, dense // 120), (37, 67)]
+    pix = synth.pixel_sample(cam.width, cam.height, 2048, seed=2001, tiles=tiles)
+    ref = O.render_pixels(scene, cam, oracle_options(opt), pix)
+    g = rgb[:, pix[:, 1], pix[:, 0]]
+    err, nex = image_error(g, ref["rgb"].T, ref["flags"])
+    assert err <= TOL_IMAGE, f"max abs error {err:.3e}, {nex} excluded"
+    assert nex <= 3
+    stats = drk.default_context().stats()
+    assert stats["n_pairs"] > 0 and stats["n_evals"] > 0
