@@ -305,7 +305,8 @@ def run_drk(args):
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks,
                 "stages_ms": {k: v[0] / max(1, v[1]) for k, v in stage.items() if v[1]},
-                "counters": {k: stats[k] for k in ("n_pairs", "n_evals", "n_emitted", "n_extra_passes", "n_visible")}}
+                "counters": {k: stats[k] for k in ("n_pairs", "n_evals", "n_contrib_evals", "n_emitted",
+                                                   "n_extra_passes", "n_visible")}}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

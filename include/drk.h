@@ -116,7 +116,9 @@ typedef struct {
     float near_plane;     /* default 0.2 */
     float bg[3];          /* background colour */
     int32_t cull_level;   /* DRK_CULL_*; default DRK_CULL_TILE */
-    int32_t kbuf_capacity;/* per-pixel depth-order buffer entries: 8 or 16 */
+    int32_t kbuf_capacity;/* per-pixel depth-order buffer entries: 8, 16 or 32
+                             (any value gives the same image; a small buffer
+                             takes extra passes over the tile's list) */
     int32_t reserved[6];  /* must be zero */
 } drk_options_t;
 
@@ -139,6 +141,7 @@ typedef struct {
     int64_t n_extra_passes;/* extra list passes taken by pixels whose depth
                              buffer filled (exactness is kept) */
     int64_t n_tiles;
+    int64_t n_contrib_evals;/* evaluations with alpha_tilde >= alpha_min */
     int32_t key_bits_depth;
     int32_t status;       /* device-side drk_status_t of the last render */
 } drk_stats_t;

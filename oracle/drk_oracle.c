@@ -87,6 +87,8 @@ typedef struct {
 #define ORD_FLAG_ALPHA_MIN 1   /* some alpha_tilde within 1e-4 (rel) of alpha_min (informational) */
 #define ORD_FLAG_T_MIN     2   /* a stop decision within FP32 margin and with visible effect */
 #define ORD_FLAG_DEPTH_TIE 4   /* two contributors with near-equal depth and visible order effect */
+#define ORD_FLAG_STEEP     8   /* float32 error of the alphas could exceed half the tolerance
+                                  (near-hard edges: Psi's middle slope (1+tau)/(1-tau)) */
 
 /* ------------------------------------------------------------------------ */
 /* Sharpening, Eq. 9, and its inverse (used by tests and by the culling
@@ -438,7 +440,26 @@ void ord_color(const ord_params *P, int64_t i, const ord_camera *cam, double *rg
 /* ------------------------------------------------------------------------ */
 /* Per-pixel contributor list, sorted by (r_t, index) -- Eq. 13, reading R6 */
 
-typedef struct { double t; int64_t idx; double alpha; } contrib;
+typedef struct { double t; int64_t idx; double alpha, dalpha; } contrib;
+
+/* Rounding-error model of a float32 evaluation of alpha_tilde.  It decides
+ * nothing in the rendered image; it only marks pixels whose result float32
+ * arithmetic cannot pin down to the parity tolerance.  The exponent E of
+ * Eq. 8 (or the filter exponent of Eq. 10) carries an absolute error of at
+ * most about 4e-6 (1 + E) in float32 (relative 2e-6 from the projected
+ * coordinates, plus the rounding of the exponent itself); it moves alpha by
+ * o Psi'(g) g dE / 2.  A clamped alpha has no error.                       */
+static double alpha_fp32_error(const pair_eval *pe, double tau, double o)
+{
+    if (pe->clamped) return 0.0;
+    if (pe->use_filter) {
+        double Xf = -log(pe->filt / o);
+        return pe->filt * 0.5 * 4e-6 * (1.0 + 2.0 * Xf);
+    }
+    double dpsi, dtau;
+    psi_grad(pe->ke.g, tau, &dpsi, &dtau);
+    return o * dpsi * pe->ke.g * 0.5 * 4e-6 * (1.0 + pe->ke.E);
+}
 
 static int contrib_cmp(const void *pa, const void *pb)
 {
@@ -462,6 +483,7 @@ static int64_t gather_contributors(const ord_params *P, const ord_camera *cam, c
             buf[cnt].t = pe.t;
             buf[cnt].idx = i;
             buf[cnt].alpha = pe.alpha_tilde;
+            buf[cnt].dalpha = alpha_fp32_error(&pe, P->tau[i], P->opacity[i]);
             cnt++;
         }
     }
@@ -516,27 +538,36 @@ int ord_render(const ord_params *P, const ord_camera *cam, const ord_options *op
             int64_t nc = composite_count(buf, cnt, opt->T_min);
             double C[3] = {0, 0, 0}, T = 1.0;
             int flag = near_amin ? ORD_FLAG_ALPHA_MIN : 0;
+            double cmax = 1.0;
+            for (int c = 0; c < 3; c++) cmax = fmax(cmax, fabs(opt->bg[c]));
+            double dT_rel = 0.0;     /* float32 error estimate of T (relative) */
+            double budget = 0.0;     /* float32 error estimate of the colour */
             for (int64_t j = 0; j <= nc && j < cnt; j++) {
                 double cj[3];
                 int cl[3];
                 prim_color(P, buf[j].idx, ocam, cj, cl);
-                double a = buf[j].alpha;
-                /* stop decision within FP32 margin with an effect above 5e-5 */
+                double a = buf[j].alpha, da = buf[j].dalpha;
+                double cm = fmax(cmax, fmax(fabs(cj[0]), fmax(fabs(cj[1]), fabs(cj[2]))));
+                /* a stop decision within the float32 error of T (1 - alpha)
+                 * whose flip would move the colour by more than 5e-5 */
                 double rel = fabs(T * (1.0 - a) / opt->T_min - 1.0);
-                if (opt->T_min > 0.0 && rel < 2e-4 * (1.0 + a / (1.0 - a)) &&
-                    T * a * max_abs_diff3(cj, opt->bg) > 5e-5)
+                double margin = 3.0 * (dT_rel + da / (1.0 - a)) + 1e-6;
+                if (opt->T_min > 0.0 && rel < margin && T * a * max_abs_diff3(cj, opt->bg) > 5e-5)
                     flag |= ORD_FLAG_T_MIN;
                 if (j == nc) break;
                 /* near-equal depths whose swap is visible */
-                for (int64_t l = j + 1; l < cnt && buf[l].t - buf[j].t <= 1e-5 * buf[l].t; l++) {
+                for (int64_t l = j + 1; l < cnt && buf[l].t - buf[j].t <= 2e-6 * buf[l].t; l++) {
                     double cl_rgb[3];
                     int cl2[3];
                     prim_color(P, buf[l].idx, ocam, cl_rgb, cl2);
                     if (T * a * buf[l].alpha * max_abs_diff3(cj, cl_rgb) > 5e-5) flag |= ORD_FLAG_DEPTH_TIE;
                 }
+                budget += T * da * 2.0 * cm;
+                dT_rel += da / (1.0 - a) + 1e-7;
                 for (int c = 0; c < 3; c++) C[c] += T * a * cj[c];
                 T *= 1.0 - a;
             }
+            if (budget > 1e-4) flag |= ORD_FLAG_STEEP;
             for (int c = 0; c < 3; c++) rgb[3 * q + c] = C[c] + T * opt->bg[c];
             if (T_final) T_final[q] = T;
             if (n_contrib) n_contrib[q] = (int32_t)nc;

@@ -30,6 +30,7 @@ _lib = None
 FLAG_ALPHA_MIN = 1
 FLAG_T_MIN = 2
 FLAG_DEPTH_TIE = 4
+FLAG_STEEP = 8
 
 
 @dataclass

@@ -87,7 +87,8 @@ struct drk_ctx {
     unsigned long long* counters = nullptr;   // evals, emitted, extra passes, visible
     int* zmax_bits = nullptr;                 // counters[4] holds the device status bits
     DepthQuant* dq = nullptr;
-    uint64_t* h_total = nullptr;              // pinned
+    uint64_t* h_total = nullptr;              // pinned: pair total, largest recorded list
+    int* emit_max = nullptr;                  // largest per-pixel contributor count so far
     drk_stats_t last{};
 };
 
@@ -104,8 +105,18 @@ struct drk_state {
     uint2* ranges = nullptr;
     DepthQuant* dq = nullptr;
     float* Cfin = nullptr;
+    uint32_t* emit_pos = nullptr;
+    int32_t* emit_n = nullptr;
+    int32_t* tile_overflow = nullptr;
+    int emit_cap = 0;
     std::vector<void*> allocs;
 };
+
+// per-pixel capacity of the recorded contributor lists (entries beyond it
+// send the tile to the exact replay in the backward); it grows with the
+// largest list seen on the context
+constexpr int kEmitCap = 256;
+constexpr int kEmitCapMax = 4096;
 
 namespace {
 
@@ -175,8 +186,8 @@ drk_status_t validate(const drk_params_t* p, const drk_camera_t* cam, const drk_
     if (!(opt->lowpass_sl >= 0.f) || !std::isfinite(opt->lowpass_sl)) return fail(DRK_ERR_INVALID_ARG, "bad lowpass_sl");
     if (!finite_pos(opt->near_plane)) return fail(DRK_ERR_INVALID_ARG, "near_plane must be > 0");
     if (opt->cull_level < 0 || opt->cull_level > 2) return fail(DRK_ERR_INVALID_ARG, "cull_level not in 0..2");
-    if (opt->kbuf_capacity != 8 && opt->kbuf_capacity != 16)
-        return fail(DRK_ERR_INVALID_ARG, "kbuf_capacity must be 8 or 16");
+    if (opt->kbuf_capacity != 8 && opt->kbuf_capacity != 16 && opt->kbuf_capacity != 32)
+        return fail(DRK_ERR_INVALID_ARG, "kbuf_capacity must be 8, 16 or 32");
     for (int i = 0; i < 6; i++)
         if (opt->reserved[i] != 0) return fail(DRK_ERR_INVALID_ARG, "reserved option fields must be zero");
     for (int i = 0; i < 3; i++)
@@ -274,6 +285,7 @@ drk_status_t drk_ctx_create(int device, drk_ctx_t** out) {
     cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &thr);
     if (cudaMalloc(&c->counters, 8 * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc(&c->zmax_bits, sizeof(int)) != cudaSuccess || cudaMalloc(&c->dq, sizeof(DepthQuant)) != cudaSuccess ||
+        cudaMalloc(&c->emit_max, sizeof(int)) != cudaSuccess || cudaMemset(c->emit_max, 0, sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&c->h_total, 2 * sizeof(uint64_t)) != cudaSuccess) {
         cudaGetLastError();
         drk_ctx_destroy(c);
@@ -291,6 +303,7 @@ void drk_ctx_destroy(drk_ctx_t* c) {
     cudaFree(c->zmax_bits);
     cudaFree(c->dq);
     if (c->h_total) cudaFreeHost(c->h_total);
+    cudaFree(c->emit_max);
     c->timer.destroy();
     if (c->pool) cudaMemPoolDestroy(c->pool);
     delete c;
@@ -350,6 +363,10 @@ drk_status_t drk_render(drk_ctx_t* ctx, const drk_params_t* params, const drk_ca
     launch_depth_quant(A, st);
     tm.end(ST_PREPROCESS, ev, st);
     DRK_CUDA(cudaMemcpyAsync(ctx->h_total, A.offsets + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    if (state) {
+        ctx->h_total[1] = 0;
+        DRK_CUDA(cudaMemcpyAsync(ctx->h_total + 1, ctx->emit_max, sizeof(int), cudaMemcpyDeviceToHost, st));
+    }
     DRK_CUDA(cudaStreamSynchronize(st));
     const int64_t P = (int64_t)ctx->h_total[0];
     if (P >= (int64_t(1) << 32) - 1)
@@ -385,10 +402,25 @@ drk_status_t drk_render(drk_ctx_t* ctx, const drk_params_t* params, const drk_ca
     R.dq = dq;
     R.counters = ctx->counters;
     R.status = reinterpret_cast<int*>(ctx->counters + 4);
+    R.task_counter = reinterpret_cast<unsigned int*>(ctx->counters + 7);
     R.out_rgb = out->rgb;
     R.out_T = out->T_final;
     R.out_n = out->n_emitted;
     R.p = *params;
+    if (state) {
+        // the backward walks these per-pixel contributor lists
+        // capacity: the largest list seen so far on this context, with a
+        // quarter of headroom, as a power of two in [kEmitCap, kEmitCapMax]
+        const int64_t seen = (int64_t)(int)(ctx->h_total[1] & 0xffffffffu);
+        int cap = kEmitCap;
+        while (cap < kEmitCapMax && cap < seen + seen / 4 + 1) cap *= 2;
+        R.emit_cap = cap;
+        R.emit_max = ctx->emit_max;
+        if ((s = al.get(&R.emit_pos, (size_t)F.n_tiles * cap * kTilePix)) != DRK_OK) return s;
+        if ((s = al.get(&R.emit_n, (size_t)F.n_tiles * kTilePix)) != DRK_OK) return s;
+        if ((s = al.get(&R.tile_overflow, (size_t)F.n_tiles)) != DRK_OK) return s;
+        DRK_CUDA(cudaMemsetAsync(R.tile_overflow, 0, sizeof(int32_t) * (size_t)F.n_tiles, st));
+    }
     ev = tm.begin(st);
     launch_raster(R, F.kmax, opt->kbuf_capacity, false, st);
     tm.end(ST_RASTER, ev, st);
@@ -419,6 +451,10 @@ drk_status_t drk_render(drk_ctx_t* ctx, const drk_params_t* params, const drk_ca
         S->vals = A.vals;
         S->ranges = ranges;
         S->dq = dq;
+        S->emit_pos = R.emit_pos;
+        S->emit_n = R.emit_n;
+        S->tile_overflow = R.tile_overflow;
+        S->emit_cap = R.emit_cap;
         const size_t npix = (size_t)cam->width * cam->height;
         float* cf = nullptr;
         if ((s = al.get(&cf, 3 * npix)) != DRK_OK) {
@@ -478,14 +514,21 @@ drk_status_t drk_render_backward(drk_ctx_t* ctx, const drk_params_t* params, con
     R.ranges = state->ranges;
     R.dq = state->dq;
     R.counters = nullptr;
+    R.status = reinterpret_cast<int*>(ctx->counters + 4);
+    R.task_counter = reinterpret_cast<unsigned int*>(ctx->counters + 7);
     R.p = *params;
     R.dL = dL_drgb;
     R.Cfin = state->Cfin;
     R.gtmp = gtmp;
     R.grads = *grads;
+    R.emit_pos = state->emit_pos;
+    R.emit_n = state->emit_n;
+    R.tile_overflow = state->tile_overflow;
+    R.emit_cap = state->emit_cap;
     StageTimer& tm = ctx->timer;
     cudaEvent_t ev = tm.begin(st);
-    launch_raster(R, F.kmax, state->cap, true, st);
+    launch_raster_backward_list(R, F.kmax, st);          // tiles with complete lists
+    launch_raster(R, F.kmax, state->cap, true, st);      // exact replay of the others
     tm.end(ST_RASTER_BWD, ev, st);
 
     PreArgs A;
@@ -564,6 +607,7 @@ drk_status_t drk_get_stats(drk_ctx_t* ctx, drk_stats_t* out) {
     out->n_emitted = (int64_t)c[1];
     out->n_extra_passes = (int64_t)c[2];
     out->n_visible = (int64_t)c[3];
+    out->n_contrib_evals = (int64_t)c[5];
     const int bits = (int)(c[4] & 0xffffffffu);
     out->status = DRK_OK;
     for (int b = 1; b < 8; b++)

@@ -35,20 +35,24 @@ constexpr double csqrt(double x) { return csqrt_iter(x, x > 1.0 ? x : 1.0, 60); 
 //   0..8   homography rows U', V', W over integer pixel indices (x, y):
 //          w = W.(x, y, 1), t = 1/w is the ray depth r_t (Eq. 13),
 //          (u', v') = (U'.(x, y, 1), V'.(x, y, 1)) * t  (Eq. 4, Eq. 5)
-//   9      eta * log2(e) / 2         (Eq. 8, base-2 exponent)
-//   10     (1 - eta) * log2(e) / 2
-//   11     o
-//   12,13  Psi breakpoints (1 + tau)/4, (3 - tau)/4          (Eq. 9)
-//   14     o (1 - tau)/(1 + tau)      outer slope (x o)
-//   15     o (1 + tau)/(1 - tau)      middle slope (x o)
-//   16     -o tau/(1 - tau)           middle offset (x o)
-//   17     2 o tau/(1 + tau)          upper offset (x o)
-//   18,19  projected centre minus 0.5 (pixel-index coordinates)   (Eq. 10)
-//   20     log2(e) / (2 s_l^2 N^2)    filter exponent per (px^2 |d|^2 t^2)
-//   21     filter cut: evaluate the filter only while its base-2 exponent
+//   9      squared radius of the kernel support in the plane (max over
+//          sectors of rho_k, see the preprocess); < 0 when the kernel
+//          term cannot reach alpha_min
+//   10     filter cut: evaluate the filter only while its base-2 exponent
 //          is below this (beyond it the filter is < alpha_min / 2); < 0 = off
-//   22     tau
-//   23     unused
+//   11,12  projected centre minus 0.5 (pixel-index coordinates)   (Eq. 10)
+//   13     log2(e) / (2 s_l^2 N^2)    filter exponent per (px^2 |d|^2 t^2)
+//   14     o
+//   15     eta * log2(e) / 2         (Eq. 8, base-2 exponent)
+//          (floats 0-15, the first 64 bytes, are all the geometry stage
+//          of the evaluation reads)
+//   16     (1 - eta) * log2(e) / 2
+//   17,18  Psi breakpoints (1 + tau)/4, (3 - tau)/4          (Eq. 9)
+//   19     o (1 - tau)/(1 + tau)      outer slope (x o)
+//   20     o (1 + tau)/(1 - tau)      middle slope (x o)
+//   21     -o tau/(1 - tau)           middle offset (x o)
+//   22     2 o tau/(1 + tau)          upper offset (x o)
+//   23     tau
 //   24..   theta'_1 .. theta'_{KMAX-1}, padded with +1e30
 // then KMAX sectors of 8 floats:
 //   theta'_k, pi / gap_k, A_k + A_k1, A_k - A_k1, Minv (row-major, 4)
@@ -57,10 +61,11 @@ constexpr double csqrt(double x) { return csqrt_iter(x, x > 1.0 ? x : 1.0, 60); 
 // ---------------------------------------------------------------------------
 enum : int {
     R_HU0 = 0, R_HU1, R_HU2, R_HV0, R_HV1, R_HV2, R_HW0, R_HW1, R_HW2,
-    R_ETA2, R_ETA2C, R_OPA, R_B1, R_B2, R_SLO, R_SMID, R_OMID, R_OHI,
-    R_FPX, R_FPY, R_FCOEF, R_FCUT, R_TAU, R_UNUSED,
+    R_RHO2, R_FCUT, R_FPX, R_FPY, R_FCOEF, R_OPA, R_ETA2,
+    R_ETA2C, R_B1, R_B2, R_SLO, R_SMID, R_OMID, R_OHI, R_TAU,
     R_TH = 24
 };
+constexpr int R_GEO4 = 4;   // float4 count of the geometry part
 enum : int { S_TH = 0, S_PG, S_SUM, S_DIF, S_M00, S_M01, S_M10, S_M11, S_STRIDE };
 
 template <int KMAX>
@@ -120,32 +125,80 @@ struct EvalInfo {
     bool filt_eval, use_filter, clamped;
 };
 
-// One (pixel, primitive) evaluation: Eq. 4 - Eq. 10 and the clamp.  Every
-// rounding step is explicit (fmaf / __fmul_rn / __fadd_rn) so that the
-// forward pass and the backward replay produce bit-identical values.
-// Returns true iff the pair contributes (alpha_tilde >= alpha_min).
-template <int KMAX, bool INFO>
-__device__ __forceinline__ bool eval_pair(const float* __restrict__ r, const PixelRay& pr, float near_plane,
-                                          float alpha_min, float alpha_max, float& t_out, float& a_out,
-                                          EvalInfo* info = nullptr) {
-    constexpr int HDR = Rec<KMAX>::HDR;
-    const float w = fmaf(r[R_HW0], pr.x, fmaf(r[R_HW1], pr.y, r[R_HW2]));
+// Record header loads (16-byte, read-only path).  The geometry stage needs
+// the first R_GEO4 float4; the kernel stage the rest of the header.
+template <int KMAX>
+__device__ __forceinline__ void load_head_geo(const float4* __restrict__ r4, float* h) {
+#pragma unroll
+    for (int q = 0; q < R_GEO4; q++) {
+        const float4 v = __ldg(r4 + q);
+        h[4 * q] = v.x; h[4 * q + 1] = v.y; h[4 * q + 2] = v.z; h[4 * q + 3] = v.w;
+    }
+}
+template <int KMAX>
+__device__ __forceinline__ void load_head_rest(const float4* __restrict__ r4, float* h) {
+#pragma unroll
+    for (int q = R_GEO4; q < Rec<KMAX>::HDR / 4; q++) {
+        const float4 v = __ldg(r4 + q);
+        h[4 * q] = v.x; h[4 * q + 1] = v.y; h[4 * q + 2] = v.z; h[4 * q + 3] = v.w;
+    }
+}
+template <int KMAX>
+__device__ __forceinline__ void load_head(const float4* __restrict__ r4, float* h) {
+    load_head_geo<KMAX>(r4, h);
+    load_head_rest<KMAX>(r4, h);
+}
+
+// Geometry of one (pixel, primitive) pair: ray-plane intersection and local
+// coordinates (Eq. 4, Eq. 5, ray depth of Eq. 13).
+struct Geo {
+    float t, u, v, r2sq;
+};
+
+// Stage 1.  Returns false when the pair cannot contribute: the ray misses
+// the plane in front of the near plane, or the point lies beyond the
+// conservative support radius of the kernel and the low-pass filter is out
+// of reach too (then alpha_tilde < alpha_min; skipping never changes a
+// result).  Every rounding step is explicit (fmaf / __fmul_rn / __fadd_rn)
+// so that the forward pass and the backward reproduce identical values.
+__device__ __forceinline__ bool eval_geometry(const float* h, const PixelRay& pr, float near_plane, Geo& g) {
+    const float w = fmaf(h[R_HW0], pr.x, fmaf(h[R_HW1], pr.y, h[R_HW2]));
     if (!(w > 0.0f)) return false;
     const float t = rcp_approx(w);
     if (!(t > near_plane)) return false;
-    const float U = fmaf(r[R_HU0], pr.x, fmaf(r[R_HU1], pr.y, r[R_HU2]));
-    const float V = fmaf(r[R_HV0], pr.x, fmaf(r[R_HV1], pr.y, r[R_HV2]));
+    const float U = fmaf(h[R_HU0], pr.x, fmaf(h[R_HU1], pr.y, h[R_HU2]));
+    const float V = fmaf(h[R_HV0], pr.x, fmaf(h[R_HV1], pr.y, h[R_HV2]));
     const float u = __fmul_rn(U, t);
     const float v = __fmul_rn(V, t);
     const float r2sq = fmaf(u, u, __fmul_rn(v, v));
+    g.t = t; g.u = u; g.v = v; g.r2sq = r2sq;
+    if (r2sq > h[R_RHO2]) {
+        if (!(h[R_FCUT] > 0.0f)) return false;
+        const float dx = __fadd_rn(pr.x, -h[R_FPX]);
+        const float dy = __fadd_rn(pr.y, -h[R_FPY]);
+        const float dp2 = fmaf(dx, dx, __fmul_rn(dy, dy));
+        const float Xf = __fmul_rn(__fmul_rn(dp2, pr.d2), __fmul_rn(__fmul_rn(t, t), h[R_FCOEF]));
+        if (!(Xf < h[R_FCUT])) return false;
+    }
+    return true;
+}
+
+// Stage 2: the deformable radial kernel (Eq. 6 - Eq. 9), the low-pass
+// filter (Eq. 10) and the clamp.  `sec` points to the record's sector
+// array in global memory.  Returns true iff alpha_tilde >= alpha_min.
+template <int KMAX, bool INFO>
+__device__ __forceinline__ bool eval_kernel(const float* h, const float* __restrict__ sec, const PixelRay& pr,
+                                            const Geo& gm, float alpha_min, float alpha_max, float& a_out,
+                                            EvalInfo* info = nullptr) {
+    const float t = gm.t, u = gm.u, v = gm.v, r2sq = gm.r2sq;
     // polar angle from the first basis (Eq. 6 with reading: full circle)
     float phi = atan2f(v, u);
     phi = phi < 0.0f ? __fadd_rn(phi, kTwoPi) : phi;
     int k = 0;
 #pragma unroll
-    for (int j = 1; j < KMAX; j++) k += (r[R_TH + j - 1] < phi) ? 1 : 0;
-    const float4 s0 = *reinterpret_cast<const float4*>(r + HDR + S_STRIDE * k);
-    const float4 s1 = *reinterpret_cast<const float4*>(r + HDR + S_STRIDE * k + 4);
+    for (int j = 1; j < KMAX; j++) k += (h[R_TH + j - 1] < phi) ? 1 : 0;
+    const float4 s0 = __ldg(reinterpret_cast<const float4*>(sec + S_STRIDE * k));
+    const float4 s1 = __ldg(reinterpret_cast<const float4*>(sec + S_STRIDE * k + 4));
     // Eq. 6: relative angle, cosine weight, inverse squared radius
     const float dth = __fmul_rn(__fadd_rn(phi, -s0.x), s0.y);
     const float c = __cosf(dth);
@@ -155,31 +208,30 @@ __device__ __forceinline__ bool eval_pair(const float* __restrict__ r, const Pix
     const float b = fmaf(s1.z, u, __fmul_rn(s1.w, v));
     const float r1 = __fadd_rn(fabsf(a), fabsf(b));
     // Eq. 8 in base 2: g = 2^-X, X = log2(e)/2 (eta r1^2 + (1 - eta) r2^2 Q)
-    const float X = fmaf(r[R_ETA2], __fmul_rn(r1, r1), __fmul_rn(r[R_ETA2C], __fmul_rn(r2sq, Q)));
+    const float X = fmaf(h[R_ETA2], __fmul_rn(r1, r1), __fmul_rn(h[R_ETA2C], __fmul_rn(r2sq, Q)));
     const float g = ex2_approx(-X);
     // Eq. 9 with o folded into the pieces
     float al;
-    if (g < r[R_B1]) al = __fmul_rn(r[R_SLO], g);
-    else if (g < r[R_B2]) al = fmaf(r[R_SMID], g, r[R_OMID]);
-    else al = fmaf(r[R_SLO], g, r[R_OHI]);
+    if (g < h[R_B1]) al = __fmul_rn(h[R_SLO], g);
+    else if (g < h[R_B2]) al = fmaf(h[R_SMID], g, h[R_OMID]);
+    else al = fmaf(h[R_SLO], g, h[R_OHI]);
     const float al_k = al;
     // Eq. 10: view-dependent low-pass filter, max with the kernel
     bool filt_eval = false, use_filter = false;
     float Xf = 0.0f, f = 0.0f;
-    if (r[R_FCUT] > 0.0f) {
-        const float dx = __fadd_rn(pr.x, -r[R_FPX]);
-        const float dy = __fadd_rn(pr.y, -r[R_FPY]);
+    if (h[R_FCUT] > 0.0f) {
+        const float dx = __fadd_rn(pr.x, -h[R_FPX]);
+        const float dy = __fadd_rn(pr.y, -h[R_FPY]);
         const float dp2 = fmaf(dx, dx, __fmul_rn(dy, dy));
-        Xf = __fmul_rn(__fmul_rn(dp2, pr.d2), __fmul_rn(__fmul_rn(t, t), r[R_FCOEF]));
-        if (Xf < r[R_FCUT]) {
+        Xf = __fmul_rn(__fmul_rn(dp2, pr.d2), __fmul_rn(__fmul_rn(t, t), h[R_FCOEF]));
+        if (Xf < h[R_FCUT]) {
             filt_eval = true;
-            f = __fmul_rn(r[R_OPA], ex2_approx(-Xf));
+            f = __fmul_rn(h[R_OPA], ex2_approx(-Xf));
             if (f > al) { al = f; use_filter = true; }
         }
     }
     bool clamped = false;
     if (al > alpha_max) { al = alpha_max; clamped = true; }
-    t_out = t;
     a_out = al;
     if (INFO) {
         info->t = t; info->u = u; info->v = v; info->phi = phi; info->r2sq = r2sq; info->dth = dth;
@@ -190,53 +242,18 @@ __device__ __forceinline__ bool eval_pair(const float* __restrict__ r, const Pix
     return al >= alpha_min;
 }
 
-// ---------------------------------------------------------------------------
-// Per-pixel depth-order buffer (the exact variant of the paper's
-// cache-sorting, Sec. 4.4 and the supplementary algorithm).
-//
-// Entries are (key, alpha) with key = (float bits of r_t) << 32 | index, so
-// an unsigned compare orders by (r_t, primitive index).  The buffer is kept
-// sorted ascending in registers; empty slots hold key = ~0.  Because the
-// tile list is visited in ascending order of a per-(primitive, tile) lower
-// bound of r_t, every buffered entry whose r_t is below the bound of the
-// next list item can be composited: no later item can precede it.  When the
-// buffer is full, the largest key is evicted and becomes the pass horizon;
-// keys at or beyond the horizon are left for another pass over the list,
-// which starts at that horizon.  The composited order is therefore exactly
-// the (r_t, index) order for any capacity.
-// ---------------------------------------------------------------------------
-template <int CAP>
-struct KBuf {
-    uint64_t key[CAP];
-    float alpha[CAP];
-
-    __device__ __forceinline__ void clear() {
-#pragma unroll
-        for (int i = 0; i < CAP; i++) { key[i] = ~0ull; alpha[i] = 0.0f; }
-    }
-    __device__ __forceinline__ bool empty() const { return key[0] == ~0ull; }
-    __device__ __forceinline__ float front_t() const { return __uint_as_float((uint32_t)(key[0] >> 32)); }
-    // insert; returns the key that fell off the end (~0 if none)
-    __device__ __forceinline__ uint64_t insert(uint64_t k, float a) {
-#pragma unroll
-        for (int i = 0; i < CAP; i++) {
-            const bool sw = k < key[i];
-            const uint64_t tk = sw ? k : key[i];
-            const float ta = sw ? a : alpha[i];
-            k = sw ? key[i] : k;
-            a = sw ? alpha[i] : a;
-            key[i] = tk;
-            alpha[i] = ta;
-        }
-        return k;
-    }
-    __device__ __forceinline__ void pop_front() {
-#pragma unroll
-        for (int i = 0; i < CAP - 1; i++) { key[i] = key[i + 1]; alpha[i] = alpha[i + 1]; }
-        key[CAP - 1] = ~0ull;
-        alpha[CAP - 1] = 0.0f;
-    }
-};
+// Both stages for a record in global memory (header loaded into registers).
+template <int KMAX, bool INFO>
+__device__ __forceinline__ bool eval_pair(const float* __restrict__ rec, const PixelRay& pr, float near_plane,
+                                          float alpha_min, float alpha_max, float& t_out, float& a_out,
+                                          EvalInfo* info = nullptr) {
+    float h[Rec<KMAX>::HDR];
+    load_head<KMAX>(reinterpret_cast<const float4*>(rec), h);
+    Geo gm;
+    if (!eval_geometry(h, pr, near_plane, gm)) return false;
+    t_out = gm.t;
+    return eval_kernel<KMAX, INFO>(h, rec + Rec<KMAX>::HDR, pr, gm, alpha_min, alpha_max, a_out, info);
+}
 
 // Launch-wide constants of one render.
 struct FrameConst {

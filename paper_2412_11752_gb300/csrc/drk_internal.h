@@ -51,10 +51,20 @@ struct RasterArgs {
     const DepthQuant* dq;
     unsigned long long* counters;   // evals, emitted, extra passes (may be null)
     int* status;                     // device status bits (may be null)
+    unsigned int* task_counter;      // work counter of the persistent raster (zeroed per launch)
     // forward outputs
     float* out_rgb;
     float* out_T;
     int32_t* out_n;
+    // contributor lists recorded by the forward for the backward (may be null):
+    // emit_pos[(tile * emit_cap + s) * kTilePix + thread] = list position of
+    // the s-th composited contributor; emit_n[tile * kTilePix + thread] =
+    // count; tile_overflow[tile] != 0 if some pixel had more than emit_cap
+    uint32_t* emit_pos;
+    int32_t* emit_n;
+    int32_t* tile_overflow;
+    int emit_cap;
+    int* emit_max;                   // running maximum of per-pixel counts (sizes later lists)
     // backward
     drk_params_t p;
     const float* dL;
@@ -81,5 +91,6 @@ void radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32
 void launch_tile_ranges(const uint32_t* keys, int64_t n, int depth_bits, uint2* ranges, int n_tiles,
                         cudaStream_t st);
 void launch_raster(const RasterArgs& A, int kmax, int cap, bool bwd, cudaStream_t st);
+void launch_raster_backward_list(const RasterArgs& A, int kmax, cudaStream_t st);
 
 }  // namespace drk

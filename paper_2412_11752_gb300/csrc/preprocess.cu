@@ -202,7 +202,6 @@ __global__ void __launch_bounds__(128) preprocess_kernel(PreArgs A) {
     rec[R_OMID] = -o * tau / (1.f - tau);
     rec[R_OHI] = 2.f * o * tau / (1.f + tau);
     rec[R_TAU] = tau;
-    rec[R_UNUSED] = 0.f;
 
     // Eq. 10 low-pass filter
     const bool filt_on = A.sl > 0.f && G.muc[2] > A.fc.near_plane && plane_ok && o > 0.5f * A.fc.alpha_min;
@@ -291,6 +290,7 @@ __global__ void __launch_bounds__(128) preprocess_kernel(PreArgs A) {
     } else {
         for (int k = 0; k < KMAX; k++) rho[k] = 0.f;
     }
+    rec[R_RHO2] = kernel_on ? rho_max * rho_max : -1.f;
     float minx = 1e30f, miny = 1e30f, maxx = -1e30f, maxy = -1e30f;
     float zlb = 1e30f, zub = -1e30f;
     bool crosses_near = false;
@@ -422,9 +422,9 @@ __device__ __forceinline__ bool tile_test(const float* __restrict__ rec, const f
         const float px = qu[c] + tpar * ex, py = qv[c] + tpar * ey;
         dmin2 = fminf(dmin2, px * px + py * py);
     }
-    const float rmax = bnd[B_RHOMAX];
-    if (dmin2 > rmax * rmax * 1.002f) return false;
     if (pos == 0 || neg == 0) return true;                          // centre inside the quad
+    const float rmax = bnd[B_RHOMAX];
+    if (dmin2 > rmax * rmax * 1.002f) return false;                 // quad beyond every sector radius
     // angular range of the quad seen from the centre (< pi since the quad is
     // convex and excludes the centre)
     float ang[4];

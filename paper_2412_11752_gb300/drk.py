@@ -57,7 +57,8 @@ class drk_image_t(C.Structure):
 
 class drk_stats_t(C.Structure):
     _fields_ = [("n_visible", C.c_int64), ("n_pairs", C.c_int64), ("n_evals", C.c_int64), ("n_emitted", C.c_int64),
-                ("n_extra_passes", C.c_int64), ("n_tiles", C.c_int64), ("key_bits_depth", C.c_int32),
+                ("n_extra_passes", C.c_int64), ("n_tiles", C.c_int64), ("n_contrib_evals", C.c_int64),
+                ("key_bits_depth", C.c_int32),
                 ("status", C.c_int32)]
 
 

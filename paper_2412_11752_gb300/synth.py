@@ -287,6 +287,8 @@ WORKLOADS = {
     # name: (scene factory, camera factory)
     "plain-2k-128": (lambda: scene_plain(2000, 8, 1000), lambda: camera_front(128, 128)),
     "clustered-100k-1080p": (lambda: scene_clustered(100_000, 8, 2000), lambda: camera_front(1920, 1080)),
+    # same scene at a quarter of the pixels (small case for counter captures)
+    "clustered-100k-540p": (lambda: scene_clustered(100_000, 8, 2000), lambda: camera_front(960, 540)),
     "train-300k-1600x1064": (lambda: scene_clustered(300_000, 8, 3000), lambda: camera_front(1600, 1064)),
     "slab-2M-k16-4k": (lambda: scene_slab(2_000_000, 16, 5000), lambda: camera_front(3840, 2160)),
 }

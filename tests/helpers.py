@@ -19,7 +19,7 @@ def oracle_options(opt) -> O.Options:
 
 def excluded(flags: np.ndarray) -> np.ndarray:
     """Pixels whose result is decided by an FP32-vs-FP64 threshold or depth tie."""
-    return (flags & (O.FLAG_T_MIN | O.FLAG_DEPTH_TIE)) != 0
+    return (flags & (O.FLAG_T_MIN | O.FLAG_DEPTH_TIE | O.FLAG_STEEP)) != 0
 
 
 def image_error(gpu_rgb: np.ndarray, ref_rgb: np.ndarray, flags: np.ndarray):
