@@ -183,6 +183,26 @@ void drk_state_free(drk_state_t *state);
  * the context's pool.  Asynchronous.  n < 2^32. */
 drk_status_t drk_sort_pairs(drk_ctx_t *ctx, uint32_t *keys, uint32_t *vals, int64_t n, int key_bits, void *stream);
 
+/* drk_sort_pairs without any device allocation, for callers that cannot
+ * allocate when they sort: a stream being captured into a graph that must
+ * hold no allocation nodes, a host callback, or an embedder whose device
+ * memory is fixed at start-up.  The paper has no counterpart; this is a
+ * service of the library.
+ *   keys, vals  device arrays of n uint32 (sorted in place, stable, by the
+ *               low key_bits bits of the keys, 1..32)
+ *   n           0 .. 1048576 (2^20); larger n returns DRK_ERR_CAPACITY
+ *               before anything is launched
+ * Working memory is one fixed device array inside the library (9 MiB per
+ * GPU that loads it, held until the process exits); the call allocates and
+ * frees nothing.  The first call on a device looks the array's address up
+ * with that device current, so make that first call before any stream
+ * capture.  All calls share the array and it keeps the contents of the last
+ * call: calls whose work could overlap on the GPU (different streams, or
+ * different host threads) race on it and must be ordered by the caller.
+ * Asynchronous on `stream`; returns DRK_ERR_INVALID_ARG for bad arguments,
+ * DRK_ERR_CUDA if a launch fails. */
+drk_status_t drk_sort_pairs_static(uint32_t *keys, uint32_t *vals, int64_t n, int key_bits, void *stream);
+
 /* Synchronises the stream of the last render and copies its counters. */
 drk_status_t drk_get_stats(drk_ctx_t *ctx, drk_stats_t *out);
 

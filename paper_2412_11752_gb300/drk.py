@@ -93,6 +93,8 @@ def lib():
         L.drk_state_free.restype = None
         L.drk_get_stats.argtypes = [vp, C.POINTER(drk_stats_t)]
         L.drk_sort_pairs.argtypes = [vp, vp, vp, C.c_int64, C.c_int, vp]
+        L.drk_sort_pairs_static.argtypes = [vp, vp, C.c_int64, C.c_int, vp]
+        L.drk_sort_pairs_static.restype = C.c_int
         L.drk_timing_enable.argtypes = [vp, C.c_int]
         L.drk_timing_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
         L.drk_launch_count.restype = C.c_int64
@@ -312,6 +314,20 @@ def drk_sort_pairs(keys: torch.Tensor, vals: torch.Tensor, key_bits: int = 32, c
     ctx = ctx or default_context(keys.device.index or 0)
     _check(lib().drk_sort_pairs(ctx.handle, C.c_void_p(keys.data_ptr()), C.c_void_p(vals.data_ptr()),
                                 keys.numel(), int(key_bits), _stream_ptr(stream)))
+
+
+def drk_sort_pairs_static(keys: torch.Tensor, vals: torch.Tensor, key_bits: int = 32, stream=None) -> None:
+    """drk_sort_pairs for callers that cannot allocate device memory while they
+    sort (graph capture without allocation nodes, host callbacks, fixed
+    start-up memory): the working memory is a fixed array inside the library,
+    shared by all calls (order overlapping calls yourself).  At most 2^20
+    pairs; make the first call on a device before any stream capture."""
+    assert keys.is_cuda and keys.dtype == torch.int32 and vals.dtype == torch.int32
+    assert keys.is_contiguous() and vals.is_contiguous() and keys.numel() == vals.numel()
+    code = lib().drk_sort_pairs_static(C.c_void_p(keys.data_ptr()), C.c_void_p(vals.data_ptr()), keys.numel(),
+                                      int(key_bits), _stream_ptr(stream))
+    if code != DRK_OK:
+        raise DrkError(code, "drk_sort_pairs_static failed (n above 2^20, bad arguments or a launch error)")
 
 
 class DRKRender(torch.autograd.Function):
