@@ -448,17 +448,26 @@ typedef struct { double t; int64_t idx; double alpha, dalpha; } contrib;
  * Eq. 8 (or the filter exponent of Eq. 10) carries an absolute error of at
  * most about 4e-6 (1 + E) in float32 (relative 2e-6 from the projected
  * coordinates, plus the rounding of the exponent itself); it moves alpha by
- * o Psi'(g) g dE / 2.  A clamped alpha has no error.                       */
+ * o Psi'(g) g dE / 2.  Near grazing incidence the ray-plane intersection
+ * of Eq. 4 is ill-conditioned: one float32 rounding (about 1.2e-7) of the
+ * ray direction moves the intersection by t |d| 1.2e-7 / cos, with cos the
+ * cosine between the ray and the plane normal, which adds about
+ * 2 E (t |d| / r2) 1.2e-7 / cos to E.  A clamped alpha has no error.       */
 static double alpha_fp32_error(const pair_eval *pe, double tau, double o)
 {
     if (pe->clamped) return 0.0;
+    double dnorm = sqrt(dot3(pe->d, pe->d));
+    double cosv = fabs(pe->dn) / dnorm;
     if (pe->use_filter) {
         double Xf = -log(pe->filt / o);
-        return pe->filt * 0.5 * 4e-6 * (1.0 + 2.0 * Xf);
+        return pe->filt * (0.5 * 4e-6 * (1.0 + 2.0 * Xf) + Xf * 2.4e-7 / cosv);
     }
     double dpsi, dtau;
     psi_grad(pe->ke.g, tau, &dpsi, &dtau);
-    return o * dpsi * pe->ke.g * 0.5 * 4e-6 * (1.0 + pe->ke.E);
+    double r2 = sqrt(pe->ke.r2sq);
+    double dE = 4e-6 * (1.0 + pe->ke.E);
+    if (r2 > 0.0) dE += 2.0 * pe->ke.E * (pe->t * dnorm / r2) * 1.2e-7 / cosv;
+    return o * dpsi * pe->ke.g * 0.5 * dE;
 }
 
 static int contrib_cmp(const void *pa, const void *pb)

@@ -18,7 +18,7 @@
 #include <new>
 #include <vector>
 
-#include "drk_internal.h"
+#include "host.h"
 
 using namespace drk;
 
@@ -29,55 +29,47 @@ namespace drk {
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 }  // namespace drk
 
-// CUDA-event timing of the pipeline stages (off unless enabled)
-enum { ST_PREPROCESS = 0, ST_EMIT, ST_SORT, ST_RASTER, ST_RASTER_BWD, ST_PREPROCESS_BWD, ST_COUNT = 8 };
-struct StageTimer {
-    bool on = false;
-    std::vector<cudaEvent_t> pool;
-    struct Pending { int stage; cudaEvent_t a, b; };
-    std::vector<Pending> pending;
-    double ms[ST_COUNT] = {0};
-    long long cnt[ST_COUNT] = {0};
-    cudaEvent_t get() {
-        if (!pool.empty()) {
-            cudaEvent_t e = pool.back();
-            pool.pop_back();
-            return e;
-        }
-        cudaEvent_t e = nullptr;
-        cudaEventCreate(&e);
+namespace drk {
+cudaEvent_t StageTimer::get() {
+    if (!pool.empty()) {
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
         return e;
     }
-    cudaEvent_t begin(cudaStream_t st) {
-        if (!on) return nullptr;
-        cudaEvent_t a = get();
-        cudaEventRecord(a, st);
-        return a;
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+cudaEvent_t StageTimer::begin(cudaStream_t st) {
+    if (!on) return nullptr;
+    cudaEvent_t a = get();
+    cudaEventRecord(a, st);
+    return a;
+}
+void StageTimer::end(int stage, cudaEvent_t a, cudaStream_t st) {
+    if (!on || !a) return;
+    cudaEvent_t b = get();
+    cudaEventRecord(b, st);
+    pending.push_back({stage, a, b});
+}
+void StageTimer::collect() {
+    for (auto& p : pending) {
+        float t = 0.f;
+        cudaEventSynchronize(p.b);
+        cudaEventElapsedTime(&t, p.a, p.b);
+        ms[p.stage] += t;
+        cnt[p.stage] += 1;
+        pool.push_back(p.a);
+        pool.push_back(p.b);
     }
-    void end(int stage, cudaEvent_t a, cudaStream_t st) {
-        if (!on || !a) return;
-        cudaEvent_t b = get();
-        cudaEventRecord(b, st);
-        pending.push_back({stage, a, b});
-    }
-    void collect() {
-        for (auto& p : pending) {
-            float t = 0.f;
-            cudaEventSynchronize(p.b);
-            cudaEventElapsedTime(&t, p.a, p.b);
-            ms[p.stage] += t;
-            cnt[p.stage] += 1;
-            pool.push_back(p.a);
-            pool.push_back(p.b);
-        }
-        pending.clear();
-    }
-    void destroy() {
-        collect();
-        for (auto e : pool) cudaEventDestroy(e);
-        pool.clear();
-    }
-};
+    pending.clear();
+}
+void StageTimer::destroy() {
+    collect();
+    for (auto e : pool) cudaEventDestroy(e);
+    pool.clear();
+}
+}  // namespace drk
 
 struct drk_ctx {
     StageTimer timer;
@@ -103,6 +95,7 @@ struct drk_state {
     uint32_t* keys = nullptr;
     uint32_t* vals = nullptr;
     uint2* ranges = nullptr;
+    uint32_t* tile_order = nullptr;
     DepthQuant* dq = nullptr;
     float* Cfin = nullptr;
     uint32_t* emit_pos = nullptr;
@@ -118,9 +111,13 @@ struct drk_state {
 constexpr int kEmitCap = 256;
 constexpr int kEmitCapMax = 4096;
 
-namespace {
+namespace drk {
 
+namespace {
 thread_local char g_err[512] = "";
+}
+
+const char* last_error_message() { return g_err; }
 
 drk_status_t fail(drk_status_t s, const char* fmt, ...) {
     va_list ap;
@@ -129,39 +126,6 @@ drk_status_t fail(drk_status_t s, const char* fmt, ...) {
     va_end(ap);
     return s;
 }
-
-#define DRK_CUDA(call)                                                                     \
-    do {                                                                                   \
-        cudaError_t e_ = (call);                                                           \
-        if (e_ != cudaSuccess)                                                             \
-            return fail(DRK_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));     \
-    } while (0)
-
-// stream-ordered allocations of one call; freed together unless kept
-struct Allocs {
-    cudaMemPool_t pool;
-    cudaStream_t st;
-    std::vector<void*> ptrs;
-    bool keep = false;
-    Allocs(cudaMemPool_t p, cudaStream_t s) : pool(p), st(s) {}
-    ~Allocs() {
-        if (!keep)
-            for (void* q : ptrs) cudaFreeAsync(q, st);
-    }
-    template <typename T>
-    drk_status_t get(T** out, size_t count) {
-        void* q = nullptr;
-        const size_t bytes = count * sizeof(T) > 0 ? count * sizeof(T) : 16;
-        const cudaError_t e = cudaMallocFromPoolAsync(&q, bytes, pool, st);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return fail(DRK_ERR_OOM, "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
-        }
-        ptrs.push_back(q);
-        *out = reinterpret_cast<T*>(q);
-        return DRK_OK;
-    }
-};
 
 bool finite_pos(float v) { return std::isfinite(v) && v > 0.f; }
 
@@ -195,15 +159,8 @@ drk_status_t validate(const drk_params_t* p, const drk_camera_t* cam, const drk_
     return DRK_OK;
 }
 
-struct Frame {
-    FrameConst fc;
-    CamDev cam;
-    float center[3];
-    int n_tiles, tile_bits, depth_bits, kmax;
-};
-
 Frame make_frame(const drk_params_t* p, const drk_camera_t* cam, const drk_options_t* opt) {
-    Frame F;
+    Frame F{};
     FrameConst& fc = F.fc;
     fc.width = cam->width;
     fc.height = cam->height;
@@ -241,7 +198,77 @@ drk_status_t check_launch() {
     return DRK_OK;
 }
 
-}  // namespace
+drk_status_t frame_phase_a(FrameWork& w, const drk_params_t* params, const drk_camera_t* cam,
+                           const drk_options_t* opt, Allocs& al, unsigned long long* counters, int* status,
+                           uint64_t* total_host, cudaStream_t st, StageTimer* tm) {
+    w.F = make_frame(params, cam, opt);
+    const Frame& F = w.F;
+    const int64_t n = params->n;
+    PreArgs& A = w.A;
+    std::memset(&A, 0, sizeof(A));
+    A.p = *params;
+    A.cam = F.cam;
+    for (int c = 0; c < 3; c++) A.cam_center[c] = F.center[c];
+    A.fc = F.fc;
+    A.sl = opt->lowpass_sl;
+    A.cull_level = opt->cull_level;
+    A.depth_bits = F.depth_bits;
+    A.counters = counters;
+    A.status = status;
+    drk_status_t s;
+    if ((s = al.get(&A.rec, (size_t)n * rec_floats(F.kmax))) != DRK_OK) return s;
+    if ((s = al.get(&A.bnd, (size_t)n * bnd_floats(F.kmax))) != DRK_OK) return s;
+    if ((s = al.get(&A.rgb, (size_t)n * 3)) != DRK_OK) return s;
+    if ((s = al.get(&A.count, (size_t)n + 1)) != DRK_OK) return s;
+    if ((s = al.get(&A.offsets, (size_t)n + 1)) != DRK_OK) return s;
+    if ((s = al.get(&A.zmax_bits, 1)) != DRK_OK) return s;
+    if ((s = al.get(&A.dq, 1)) != DRK_OK) return s;
+    uint8_t* scan_scr = nullptr;
+    if ((s = al.get(&scan_scr, scan_scratch_bytes(n + 1))) != DRK_OK) return s;
+    // 0.0f: every bound is beyond the near plane, so any maximum wins
+    DRK_CUDA(cudaMemsetAsync(A.zmax_bits, 0, sizeof(int), st));
+    cudaEvent_t ev = tm ? tm->begin(st) : nullptr;
+    if (F.kmax == 8) launch_preprocess<8>(A, st); else launch_preprocess<16>(A, st);
+    if (opt->cull_level >= 2) {
+        if (F.kmax == 8) launch_count<8>(A, st); else launch_count<16>(A, st);
+    }
+    if ((s = check_launch()) != DRK_OK) return s;
+    exclusive_scan_u32_u64(A.count, A.offsets, n, scan_scr, st);
+    launch_depth_quant(A, st);
+    if (tm) tm->end(ST_PREPROCESS, ev, st);
+    DRK_CUDA(cudaMemcpyAsync(total_host, A.offsets + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    return check_launch();
+}
+
+drk_status_t frame_phase_b(FrameWork& w, Allocs& al, cudaStream_t st, StageTimer* tm) {
+    const Frame& F = w.F;
+    PreArgs& A = w.A;
+    const int64_t P = w.P;
+    if (P >= (int64_t(1) << 32) - 1)
+        return fail(DRK_ERR_CAPACITY, "%lld pairs exceed the 2^32 - 1 limit of one render", (long long)P);
+    drk_status_t s;
+    uint8_t* sort_scr = nullptr;
+    uint8_t* order_work = nullptr;
+    if ((s = al.get(&A.keys, (size_t)P)) != DRK_OK) return s;
+    if ((s = al.get(&A.vals, (size_t)P)) != DRK_OK) return s;
+    if ((s = al.get(&w.kalt, (size_t)P)) != DRK_OK) return s;
+    if ((s = al.get(&w.valt, (size_t)P)) != DRK_OK) return s;
+    if ((s = al.get(&w.ranges, (size_t)F.n_tiles)) != DRK_OK) return s;
+    if ((s = al.get(&sort_scr, radix_sort_scratch_bytes(P))) != DRK_OK) return s;
+    if ((s = al.get(&w.tile_order, (size_t)F.n_tiles)) != DRK_OK) return s;
+    if ((s = al.get(&order_work, tile_order_work_bytes(F.n_tiles))) != DRK_OK) return s;
+    cudaEvent_t ev = tm ? tm->begin(st) : nullptr;
+    if (F.kmax == 8) launch_emit<8>(A, st); else launch_emit<16>(A, st);
+    if (tm) tm->end(ST_EMIT, ev, st);
+    ev = tm ? tm->begin(st) : nullptr;
+    radix_sort_pairs(A.keys, A.vals, w.kalt, w.valt, P, 32, sort_scr, st);
+    launch_tile_ranges(A.keys, P, F.depth_bits, w.ranges, F.n_tiles, st);
+    launch_tile_order(w.ranges, F.n_tiles, w.tile_order, order_work, st);
+    if (tm) tm->end(ST_SORT, ev, st);
+    return check_launch();
+}
+
+}  // namespace drk
 
 extern "C" {
 
@@ -257,7 +284,7 @@ void drk_options_default(drk_options_t* opt) {
     opt->kbuf_capacity = 16;
 }
 
-const char* drk_last_error(void) { return g_err; }
+const char* drk_last_error(void) { return last_error_message(); }
 
 const char* drk_version(void) { return "libdrk 0.1 (sm_103a)"; }
 
@@ -319,76 +346,24 @@ drk_status_t drk_render(drk_ctx_t* ctx, const drk_params_t* params, const drk_ca
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     DRK_CUDA(cudaSetDevice(ctx->device));
     ctx->last_stream = st;
-    const Frame F = make_frame(params, cam, opt);
     const int64_t n = params->n;
     Allocs al(ctx->pool, st);
-
-    PreArgs A;
-    std::memset(&A, 0, sizeof(A));
-    A.p = *params;
-    A.cam = F.cam;
-    for (int c = 0; c < 3; c++) A.cam_center[c] = F.center[c];
-    A.fc = F.fc;
-    A.sl = opt->lowpass_sl;
-    A.cull_level = opt->cull_level;
-    A.depth_bits = F.depth_bits;
-    A.zmax_bits = ctx->zmax_bits;
-    A.counters = ctx->counters;
-    A.status = reinterpret_cast<int*>(ctx->counters + 4);
-    if ((s = al.get(&A.rec, (size_t)n * rec_floats(F.kmax))) != DRK_OK) return s;
-    if ((s = al.get(&A.bnd, (size_t)n * bnd_floats(F.kmax))) != DRK_OK) return s;
-    if ((s = al.get(&A.rgb, (size_t)n * 3)) != DRK_OK) return s;
-    if ((s = al.get(&A.count, (size_t)n + 1)) != DRK_OK) return s;
-    if ((s = al.get(&A.offsets, (size_t)n + 1)) != DRK_OK) return s;
-    void* scan_scr = nullptr;
-    if ((s = al.get(reinterpret_cast<uint8_t**>(&scan_scr), scan_scratch_bytes(n + 1))) != DRK_OK) return s;
-    DepthQuant* dq = nullptr;
-    if ((s = al.get(&dq, 1)) != DRK_OK) return s;
-    A.dq = dq;
-
-    const float near_bits_f = opt->near_plane;
-    int near_bits;
-    std::memcpy(&near_bits, &near_bits_f, sizeof(int));
-    DRK_CUDA(cudaMemcpyAsync(ctx->zmax_bits, &near_bits, sizeof(int), cudaMemcpyHostToDevice, st));
+    StageTimer& tm = ctx->timer;
     DRK_CUDA(cudaMemsetAsync(ctx->counters, 0, 8 * sizeof(unsigned long long), st));
 
-    StageTimer& tm = ctx->timer;
-    cudaEvent_t ev = tm.begin(st);
-    if (F.kmax == 8) launch_preprocess<8>(A, st); else launch_preprocess<16>(A, st);
-    if (opt->cull_level >= 2) {
-        if (F.kmax == 8) launch_count<8>(A, st); else launch_count<16>(A, st);
-    }
-    if ((s = check_launch()) != DRK_OK) return s;
-    exclusive_scan_u32_u64(A.count, A.offsets, n, scan_scr, st);
-    launch_depth_quant(A, st);
-    tm.end(ST_PREPROCESS, ev, st);
-    DRK_CUDA(cudaMemcpyAsync(ctx->h_total, A.offsets + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    FrameWork w;
+    if ((s = frame_phase_a(w, params, cam, opt, al, ctx->counters, reinterpret_cast<int*>(ctx->counters + 4),
+                           ctx->h_total, st, &tm)) != DRK_OK)
+        return s;
     if (state) {
         ctx->h_total[1] = 0;
         DRK_CUDA(cudaMemcpyAsync(ctx->h_total + 1, ctx->emit_max, sizeof(int), cudaMemcpyDeviceToHost, st));
     }
-    DRK_CUDA(cudaStreamSynchronize(st));
-    const int64_t P = (int64_t)ctx->h_total[0];
-    if (P >= (int64_t(1) << 32) - 1)
-        return fail(DRK_ERR_CAPACITY, "%lld pairs exceed the 2^32 - 1 limit of one render", (long long)P);
-
-    uint32_t *kalt = nullptr, *valt = nullptr;
-    uint2* ranges = nullptr;
-    void* sort_scr = nullptr;
-    if ((s = al.get(&A.keys, (size_t)P)) != DRK_OK) return s;
-    if ((s = al.get(&A.vals, (size_t)P)) != DRK_OK) return s;
-    if ((s = al.get(&kalt, (size_t)P)) != DRK_OK) return s;
-    if ((s = al.get(&valt, (size_t)P)) != DRK_OK) return s;
-    if ((s = al.get(&ranges, (size_t)F.n_tiles)) != DRK_OK) return s;
-    if ((s = al.get(reinterpret_cast<uint8_t**>(&sort_scr), radix_sort_scratch_bytes(P))) != DRK_OK) return s;
-
-    ev = tm.begin(st);
-    if (F.kmax == 8) launch_emit<8>(A, st); else launch_emit<16>(A, st);
-    tm.end(ST_EMIT, ev, st);
-    ev = tm.begin(st);
-    radix_sort_pairs(A.keys, A.vals, kalt, valt, P, 32, sort_scr, st);
-    launch_tile_ranges(A.keys, P, F.depth_bits, ranges, F.n_tiles, st);
-    tm.end(ST_SORT, ev, st);
+    DRK_CUDA(cudaStreamSynchronize(st));   // the pair total sizes the sort
+    w.P = (int64_t)ctx->h_total[0];
+    if ((s = frame_phase_b(w, al, st, &tm)) != DRK_OK) return s;
+    const Frame& F = w.F;
+    const PreArgs& A = w.A;
 
     RasterArgs R;
     std::memset(&R, 0, sizeof(R));
@@ -398,8 +373,9 @@ drk_status_t drk_render(drk_ctx_t* ctx, const drk_params_t* params, const drk_ca
     R.rgb = A.rgb;
     R.keys = A.keys;
     R.vals = A.vals;
-    R.ranges = ranges;
-    R.dq = dq;
+    R.ranges = w.ranges;
+    R.tile_order = w.tile_order;
+    R.dq = A.dq;
     R.counters = ctx->counters;
     R.status = reinterpret_cast<int*>(ctx->counters + 4);
     R.task_counter = reinterpret_cast<unsigned int*>(ctx->counters + 7);
@@ -421,13 +397,13 @@ drk_status_t drk_render(drk_ctx_t* ctx, const drk_params_t* params, const drk_ca
         if ((s = al.get(&R.tile_overflow, (size_t)F.n_tiles)) != DRK_OK) return s;
         DRK_CUDA(cudaMemsetAsync(R.tile_overflow, 0, sizeof(int32_t) * (size_t)F.n_tiles, st));
     }
-    ev = tm.begin(st);
+    cudaEvent_t ev = tm.begin(st);
     launch_raster(R, F.kmax, opt->kbuf_capacity, false, st);
     tm.end(ST_RASTER, ev, st);
     if ((s = check_launch()) != DRK_OK) return s;
 
     ctx->last = drk_stats_t{};
-    ctx->last.n_pairs = P;
+    ctx->last.n_pairs = w.P;
     ctx->last.n_tiles = F.n_tiles;
     ctx->last.key_bits_depth = F.depth_bits;
 
@@ -437,7 +413,7 @@ drk_status_t drk_render(drk_ctx_t* ctx, const drk_params_t* params, const drk_ca
         S->ctx = ctx;
         S->stream = st;
         S->n = n;
-        S->pairs = P;
+        S->pairs = w.P;
         S->K = params->K;
         S->kmax = F.kmax;
         S->cap = opt->kbuf_capacity;
@@ -449,8 +425,9 @@ drk_status_t drk_render(drk_ctx_t* ctx, const drk_params_t* params, const drk_ca
         S->rgb = A.rgb;
         S->keys = A.keys;
         S->vals = A.vals;
-        S->ranges = ranges;
-        S->dq = dq;
+        S->ranges = w.ranges;
+        S->tile_order = w.tile_order;
+        S->dq = A.dq;
         S->emit_pos = R.emit_pos;
         S->emit_n = R.emit_n;
         S->tile_overflow = R.tile_overflow;
@@ -512,6 +489,7 @@ drk_status_t drk_render_backward(drk_ctx_t* ctx, const drk_params_t* params, con
     R.keys = state->keys;
     R.vals = state->vals;
     R.ranges = state->ranges;
+    R.tile_order = state->tile_order;
     R.dq = state->dq;
     R.counters = nullptr;
     R.status = reinterpret_cast<int*>(ctx->counters + 4);

@@ -39,6 +39,20 @@ struct PreArgs {
     int* status;                   // device status bits (1 << drk_status_t)
 };
 
+// One frame of a batched forward raster (serving): everything the raster
+// reads per request.  order values of a batch encode (slot << 20) | tile.
+struct FrameSlot {
+    FrameConst fc;
+    const float* rec;
+    const float* rgb;
+    const uint32_t* keys;
+    const uint32_t* vals;
+    const uint2* ranges;
+    const DepthQuant* dq;
+    float* out_rgb;
+    int K;
+};
+
 // arguments of the raster kernels
 struct RasterArgs {
     FrameConst fc;
@@ -52,6 +66,12 @@ struct RasterArgs {
     unsigned long long* counters;   // evals, emitted, extra passes (may be null)
     int* status;                     // device status bits (may be null)
     unsigned int* task_counter;      // work counter of the persistent raster (zeroed per launch)
+    const uint32_t* tile_order;      // tiles by descending list length (may be null)
+    // batched forward (serving): when slots != null the kernel renders
+    // n_batch_tiles tiles taken from tile_order, each encoding (slot, tile),
+    // and reads the frame of each task from slots[slot]
+    const FrameSlot* slots;
+    int n_batch_tiles;
     // forward outputs
     float* out_rgb;
     float* out_T;
@@ -90,7 +110,13 @@ void radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32
                       void* scratch, cudaStream_t st);
 void launch_tile_ranges(const uint32_t* keys, int64_t n, int depth_bits, uint2* ranges, int n_tiles,
                         cudaStream_t st);
+// order[] = tile ids by descending list length; work holds 4 x n_tiles words
+// followed by radix_sort_scratch_bytes(n_tiles) bytes
+size_t tile_order_work_bytes(int n_tiles);
+void launch_tile_order(const uint2* ranges, int n_tiles, uint32_t* order, void* work, cudaStream_t st);
 void launch_raster(const RasterArgs& A, int kmax, int cap, bool bwd, cudaStream_t st);
 void launch_raster_backward_list(const RasterArgs& A, int kmax, cudaStream_t st);
+// batched forward over A.n_batch_tiles tiles of the frames in A.slots
+void launch_raster_batch(const RasterArgs& A, int kmax, int cap, cudaStream_t st);
 
 }  // namespace drk

@@ -75,15 +75,20 @@ struct RingBuf {
     float* sa;
     const uint32_t* vals;   // the tile's list (primitive index of position p)
     int head, n;
+    float ft;               // r_t of the front entry (+inf when empty), kept in a register
     __device__ __forceinline__ void init(float* t, uint32_t* p, float* a, const uint32_t* list) {
-        st = t; sp = p; sa = a; vals = list; head = 0; n = 0;
+        st = t; sp = p; sa = a; vals = list; head = 0; n = 0; ft = __int_as_float(0x7f800000);
     }
     __device__ __forceinline__ bool empty() const { return n == 0; }
-    __device__ __forceinline__ float front_t() const { return st[head * STRIDE]; }
+    __device__ __forceinline__ float front_t() const { return ft; }
     __device__ __forceinline__ uint32_t front_p() const { return sp[head * STRIDE]; }
     __device__ __forceinline__ float front_a() const { return sa[head * STRIDE]; }
-    __device__ __forceinline__ void pop_front() { head = (head + 1) & (CAP - 1); n--; }
-    __device__ __forceinline__ void clear() { head = 0; n = 0; }
+    __device__ __forceinline__ void pop_front() {
+        head = (head + 1) & (CAP - 1);
+        n--;
+        ft = n > 0 ? st[head * STRIDE] : __int_as_float(0x7f800000);
+    }
+    __device__ __forceinline__ void clear() { head = 0; n = 0; ft = __int_as_float(0x7f800000); }
     // (ts, index of ps) > (t, idx)?
     __device__ __forceinline__ bool after(float ts, uint32_t ps, float t, uint32_t idx) const {
         return ts > t || (ts == t && __ldg(vals + ps) > idx);
@@ -121,6 +126,7 @@ struct RingBuf {
         sp[d * STRIDE] = p;
         sa[d * STRIDE] = a;
         n++;
+        if (i == 0) ft = t;
         return out;
     }
 };
@@ -268,38 +274,239 @@ __device__ __forceinline__ void add_global(const RasterArgs& A, uint32_t idx, co
 }
 
 // ---------------------------------------------------------------------------
+// Counters a warp accumulates over its tasks.
+struct WarpCounters {
+    unsigned long long evals = 0, emit = 0, passes = 0, contrib = 0;
+    int max_emit = 0;
+};
+
+// One task of the forward (or replay) traversal: the 8 x 4 block `blk` of
+// `tile` in the frame (fc, rec, rgb, vals, keys, ranges, dq, out).
+template <int KMAX, int CAP, bool BWD>
+__device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& fc, const float* __restrict__ recp,
+                                         const float* __restrict__ rgbp, const uint32_t* __restrict__ valsp,
+                                         const uint32_t* __restrict__ keysp, const uint2* __restrict__ rangesp,
+                                         const DepthQuant* __restrict__ dqp, float* __restrict__ outp, bool batched,
+                                         int tile, uint32_t task, float4* stage, float* ring,
+                                         RingBuf<CAP, kRasterThreads>& kb, WarpCounters& wc) {
+    constexpr int HDR = Rec<KMAX>::HDR;
+    constexpr int STRIDE4 = Rec<KMAX>::STRIDE4;
+    constexpr int HDR4 = HDR / 4;
+    const int lane = threadIdx.x & 31;
+    const DepthQuant dq = *dqp;
+    const uint32_t qmask = (1u << dq.depth_bits) - 1u;
+    const float4* rec4 = reinterpret_cast<const float4*>(recp);
+    const size_t npix = (size_t)fc.width * fc.height;
+    const int blk = (int)(task & 7u);
+    if (BWD && A.tile_overflow && A.tile_overflow[tile] == 0) return;   // handled by the list kernel
+    const int tx = tile % fc.tiles_x, ty = tile / fc.tiles_x;
+    const int x = tx * kTile + (blk & 1) * 8 + (lane & 7);
+    const int y = ty * kTile + (blk >> 1) * 4 + (lane >> 3);
+    const int tpix = blk * 32 + lane;          // pixel slot within the tile
+    const bool inside = x < fc.width && y < fc.height;
+    const uint2 rg = rangesp[tile];
+    const uint32_t L = rg.y - rg.x;
+    const uint32_t* list = valsp + rg.x;
+    const uint32_t* lkeys = keysp + rg.x;
+    const PixelRay pr = make_ray(fc, x, y);
+    const size_t pix = (size_t)y * fc.width + x;
+
+    PixelState ps;
+    ps.T = 1.f;
+    ps.C[0] = ps.C[1] = ps.C[2] = 0.f;
+    ps.n_emit = 0;
+    ps.done = !inside;
+    float dL[3] = {0.f, 0.f, 0.f}, Cf[3] = {0.f, 0.f, 0.f};
+    if (BWD && inside) {
+        for (int c = 0; c < 3; c++) {
+            dL[c] = A.dL[c * npix + pix];
+            Cf[c] = A.Cfin[c * npix + pix];
+        }
+    }
+    uint32_t* rec_pos = (!BWD && A.emit_pos) ? A.emit_pos + (size_t)tile * A.emit_cap * kTilePix + tpix
+                                             : nullptr;
+    kb.init(ring + threadIdx.x, reinterpret_cast<uint32_t*>(ring) + CAP * kRasterThreads + threadIdx.x,
+            ring + 2 * CAP * kRasterThreads + threadIdx.x, list);
+    uint64_t lo = 0ull, horizon = ~0ull;
+    bool finished = ps.done;
+
+    auto emit_front = [&]() {
+        const float a = kb.front_a();
+        const float Tn = __fmul_rn(ps.T, __fsub_rn(1.f, a));
+        if (Tn < fc.T_min) {
+            ps.done = true;
+            return;
+        }
+        const uint32_t p = kb.front_p();
+        const uint32_t idx = __ldg(list + p);
+        const float col[3] = {__ldg(rgbp + 3 * (size_t)idx), __ldg(rgbp + 3 * (size_t)idx + 1),
+                              __ldg(rgbp + 3 * (size_t)idx + 2)};
+        const float wgt = __fmul_rn(a, ps.T);
+        if (!BWD) {
+            for (int c = 0; c < 3; c++) ps.C[c] = fmaf(wgt, col[c], ps.C[c]);
+            if (rec_pos) {
+                if (ps.n_emit < A.emit_cap) rec_pos[(size_t)ps.n_emit * kTilePix] = p;
+                else A.tile_overflow[tile] = 1;
+            }
+        } else {
+            float G = 0.f;
+            const float inv1ma = 1.f / (1.f - a);
+            for (int c = 0; c < 3; c++) {
+                ps.C[c] = fmaf(wgt, col[c], ps.C[c]);
+                const float S = Cf[c] - ps.C[c];
+                G += dL[c] * (ps.T * col[c] - S * inv1ma);
+            }
+            PairGrad g;
+            pair_grad<KMAX>(A, A.rec + (size_t)Rec<KMAX>::STRIDE * idx, idx, pr, G, g);
+            for (int c = 0; c < 3; c++) g.v[A_RGB + c] = dL[c] * wgt;
+            add_global(A, idx, g);
+        }
+        ps.T = Tn;
+        ps.n_emit++;
+    };
+
+    while (true) {   // passes over the list
+        bool pass_done = finished;
+        // chunk c covers list positions [32 c, 32 c + 32); lane l holds item 32 c + l
+        uint32_t idx_a = lane < L ? __ldg(list + lane) : 0u;
+        uint32_t key_a = lane < L ? __ldg(lkeys + lane) : 0u;
+        uint32_t idx_b = 32 + lane < L ? __ldg(list + 32 + lane) : 0u;
+        uint32_t key_b = 32 + lane < L ? __ldg(lkeys + 32 + lane) : 0u;
+        if ((uint32_t)lane < L)
+            for (int q = 0; q < HDR4; q++)
+                cp_async16(stage + lane * HDR4 + q, rec4 + (size_t)idx_a * STRIDE4 + q);
+        cp_async_commit();
+        for (uint32_t c0 = 0; c0 < L; c0 += 32) {
+            const int buf = (c0 >> 5) & 1;
+            // stage the next chunk's geometry, fetch the one after's entries
+            const uint32_t n1 = c0 + 32 + lane;
+            if (n1 < L)
+                for (int q = 0; q < HDR4; q++)
+                    cp_async16(stage + ((buf ^ 1) * 32 + lane) * HDR4 + q, rec4 + (size_t)idx_b * STRIDE4 + q);
+            cp_async_commit();
+            const uint32_t n2 = c0 + 64 + lane;
+            const uint32_t idx_c = n2 < L ? __ldg(list + n2) : 0u;
+            const uint32_t key_c = n2 < L ? __ldg(lkeys + n2) : 0u;
+            cp_async_wait_1();
+            __syncwarp();
+            const uint32_t cn = min(32u, L - c0);
+            for (uint32_t jj = 0; jj < cn; jj++) {
+                const uint32_t idx = __shfl_sync(0xffffffffu, idx_a, jj);
+                const uint32_t key = __shfl_sync(0xffffffffu, key_a, jj);
+                const uint32_t j = c0 + jj;
+                float h[HDR];
+                Geo gm;
+                bool geo = false;
+                const float4* sg = stage + (buf * 32 + jj) * HDR4;
+                if (!pass_done) {
+                    const float thr = fmaf((float)(key & qmask), dq.inv_scale, dq.zmin);
+                    // composite every buffered entry that no later item can precede
+                    while (!kb.empty() && kb.front_t() < thr) {
+                        emit_front();
+                        if (ps.done) break;
+                        kb.pop_front();
+                    }
+                    if (ps.done) pass_done = true;
+                    else if (horizon != ~0ull && thr > __uint_as_float((uint32_t)(horizon >> 32))) pass_done = true;
+                    if (!pass_done) {
+                        wc.evals++;
+#pragma unroll
+                        for (int q = 0; q < R_GEO4; q++) {
+                            const float4 v = sg[q];
+                            h[4 * q] = v.x; h[4 * q + 1] = v.y; h[4 * q + 2] = v.z; h[4 * q + 3] = v.w;
+                        }
+                        geo = eval_geometry(h, pr, fc.near_plane, gm);
+                    }
+                }
+                if (__any_sync(0xffffffffu, geo)) {
+                    if (geo) {
+#pragma unroll
+                        for (int q = R_GEO4; q < HDR4; q++) {
+                            const float4 v = sg[q];
+                            h[4 * q] = v.x; h[4 * q + 1] = v.y; h[4 * q + 2] = v.z; h[4 * q + 3] = v.w;
+                        }
+                        float a;
+                        if (eval_kernel<KMAX, false>(h, recp + (size_t)idx * (STRIDE4 * 4) + HDR, pr, gm,
+                                                     fc.alpha_min, fc.alpha_max, a)) {
+                            wc.contrib++;
+                            const uint64_t kk = key_of(gm.t, idx);
+                            if (kk >= lo && kk < horizon) {
+                                const uint64_t out = kb.insert(gm.t, j, idx, a);
+                                if (out != ~0ull) horizon = out;
+                            }
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+            idx_a = idx_b; key_a = key_b;
+            idx_b = idx_c; key_b = key_c;
+            if (__all_sync(0xffffffffu, pass_done)) break;
+        }
+        cp_async_wait_all();
+        __syncwarp();
+        // end of the list for this pass: composite what is left in order
+        while (!ps.done && !kb.empty()) {
+            emit_front();
+            if (ps.done) break;
+            kb.pop_front();
+        }
+        bool need = !ps.done && horizon != ~0ull;
+        if (need && wc.passes >= (unsigned long long)kMaxPasses) {
+            // every pass composites at least CAP entries, so this bound is
+            // never reached by a correct traversal; it only guards the loop
+            need = false;
+            if (A.status) atomicOr(A.status, 1 << DRK_ERR_CAPACITY);
+        }
+        if (need) {
+            lo = horizon;
+            horizon = ~0ull;
+            kb.clear();
+            wc.passes++;
+        }
+        finished = !need;
+        if (!__any_sync(0xffffffffu, need)) break;
+    }
+
+    if (!BWD && inside) {
+        for (int c = 0; c < 3; c++) outp[c * npix + pix] = fmaf(ps.T, fc.bg[c], ps.C[c]);
+        if (!batched && A.out_T) A.out_T[pix] = ps.T;
+        if (!batched && A.out_n) A.out_n[pix] = ps.n_emit;
+    }
+    if (!BWD && A.emit_n) A.emit_n[(size_t)tile * kTilePix + tpix] = inside ? ps.n_emit : 0;
+    wc.emit += (unsigned long long)ps.n_emit;
+    wc.max_emit = max(wc.max_emit, ps.n_emit);
+}
+
 // Forward traversal; with BWD it is the exact replay used by the backward of
-// tiles whose composited lists were not recorded in full.
+// tiles whose composited lists were not recorded in full; with BATCH it
+// renders every tile of a batch of frames in one launch (serving).
 //
 // Persistent warps.  The work unit is an 8 x 4 block of a tile (a task;
 // 8 per tile); each warp takes tasks from a global counter until none are
 // left and walks the tile's list on its own, so there is no block-wide
 // barrier anywhere.  List entries (primitive index, depth key) are fetched
 // 32 at a time with one coalesced load and broadcast by shuffle; the
-// geometry part of the next 32 records (the first 64 bytes of each) is
-// copied into the warp's shared-memory stage with cp.async one chunk ahead
-// of use; the kernel-stage fields are read through L1 only when some lane
-// of the warp passes the geometry stage.
-template <int KMAX, int CAP, bool BWD>
+// headers of the next 32 records are copied into the warp's shared-memory
+// stage with cp.async one chunk ahead of use; the kernel stage runs only
+// when some lane of the warp passes the geometry stage.  Tasks are taken
+// heaviest tile first (longest list), which keeps the tail short.
+template <int KMAX, int CAP, bool BWD, bool BATCH>
 __global__ void __launch_bounds__(kRasterThreads) raster_kernel(RasterArgs A) {
     constexpr int HDR = Rec<KMAX>::HDR;
     constexpr int STRIDE4 = Rec<KMAX>::STRIDE4;
     constexpr int kWarps = kRasterThreads / 32;
+    constexpr int HDR4 = HDR / 4;
     extern __shared__ float4 smem4[];
-    // [kWarps][2 chunks][32 items][R_GEO4] float4 staging, then the rings
+    // [kWarps][2 chunks][32 items][HDR4] float4 staging of record headers,
+    // then the rings
     float4* stage_all = smem4;
-    float* ring = reinterpret_cast<float*>(smem4 + kWarps * 2 * 32 * R_GEO4);
+    float* ring = reinterpret_cast<float*>(smem4 + kWarps * 2 * 32 * HDR4);
 
-    const FrameConst& fc = A.fc;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float4* stage = stage_all + warp * (2 * 32 * R_GEO4);
-    const DepthQuant dq = *A.dq;
-    const uint32_t qmask = (1u << dq.depth_bits) - 1u;
-    const float4* rec4 = reinterpret_cast<const float4*>(A.rec);
-    const size_t npix = (size_t)fc.width * fc.height;
-    const uint32_t n_tasks = (uint32_t)(fc.tiles_x * fc.tiles_y) * 8u;
-    unsigned long long c_evals = 0, c_emit = 0, c_passes = 0, c_contrib = 0;
-    int c_max_emit = 0;
+    float4* stage = stage_all + warp * (2 * 32 * HDR4);
+    const uint32_t n_tasks = BATCH ? (uint32_t)A.n_batch_tiles * 8u : (uint32_t)(A.fc.tiles_x * A.fc.tiles_y) * 8u;
+    WarpCounters wc;
 
     RingBuf<CAP, kRasterThreads> kb;
 
@@ -308,200 +515,34 @@ __global__ void __launch_bounds__(kRasterThreads) raster_kernel(RasterArgs A) {
         if (lane == 0) task = atomicAdd(A.task_counter, 1u);
         task = __shfl_sync(0xffffffffu, task, 0);
         if (task >= n_tasks) break;
-        const int tile = (int)(task >> 3), blk = (int)(task & 7u);
-        if (BWD && A.tile_overflow && A.tile_overflow[tile] == 0) continue;   // handled by the list kernel
-        const int tx = tile % fc.tiles_x, ty = tile / fc.tiles_x;
-        const int x = tx * kTile + (blk & 1) * 8 + (lane & 7);
-        const int y = ty * kTile + (blk >> 1) * 4 + (lane >> 3);
-        const int tpix = blk * 32 + lane;          // pixel slot within the tile
-        const bool inside = x < fc.width && y < fc.height;
-        const uint2 rg = A.ranges[tile];
-        const uint32_t L = rg.y - rg.x;
-        const uint32_t* list = A.vals + rg.x;
-        const uint32_t* lkeys = A.keys + rg.x;
-        const PixelRay pr = make_ray(fc, x, y);
-        const size_t pix = (size_t)y * fc.width + x;
-
-        PixelState ps;
-        ps.T = 1.f;
-        ps.C[0] = ps.C[1] = ps.C[2] = 0.f;
-        ps.n_emit = 0;
-        ps.done = !inside;
-        float dL[3] = {0.f, 0.f, 0.f}, Cf[3] = {0.f, 0.f, 0.f};
-        if (BWD && inside) {
-            for (int c = 0; c < 3; c++) {
-                dL[c] = A.dL[c * npix + pix];
-                Cf[c] = A.Cfin[c * npix + pix];
-            }
+        const int tile = A.tile_order ? (int)A.tile_order[task >> 3] : (int)(task >> 3);
+        if (BATCH) {
+            const FrameSlot& sl = A.slots[(uint32_t)tile >> 20];
+            run_task<KMAX, CAP, BWD>(A, sl.fc, sl.rec, sl.rgb, sl.vals, sl.keys, sl.ranges, sl.dq, sl.out_rgb, true,
+                                     tile & ((1 << 20) - 1), task, stage, ring, kb, wc);
+        } else {
+            run_task<KMAX, CAP, BWD>(A, A.fc, A.rec, A.rgb, A.vals, A.keys, A.ranges, A.dq, A.out_rgb, false, tile, task,
+                                     stage, ring, kb, wc);
         }
-        uint32_t* rec_pos = (!BWD && A.emit_pos) ? A.emit_pos + (size_t)tile * A.emit_cap * kTilePix + tpix
-                                                 : nullptr;
-        kb.init(ring + threadIdx.x, reinterpret_cast<uint32_t*>(ring) + CAP * kRasterThreads + threadIdx.x,
-                ring + 2 * CAP * kRasterThreads + threadIdx.x, list);
-        uint64_t lo = 0ull, horizon = ~0ull;
-        bool finished = ps.done;
-
-        auto emit_front = [&]() {
-            const float a = kb.front_a();
-            const float Tn = __fmul_rn(ps.T, __fsub_rn(1.f, a));
-            if (Tn < fc.T_min) {
-                ps.done = true;
-                return;
-            }
-            const uint32_t p = kb.front_p();
-            const uint32_t idx = __ldg(list + p);
-            const float col[3] = {__ldg(A.rgb + 3 * (size_t)idx), __ldg(A.rgb + 3 * (size_t)idx + 1),
-                                  __ldg(A.rgb + 3 * (size_t)idx + 2)};
-            const float wgt = __fmul_rn(a, ps.T);
-            if (!BWD) {
-                for (int c = 0; c < 3; c++) ps.C[c] = fmaf(wgt, col[c], ps.C[c]);
-                if (rec_pos) {
-                    if (ps.n_emit < A.emit_cap) rec_pos[(size_t)ps.n_emit * kTilePix] = p;
-                    else A.tile_overflow[tile] = 1;
-                }
-            } else {
-                float G = 0.f;
-                const float inv1ma = 1.f / (1.f - a);
-                for (int c = 0; c < 3; c++) {
-                    ps.C[c] = fmaf(wgt, col[c], ps.C[c]);
-                    const float S = Cf[c] - ps.C[c];
-                    G += dL[c] * (ps.T * col[c] - S * inv1ma);
-                }
-                PairGrad g;
-                pair_grad<KMAX>(A, A.rec + (size_t)Rec<KMAX>::STRIDE * idx, idx, pr, G, g);
-                for (int c = 0; c < 3; c++) g.v[A_RGB + c] = dL[c] * wgt;
-                add_global(A, idx, g);
-            }
-            ps.T = Tn;
-            ps.n_emit++;
-        };
-
-        while (true) {   // passes over the list
-            bool pass_done = finished;
-            // chunk c covers list positions [32 c, 32 c + 32); lane l holds item 32 c + l
-            uint32_t idx_a = lane < L ? __ldg(list + lane) : 0u;
-            uint32_t key_a = lane < L ? __ldg(lkeys + lane) : 0u;
-            uint32_t idx_b = 32 + lane < L ? __ldg(list + 32 + lane) : 0u;
-            uint32_t key_b = 32 + lane < L ? __ldg(lkeys + 32 + lane) : 0u;
-            if ((uint32_t)lane < L)
-                for (int q = 0; q < R_GEO4; q++)
-                    cp_async16(stage + lane * R_GEO4 + q, rec4 + (size_t)idx_a * STRIDE4 + q);
-            cp_async_commit();
-            for (uint32_t c0 = 0; c0 < L; c0 += 32) {
-                const int buf = (c0 >> 5) & 1;
-                // stage the next chunk's geometry, fetch the one after's entries
-                const uint32_t n1 = c0 + 32 + lane;
-                if (n1 < L)
-                    for (int q = 0; q < R_GEO4; q++)
-                        cp_async16(stage + ((buf ^ 1) * 32 + lane) * R_GEO4 + q, rec4 + (size_t)idx_b * STRIDE4 + q);
-                cp_async_commit();
-                const uint32_t n2 = c0 + 64 + lane;
-                const uint32_t idx_c = n2 < L ? __ldg(list + n2) : 0u;
-                const uint32_t key_c = n2 < L ? __ldg(lkeys + n2) : 0u;
-                cp_async_wait_1();
-                __syncwarp();
-                const uint32_t cn = min(32u, L - c0);
-                for (uint32_t jj = 0; jj < cn; jj++) {
-                    const uint32_t idx = __shfl_sync(0xffffffffu, idx_a, jj);
-                    const uint32_t key = __shfl_sync(0xffffffffu, key_a, jj);
-                    const uint32_t j = c0 + jj;
-                    float h[HDR];
-                    Geo gm;
-                    bool geo = false;
-                    if (!pass_done) {
-                        const float thr = fmaf((float)(key & qmask), dq.inv_scale, dq.zmin);
-                        // composite every buffered entry that no later item can precede
-                        while (!kb.empty() && kb.front_t() < thr) {
-                            emit_front();
-                            if (ps.done) break;
-                            kb.pop_front();
-                        }
-                        if (ps.done) pass_done = true;
-                        else if (horizon != ~0ull && thr > __uint_as_float((uint32_t)(horizon >> 32))) pass_done = true;
-                        if (!pass_done) {
-                            c_evals++;
-                            const float4* sg = stage + (buf * 32 + jj) * R_GEO4;
-#pragma unroll
-                            for (int q = 0; q < R_GEO4; q++) {
-                                const float4 v = sg[q];
-                                h[4 * q] = v.x; h[4 * q + 1] = v.y; h[4 * q + 2] = v.z; h[4 * q + 3] = v.w;
-                            }
-                            geo = eval_geometry(h, pr, fc.near_plane, gm);
-                        }
-                    }
-                    if (__any_sync(0xffffffffu, geo)) {
-                        if (geo) {
-                            load_head_rest<KMAX>(rec4 + (size_t)idx * STRIDE4, h);
-                            float a;
-                            if (eval_kernel<KMAX, false>(h, A.rec + (size_t)idx * (STRIDE4 * 4) + HDR, pr, gm,
-                                                         fc.alpha_min, fc.alpha_max, a)) {
-                                c_contrib++;
-                                const uint64_t kk = key_of(gm.t, idx);
-                                if (kk >= lo && kk < horizon) {
-                                    const uint64_t out = kb.insert(gm.t, j, idx, a);
-                                    if (out != ~0ull) horizon = out;
-                                }
-                            }
-                        }
-                    }
-                }
-                __syncwarp();
-                idx_a = idx_b; key_a = key_b;
-                idx_b = idx_c; key_b = key_c;
-                if (__all_sync(0xffffffffu, pass_done)) break;
-            }
-            cp_async_wait_all();
-            __syncwarp();
-            // end of the list for this pass: composite what is left in order
-            while (!ps.done && !kb.empty()) {
-                emit_front();
-                if (ps.done) break;
-                kb.pop_front();
-            }
-            bool need = !ps.done && horizon != ~0ull;
-            if (need && c_passes >= (unsigned long long)kMaxPasses) {
-                // every pass composites at least CAP entries, so this bound is
-                // never reached by a correct traversal; it only guards the loop
-                need = false;
-                if (A.status) atomicOr(A.status, 1 << DRK_ERR_CAPACITY);
-            }
-            if (need) {
-                lo = horizon;
-                horizon = ~0ull;
-                kb.clear();
-                c_passes++;
-            }
-            finished = !need;
-            if (!__any_sync(0xffffffffu, need)) break;
-        }
-
-        if (!BWD && inside) {
-            for (int c = 0; c < 3; c++) A.out_rgb[c * npix + pix] = fmaf(ps.T, fc.bg[c], ps.C[c]);
-            if (A.out_T) A.out_T[pix] = ps.T;
-            if (A.out_n) A.out_n[pix] = ps.n_emit;
-        }
-        if (!BWD && A.emit_n) A.emit_n[(size_t)tile * kTilePix + tpix] = inside ? ps.n_emit : 0;
-        c_emit += (unsigned long long)ps.n_emit;
-        c_max_emit = max(c_max_emit, ps.n_emit);
     }
     // counters: one atomic per warp
     if (A.counters) {
         for (int o = 16; o > 0; o >>= 1) {
-            c_evals += __shfl_down_sync(0xffffffffu, c_evals, o);
-            c_emit += __shfl_down_sync(0xffffffffu, c_emit, o);
-            c_passes += __shfl_down_sync(0xffffffffu, c_passes, o);
-            c_contrib += __shfl_down_sync(0xffffffffu, c_contrib, o);
+            wc.evals += __shfl_down_sync(0xffffffffu, wc.evals, o);
+            wc.emit += __shfl_down_sync(0xffffffffu, wc.emit, o);
+            wc.passes += __shfl_down_sync(0xffffffffu, wc.passes, o);
+            wc.contrib += __shfl_down_sync(0xffffffffu, wc.contrib, o);
         }
         if (lane == 0) {
-            atomicAdd(A.counters + 0, c_evals);
-            atomicAdd(A.counters + 1, c_emit);
-            atomicAdd(A.counters + 2, c_passes);
-            atomicAdd(A.counters + 5, c_contrib);
+            atomicAdd(A.counters + 0, wc.evals);
+            atomicAdd(A.counters + 1, wc.emit);
+            atomicAdd(A.counters + 2, wc.passes);
+            atomicAdd(A.counters + 5, wc.contrib);
         }
     }
     if (!BWD && A.emit_max) {
-        for (int o = 16; o > 0; o >>= 1) c_max_emit = max(c_max_emit, __shfl_down_sync(0xffffffffu, c_max_emit, o));
-        if (lane == 0) atomicMax(A.emit_max, c_max_emit);
+        for (int o = 16; o > 0; o >>= 1) wc.max_emit = max(wc.max_emit, __shfl_down_sync(0xffffffffu, wc.max_emit, o));
+        if (lane == 0) atomicMax(A.emit_max, wc.max_emit);
     }
 }
 
@@ -518,7 +559,7 @@ __global__ void __launch_bounds__(kTilePix) raster_backward_list_kernel(RasterAr
     __shared__ float acc[kWin * AS];
     __shared__ uint32_t s_min;
     const FrameConst& fc = A.fc;
-    const int tile = blockIdx.x;
+    const int tile = A.tile_order ? (int)A.tile_order[blockIdx.x] : (int)blockIdx.x;
     if (A.tile_overflow[tile] != 0) return;                     // replayed exactly instead
     const int tx = tile % fc.tiles_x, ty = tile / fc.tiles_x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -604,33 +645,53 @@ __global__ void __launch_bounds__(kTilePix) raster_backward_list_kernel(RasterAr
     }
 }
 
-template <int KMAX, int CAP, bool BWD>
-static void launch_raster_t(const RasterArgs& A, cudaStream_t st) {
+template <int KMAX, int CAP, bool BWD, bool BATCH>
+static void launch_raster_t(const RasterArgs& A, int n_tiles, cudaStream_t st) {
     constexpr int kWarps = kRasterThreads / 32;
-    const size_t smem = (size_t)kWarps * 2 * 32 * R_GEO4 * sizeof(float4) +
+    const size_t smem = (size_t)kWarps * 2 * 32 * (Rec<KMAX>::HDR / 4) * sizeof(float4) +
                         (size_t)3 * CAP * kRasterThreads * sizeof(float);
     static int grid = 0;   // per instantiation: resident blocks x SMs
     if (grid == 0) {
-        cudaFuncSetAttribute(raster_kernel<KMAX, CAP, BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(raster_kernel<KMAX, CAP, BWD, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raster_kernel<KMAX, CAP, BWD>, kRasterThreads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raster_kernel<KMAX, CAP, BWD, BATCH>, kRasterThreads,
+                                                      smem);
         grid = sms * (per_sm > 0 ? per_sm : 1);
     }
-    const int n_tasks = A.fc.tiles_x * A.fc.tiles_y * 8;
+    const int n_tasks = n_tiles * 8;
     const int blocks = std::min(grid, (n_tasks + kWarps - 1) / kWarps);
+    if (blocks <= 0) return;
     cudaMemsetAsync(A.task_counter, 0, sizeof(unsigned int), st);
-    raster_kernel<KMAX, CAP, BWD><<<blocks, kRasterThreads, smem, st>>>(A); note_launch();
+    raster_kernel<KMAX, CAP, BWD, BATCH><<<blocks, kRasterThreads, smem, st>>>(A); note_launch();
 }
 
 void launch_raster(const RasterArgs& A, int kmax, int cap, bool bwd, cudaStream_t st) {
-    if (A.fc.tiles_x * A.fc.tiles_y == 0) return;
-#define DRK_RASTER_CASE(KM, CP)                                   \
-    if (kmax == KM && cap == CP) {                                \
-        if (bwd) launch_raster_t<KM, CP, true>(A, st);            \
-        else launch_raster_t<KM, CP, false>(A, st);               \
-        return;                                                   \
+    const int n_tiles = A.fc.tiles_x * A.fc.tiles_y;
+    if (n_tiles == 0) return;
+#define DRK_RASTER_CASE(KM, CP)                                                   \
+    if (kmax == KM && cap == CP) {                                                \
+        if (bwd) launch_raster_t<KM, CP, true, false>(A, n_tiles, st);            \
+        else launch_raster_t<KM, CP, false, false>(A, n_tiles, st);               \
+        return;                                                                   \
+    }
+    DRK_RASTER_CASE(8, 8)
+    DRK_RASTER_CASE(8, 16)
+    DRK_RASTER_CASE(8, 32)
+    DRK_RASTER_CASE(16, 8)
+    DRK_RASTER_CASE(16, 16)
+    DRK_RASTER_CASE(16, 32)
+#undef DRK_RASTER_CASE
+}
+
+void launch_raster_batch(const RasterArgs& A, int kmax, int cap, cudaStream_t st) {
+    if (A.n_batch_tiles <= 0) return;
+#define DRK_RASTER_CASE(KM, CP)                                                        \
+    if (kmax == KM && cap == CP) {                                                     \
+        launch_raster_t<KM, CP, false, true>(A, A.n_batch_tiles, st);                  \
+        return;                                                                        \
     }
     DRK_RASTER_CASE(8, 8)
     DRK_RASTER_CASE(8, 16)

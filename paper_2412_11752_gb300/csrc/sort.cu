@@ -264,6 +264,31 @@ __global__ void tile_ranges_kernel(const uint32_t* __restrict__ keys, int64_t n,
     if (i == n - 1 || (keys[i + 1] >> depth_bits) != t) ranges[t].y = (uint32_t)(i + 1);
 }
 
+// key = 2^24 - 1 - min(list length, 2^24 - 1): ascending keys = longest first
+__global__ void tile_order_keys_kernel(const uint2* __restrict__ ranges, int n_tiles, uint32_t* __restrict__ keys,
+                                       uint32_t* __restrict__ vals) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tiles) return;
+    const uint2 r = ranges[t];
+    const uint32_t len = min(r.y - r.x, 0xffffffu);
+    keys[t] = 0xffffffu - len;
+    vals[t] = (uint32_t)t;
+}
+
+size_t tile_order_work_bytes(int n_tiles) {
+    return 4 * sizeof(uint32_t) * (size_t)n_tiles + radix_sort_scratch_bytes(n_tiles) + 64;
+}
+
+void launch_tile_order(const uint2* ranges, int n_tiles, uint32_t* order, void* work, cudaStream_t st) {
+    if (n_tiles <= 0) return;
+    uint32_t* keys = reinterpret_cast<uint32_t*>(work);
+    uint32_t* kalt = keys + n_tiles;
+    uint32_t* valt = kalt + n_tiles;
+    void* scr = reinterpret_cast<void*>((reinterpret_cast<uintptr_t>(valt + n_tiles) + 15) & ~uintptr_t(15));
+    tile_order_keys_kernel<<<(n_tiles + 255) / 256, 256, 0, st>>>(ranges, n_tiles, keys, order); note_launch();
+    radix_sort_pairs(keys, order, kalt, valt, n_tiles, 24, scr, st);
+}
+
 void launch_tile_ranges(const uint32_t* keys, int64_t n, int depth_bits, uint2* ranges, int n_tiles,
                         cudaStream_t st) {
     cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_tiles, st);

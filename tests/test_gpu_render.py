@@ -26,7 +26,7 @@ def render_gpu(drk, scene, cam, opt, **kw):
     return rgb.cpu().numpy(), T.cpu().numpy(), n.cpu().numpy(), st
 
 
-def check_full(drk, scene, cam, opt, max_excluded_frac=1e-2):
+def check_full(drk, scene, cam, opt, max_excluded_frac=3e-2):
     rgb, T, n, _ = render_gpu(drk, scene, cam, opt)
     ref = O.render(scene, cam, oracle_options(opt))
     err, nex = image_error(rgb, ref["rgb"], ref["flags"])
