@@ -4,6 +4,7 @@ forward + backward render (Sec. 4.4 pipeline and its reverse mode) of a
 100k-primitive, K = 8, SH-degree-3 scene at 1920 x 1080, synthetic data.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl drk|reference]
+    python bench.py --serve [--serve-requests R] [--serve-rate HZ] [--serve-batch B]
 
 One process per GPU (torchrun for N > 1).  The path does not shard: every
 rank renders its own replica of the workload ("replicas only"), value =
@@ -49,6 +50,13 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-pixels", type=int, default=1024, help="oracle sample size (pixels, fwd+bwd)")
+    ap.add_argument("--kbuf-capacity", type=int, default=16, choices=(8, 16, 32),
+                    help="per-pixel depth-order buffer entries (any value gives the same image)")
+    ap.add_argument("--serve", action="store_true",
+                    help="serving mode: Poisson request mix through drk_serve (batched vs one at a time)")
+    ap.add_argument("--serve-requests", type=int, default=160)
+    ap.add_argument("--serve-rate", type=float, default=0.0, help="arrivals per second (0 = all at once)")
+    ap.add_argument("--serve-batch", type=int, default=16)
     return ap.parse_args()
 
 
@@ -199,7 +207,7 @@ def run_drk(args):
     H, W = cam.height, cam.width
     ds = drk.DeviceScene.from_scene(scene, dev)
     target = torch.from_numpy(synth.target_image(H, W)).to(dev)
-    opt = drk.Options()
+    opt = drk.Options(kbuf_capacity=args.kbuf_capacity)
     ctx = drk.Context(local)
     out = dict(rgb=torch.empty((3, H, W), device=dev), T=None, n=None)
     inv_n = 1.0 / float(3 * H * W)
@@ -305,7 +313,7 @@ def run_drk(args):
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks,
                 "stages_ms": {k: v[0] / max(1, v[1]) for k, v in stage.items() if v[1]},
-                "counters": {k: stats[k] for k in ("n_pairs", "n_evals", "n_contrib_evals", "n_emitted",
+                "counters": {k: stats[k] for k in ("n_pairs", "n_evals", "n_geo_evals", "n_contrib_evals", "n_emitted",
                                                    "n_extra_passes", "n_visible")}}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -314,8 +322,61 @@ def run_drk(args):
     return 0
 
 
+def serve_run(D, torch, dscenes, reqs, max_batch: int, budget: int) -> dict:
+    """Replays (arrival_s, scene, camera) requests through one server; latency
+    = completion - arrival of each request, throughput over the whole run."""
+    outs = [torch.empty((3, c.height, c.width), device="cuda") for _, _, c in reqs]
+    torch.cuda.synchronize()
+    with D.Server(0, mem_budget=budget, max_batch=max_batch) as srv:
+        ids = [srv.add_scene(d) for d in dscenes]
+        # warm-up: four requests fill the server's memory pool
+        for _, sid, cam in reqs[:4]:
+            o = torch.empty((3, cam.height, cam.width), device="cuda")
+            srv.release(_wait_release(srv, srv.submit(ids[sid], cam, o)))
+        t0 = time.perf_counter()
+        tickets = []
+        for (arr, sid, cam), o in zip(reqs, outs):
+            dt = arr - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            tickets.append(srv.submit(ids[sid], cam, o))
+        tm = [srv.wait(t, 600000) for t in tickets]
+    bad = [t["status"] for t in tm if t["status"] != 0]
+    lat = np.array([t["end_ms"] - t["arrival_ms"] for t in tm])
+    span_ms = max(t["end_ms"] for t in tm) - min(t["arrival_ms"] for t in tm)
+    px = sum(c.width * c.height for _, _, c in reqs)
+    return {"max_batch": max_batch, "frames_per_s": len(reqs) / (span_ms / 1e3), "Mpix_per_s": px / (span_ms / 1e3) / 1e6,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_batch": float(np.mean([t["batch_size"] for t in tm])), "failed": len(bad)}
+
+
+def _wait_release(srv, tk):
+    srv.wait(tk, 600000)
+    return tk
+
+
+def run_serve(args):
+    import torch
+    from paper_2412_11752_gb300 import drk as D
+    D.lib()
+    scenes = synth.serve_scenes()
+    dscenes = [D.DeviceScene.from_scene(s, "cuda") for s in scenes]
+    reqs = synth.serve_requests(args.serve_requests, len(scenes), args.serve_rate)
+    budget = 64 << 30
+    res = {"metric": "serving throughput and latency, Poisson request mix", "impl": "drk-serve",
+           "data": "synthetic", "requests": len(reqs), "rate_hz": args.serve_rate,
+           "config": {"scenes": [s.n for s in scenes], "resolutions": list(synth.SERVE_RESOLUTIONS),
+                      "weights": list(synth.SERVE_RES_WEIGHTS), "mem_budget": budget}}
+    res["batched"] = serve_run(D, torch, dscenes, reqs, args.serve_batch, budget)
+    res["one_at_a_time"] = serve_run(D, torch, dscenes, reqs, 1, budget)
+    print(json.dumps(res), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.serve:
+        return run_serve(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_drk(args)

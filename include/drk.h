@@ -142,6 +142,9 @@ typedef struct {
                              buffer filled (exactness is kept) */
     int64_t n_tiles;
     int64_t n_contrib_evals;/* evaluations with alpha_tilde >= alpha_min */
+    int64_t n_geo_evals;  /* evaluations that passed the geometry stage (ray
+                             in front, point within the support radius or
+                             the filter's reach) */
     int32_t key_bits_depth;
     int32_t status;       /* device-side drk_status_t of the last render */
 } drk_stats_t;
@@ -220,6 +223,63 @@ drk_status_t drk_timing_read(drk_ctx_t *ctx, double *ms, int64_t *launches);
 /* Number of kernel launches the library has issued so far, process-wide
  * (host counter). */
 int64_t drk_launch_count(void);
+
+/* ------------------------------------------------------------------------
+ * Serving: a continuous-batching request loop over resident scenes.
+ *
+ * A server owns a worker thread, two CUDA streams and copies of its scenes
+ * in device memory.  drk_serve_submit queues a camera request; the worker
+ * forms a batch from the queued requests whenever one of its two streams is
+ * free (at most max_batch requests, while their estimated device memory
+ * fits in mem_budget beside the batch already running), renders every
+ * request of the batch with one preprocess/sort phase per request and ONE
+ * rasterizer launch over all tiles of all of them, and marks the tickets
+ * done when the batch's completion event fires.  Requests that arrive while
+ * a batch runs join the next batch, whose preprocess and sort overlap the
+ * running batch's rasterizer.  Each image is bit-identical to a
+ * drk_render of the same scene and camera (the batch does not change any
+ * pixel's arithmetic or order).  All requests of a batch share one basis
+ * count class (K <= 8 or K <= 16).  The rendering options are the server's.
+ */
+typedef struct drk_serve drk_serve_t;
+
+typedef struct {
+    double arrival_ms;    /* submit time, ms since the server was created */
+    double start_ms;      /* its batch was launched */
+    double end_ms;        /* its batch completed (worker saw the event) */
+    int32_t batch_size;   /* requests in its batch */
+    int32_t status;       /* drk_status_t of the request */
+} drk_serve_timing_t;
+
+/* device: CUDA ordinal; mem_budget: device bytes the in-flight batches may
+ * use (estimated before, counted after preprocess); max_batch: 1..64 (1
+ * renders one request at a time); opt: rendering options (copied). */
+drk_status_t drk_serve_create(int device, size_t mem_budget, int max_batch, const drk_options_t *opt,
+                              drk_serve_t **out);
+/* Copies the scene's parameter arrays (device pointers) into server-owned
+ * device memory; *scene_id receives its index. Synchronous. */
+drk_status_t drk_serve_add_scene(drk_serve_t *srv, const drk_params_t *params, int *scene_id);
+/* Queues a request; out_rgb is a caller-owned device buffer of
+ * 3 x H x W floats that must stay valid until the ticket is done.  Returns
+ * DRK_ERR_NOT_FOUND for an unknown scene, DRK_ERR_INVALID_ARG for a bad
+ * camera.  A request whose own estimate exceeds mem_budget completes with
+ * status DRK_ERR_OOM. */
+drk_status_t drk_serve_submit(drk_serve_t *srv, int scene_id, const drk_camera_t *cam, float *out_rgb,
+                              uint64_t *ticket);
+/* *done = 1 once the ticket's image is complete (or failed; see t->status).
+ * t may be NULL.  DRK_ERR_NOT_FOUND for an unknown or released ticket. */
+drk_status_t drk_serve_poll(drk_serve_t *srv, uint64_t ticket, int *done, drk_serve_timing_t *t);
+/* Waits up to timeout_ms for the ticket (DRK_ERR_TIMEOUT when it is not
+ * done by then).  Done tickets are kept until drk_serve_release. */
+drk_status_t drk_serve_wait(drk_serve_t *srv, uint64_t ticket, double timeout_ms, drk_serve_timing_t *t);
+drk_status_t drk_serve_release(drk_serve_t *srv, uint64_t ticket);
+/* Fault injection for tests: the n-th device allocation the worker makes
+ * from now on (0 = the next one) fails as if the device were out of
+ * memory; the affected request completes with DRK_ERR_OOM and the server
+ * continues.  n < 0 switches it off. */
+drk_status_t drk_serve_inject_alloc_failure(drk_serve_t *srv, int n);
+/* Drains the queue, joins the worker and frees everything. */
+drk_status_t drk_serve_destroy(drk_serve_t *srv);
 
 /* Message for the last failure on the calling thread ("" if none). */
 const char *drk_last_error(void);

@@ -18,11 +18,11 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libdrk.so")
-SOURCES = ["api.cu", "preprocess.cu", "sort.cu", "raster.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "preprocess.cu", "sort.cu", "raster.cu", "noalloc.cu", "serve.cu"]
 # The pair count and pair emission kernels must take identical culling
 # decisions; without FMA contraction both compile to the same arithmetic.
 FILE_FLAGS = {"preprocess.cu": ["-fmad=false"]}
-HEADERS = ["drk_common.cuh", "drk_internal.h"]
+HEADERS = ["drk_common.cuh", "drk_internal.h", "host.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]

@@ -586,6 +586,7 @@ drk_status_t drk_get_stats(drk_ctx_t* ctx, drk_stats_t* out) {
     out->n_extra_passes = (int64_t)c[2];
     out->n_visible = (int64_t)c[3];
     out->n_contrib_evals = (int64_t)c[5];
+    out->n_geo_evals = (int64_t)c[6];
     const int bits = (int)(c[4] & 0xffffffffu);
     out->status = DRK_OK;
     for (int b = 1; b < 8; b++)

@@ -114,6 +114,10 @@ void launch_tile_ranges(const uint32_t* keys, int64_t n, int depth_bits, uint2* 
 // followed by radix_sort_scratch_bytes(n_tiles) bytes
 size_t tile_order_work_bytes(int n_tiles);
 void launch_tile_order(const uint2* ranges, int n_tiles, uint32_t* order, void* work, cudaStream_t st);
+// batch tile order: writes n_tiles (key, slot << 20 | tile) entries; sorting
+// them by 24-bit key gives the heaviest-first order over all frames
+void launch_batch_order_keys(const uint2* ranges, int n_tiles, int slot, uint32_t* keys, uint32_t* vals,
+                             cudaStream_t st);
 void launch_raster(const RasterArgs& A, int kmax, int cap, bool bwd, cudaStream_t st);
 void launch_raster_backward_list(const RasterArgs& A, int kmax, cudaStream_t st);
 // batched forward over A.n_batch_tiles tiles of the frames in A.slots

@@ -74,6 +74,9 @@ struct Frame {
     int n_tiles, tile_bits, depth_bits, kmax;
 };
 Frame make_frame(const drk_params_t* p, const drk_camera_t* cam, const drk_options_t* opt);
+// floats per raster record / per culling bound of a primitive
+size_t rec_floats(int kmax);
+size_t bnd_floats(int kmax);
 drk_status_t check_launch();
 
 // Work of one frame between the two host phases.

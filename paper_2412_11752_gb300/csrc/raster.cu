@@ -276,7 +276,7 @@ __device__ __forceinline__ void add_global(const RasterArgs& A, uint32_t idx, co
 // ---------------------------------------------------------------------------
 // Counters a warp accumulates over its tasks.
 struct WarpCounters {
-    unsigned long long evals = 0, emit = 0, passes = 0, contrib = 0;
+    unsigned long long evals = 0, emit = 0, passes = 0, contrib = 0, geo = 0;
     int max_emit = 0;
 };
 
@@ -420,6 +420,7 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
                 }
                 if (__any_sync(0xffffffffu, geo)) {
                     if (geo) {
+                        wc.geo++;
 #pragma unroll
                         for (int q = R_GEO4; q < HDR4; q++) {
                             const float4 v = sg[q];
@@ -532,12 +533,14 @@ __global__ void __launch_bounds__(kRasterThreads) raster_kernel(RasterArgs A) {
             wc.emit += __shfl_down_sync(0xffffffffu, wc.emit, o);
             wc.passes += __shfl_down_sync(0xffffffffu, wc.passes, o);
             wc.contrib += __shfl_down_sync(0xffffffffu, wc.contrib, o);
+            wc.geo += __shfl_down_sync(0xffffffffu, wc.geo, o);
         }
         if (lane == 0) {
             atomicAdd(A.counters + 0, wc.evals);
             atomicAdd(A.counters + 1, wc.emit);
             atomicAdd(A.counters + 2, wc.passes);
             atomicAdd(A.counters + 5, wc.contrib);
+            atomicAdd(A.counters + 6, wc.geo);
         }
     }
     if (!BWD && A.emit_max) {

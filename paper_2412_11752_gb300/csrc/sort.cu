@@ -275,6 +275,23 @@ __global__ void tile_order_keys_kernel(const uint2* __restrict__ ranges, int n_t
     vals[t] = (uint32_t)t;
 }
 
+// keys/vals of one frame of a batch: key as above, value = slot << 20 | tile
+__global__ void batch_order_keys_kernel(const uint2* __restrict__ ranges, int n_tiles, uint32_t slot,
+                                        uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tiles) return;
+    const uint2 r = ranges[t];
+    keys[t] = 0xffffffu - min(r.y - r.x, 0xffffffu);
+    vals[t] = (slot << 20) | (uint32_t)t;
+}
+
+void launch_batch_order_keys(const uint2* ranges, int n_tiles, int slot, uint32_t* keys, uint32_t* vals,
+                             cudaStream_t st) {
+    if (n_tiles <= 0) return;
+    batch_order_keys_kernel<<<(n_tiles + 255) / 256, 256, 0, st>>>(ranges, n_tiles, (uint32_t)slot, keys, vals);
+    note_launch();
+}
+
 size_t tile_order_work_bytes(int n_tiles) {
     return 4 * sizeof(uint32_t) * (size_t)n_tiles + radix_sort_scratch_bytes(n_tiles) + 64;
 }

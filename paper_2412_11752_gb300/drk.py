@@ -58,11 +58,17 @@ class drk_image_t(C.Structure):
 class drk_stats_t(C.Structure):
     _fields_ = [("n_visible", C.c_int64), ("n_pairs", C.c_int64), ("n_evals", C.c_int64), ("n_emitted", C.c_int64),
                 ("n_extra_passes", C.c_int64), ("n_tiles", C.c_int64), ("n_contrib_evals", C.c_int64),
+                ("n_geo_evals", C.c_int64),
                 ("key_bits_depth", C.c_int32),
                 ("status", C.c_int32)]
 
 
 _lib = None
+
+
+class drk_serve_timing_t(C.Structure):
+    _fields_ = [("arrival_ms", C.c_double), ("start_ms", C.c_double), ("end_ms", C.c_double),
+                ("batch_size", C.c_int32), ("status", C.c_int32)]
 
 
 def library_path() -> str:
@@ -98,8 +104,18 @@ def lib():
         L.drk_timing_enable.argtypes = [vp, C.c_int]
         L.drk_timing_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
         L.drk_launch_count.restype = C.c_int64
+        L.drk_serve_create.argtypes = [C.c_int, C.c_size_t, C.c_int, C.POINTER(drk_options_t), C.POINTER(vp)]
+        L.drk_serve_add_scene.argtypes = [vp, C.POINTER(drk_params_t), C.POINTER(C.c_int)]
+        L.drk_serve_submit.argtypes = [vp, C.c_int, C.POINTER(drk_camera_t), _fp, C.POINTER(C.c_uint64)]
+        L.drk_serve_poll.argtypes = [vp, C.c_uint64, C.POINTER(C.c_int), C.POINTER(drk_serve_timing_t)]
+        L.drk_serve_wait.argtypes = [vp, C.c_uint64, C.c_double, C.POINTER(drk_serve_timing_t)]
+        L.drk_serve_release.argtypes = [vp, C.c_uint64]
+        L.drk_serve_inject_alloc_failure.argtypes = [vp, C.c_int]
+        L.drk_serve_destroy.argtypes = [vp]
         for f in ("drk_ctx_create", "drk_render", "drk_render_backward", "drk_get_stats", "drk_sort_pairs",
-                  "drk_timing_enable", "drk_timing_read"):
+                  "drk_timing_enable", "drk_timing_read", "drk_serve_create", "drk_serve_add_scene",
+                  "drk_serve_submit", "drk_serve_poll", "drk_serve_wait", "drk_serve_release",
+                  "drk_serve_inject_alloc_failure", "drk_serve_destroy"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -352,3 +368,75 @@ class DRKRender(torch.autograd.Function):
 
 def render_autograd(params: dict, cam, opt: Options | None = None, sh_degree: int = -1) -> torch.Tensor:
     return DRKRender.apply(cam, opt or Options(), sh_degree, *(params[k] for k in PARAM_NAMES))
+
+
+# ---------------------------------------------------------------------------
+class Server:
+    """drk_serve_t: continuous-batching render server over resident scenes.
+
+    submit() returns a ticket; the image is written into the caller's
+    (3, H, W) float32 CUDA tensor, which must stay alive until the ticket is
+    done.  wait()/poll() return the ticket's timing record as a dict.
+    """
+
+    def __init__(self, device: int = 0, mem_budget: int = 8 << 30, max_batch: int = 16,
+                 opt: Options | None = None):
+        self.opt = opt or Options()
+        oc = self.opt.to_c()
+        h = C.c_void_p()
+        _check(lib().drk_serve_create(int(device), int(mem_budget), int(max_batch), C.byref(oc), C.byref(h)))
+        self.handle = h
+        self.device = int(device)
+
+    def close(self):
+        if self.handle:
+            _check(lib().drk_serve_destroy(self.handle))
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_scene(self, scene: DeviceScene) -> int:
+        p = scene.to_c()
+        sid = C.c_int()
+        _check(lib().drk_serve_add_scene(self.handle, C.byref(p), C.byref(sid)))
+        return int(sid.value)
+
+    def submit(self, scene_id: int, cam, out_rgb: torch.Tensor) -> int:
+        if not (out_rgb.is_cuda and out_rgb.dtype == torch.float32 and out_rgb.is_contiguous()
+                and tuple(out_rgb.shape) == (3, int(cam.height), int(cam.width))):
+            raise DrkError(1, "out_rgb must be a contiguous float32 CUDA tensor of shape (3, H, W)")
+        cc = camera_c(cam)
+        tk = C.c_uint64()
+        _check(lib().drk_serve_submit(self.handle, int(scene_id), C.byref(cc), _fptr(out_rgb), C.byref(tk)))
+        return int(tk.value)
+
+    @staticmethod
+    def _timing(t: drk_serve_timing_t) -> dict:
+        return {f: getattr(t, f) for f, _ in drk_serve_timing_t._fields_}
+
+    def poll(self, ticket: int):
+        done = C.c_int()
+        t = drk_serve_timing_t()
+        _check(lib().drk_serve_poll(self.handle, C.c_uint64(ticket), C.byref(done), C.byref(t)))
+        return bool(done.value), self._timing(t)
+
+    def wait(self, ticket: int, timeout_ms: float = 60000.0) -> dict:
+        t = drk_serve_timing_t()
+        _check(lib().drk_serve_wait(self.handle, C.c_uint64(ticket), float(timeout_ms), C.byref(t)))
+        return self._timing(t)
+
+    def release(self, ticket: int) -> None:
+        _check(lib().drk_serve_release(self.handle, C.c_uint64(ticket)))
+
+    def inject_alloc_failure(self, n: int) -> None:
+        _check(lib().drk_serve_inject_alloc_failure(self.handle, int(n)))
