@@ -116,10 +116,16 @@ typedef struct {
     float near_plane;     /* default 0.2 */
     float bg[3];          /* background colour */
     int32_t cull_level;   /* DRK_CULL_*; default DRK_CULL_TILE */
-    int32_t kbuf_capacity;/* per-pixel depth-order buffer entries: 8, 16 or 32
+    int32_t kbuf_capacity;/* per-pixel depth-order heap slots in shared
+                             memory: 8, 16 or 32
                              (any value gives the same image; a small buffer
                              takes extra passes over the tile's list) */
-    int32_t reserved[6];  /* must be zero */
+    int32_t ovf_capacity; /* depth-order heap slots per pixel in global memory
+                             beyond the kbuf_capacity slots in shared memory
+                             (any value gives the same image): 0 = 2048
+                             (default), 1..2048, or -1 = none (a full heap
+                             then takes extra passes over the list) */
+    int32_t reserved[5];  /* must be zero */
 } drk_options_t;
 
 /* Fills *opt with the defaults listed above. */
@@ -142,6 +148,9 @@ typedef struct {
                              buffer filled (exactness is kept) */
     int64_t n_tiles;
     int64_t n_contrib_evals;/* evaluations with alpha_tilde >= alpha_min */
+    int64_t n_spills;     /* contributors pushed while the shared-memory
+                             part of their pixel's depth-order heap was full
+                             (they went to the overflow column) */
     int64_t n_geo_evals;  /* evaluations that passed the geometry stage (ray
                              in front, point within the support radius or
                              the filter's reach) */

@@ -10,6 +10,7 @@
 //   K5 raster                      -> image, final transmittance, counts
 // drk_render_backward replays K5 (K6) and then runs the per-primitive
 // backward (K7).
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -81,6 +82,8 @@ struct drk_ctx {
     DepthQuant* dq = nullptr;
     uint64_t* h_total = nullptr;              // pinned: pair total, largest recorded list
     int* emit_max = nullptr;                  // largest per-pixel contributor count so far
+    uint4* ovf = nullptr;                     // overflow columns of the raster's depth-order buffers
+    size_t ovf_bytes = 0;
     drk_stats_t last{};
 };
 
@@ -104,6 +107,40 @@ struct drk_state {
     int emit_cap = 0;
     std::vector<void*> allocs;
 };
+
+namespace {
+// Gives the raster launch for n_tiles tiles the context's overflow columns,
+// grown (stream-ordered) to one slot per warp of the launch.  If the pool
+// cannot provide them the raster runs without (extra list passes instead).
+void attach_ovf(drk_ctx* c, const drk_options_t* opt, int kmax, int cap, bool bwd, int n_tiles, cudaStream_t st,
+                RasterArgs& R) {
+    R.ovf = nullptr;
+    R.ovf_slots = 0;
+    R.ovf_cap = opt->ovf_capacity == 0 ? 2048 : std::max(0, (int)opt->ovf_capacity);
+    if (R.ovf_cap == 0) return;
+    const int slots = raster_slots(kmax, cap, bwd, false, n_tiles);
+    const size_t need = raster_ovf_bytes(slots);
+    if (need > c->ovf_bytes) {
+        if (c->ovf) cudaFreeAsync(c->ovf, st);
+        c->ovf = nullptr;
+        c->ovf_bytes = 0;
+        void* p = nullptr;
+        if (cudaMallocFromPoolAsync(&p, need, c->pool, st) == cudaSuccess) {
+            c->ovf = reinterpret_cast<uint4*>(p);
+            c->ovf_bytes = need;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    R.ovf = c->ovf;
+    R.ovf_slots = c->ovf ? (int)(c->ovf_bytes / raster_ovf_bytes(1)) : 0;
+}
+}  // namespace
+
+// device counters of a context: 0 evaluations, 1 composited, 2 extra
+// passes, 3 visible primitives, 4 status bits, 5 contributing evaluations,
+// 6 geometry passes, 7 raster task counter, 8 spills to overflow columns
+constexpr int kCtxCounters = 16;
 
 // per-pixel capacity of the recorded contributor lists (entries beyond it
 // send the tile to the exact replay in the backward); it grows with the
@@ -152,7 +189,9 @@ drk_status_t validate(const drk_params_t* p, const drk_camera_t* cam, const drk_
     if (opt->cull_level < 0 || opt->cull_level > 2) return fail(DRK_ERR_INVALID_ARG, "cull_level not in 0..2");
     if (opt->kbuf_capacity != 8 && opt->kbuf_capacity != 16 && opt->kbuf_capacity != 32)
         return fail(DRK_ERR_INVALID_ARG, "kbuf_capacity must be 8, 16 or 32");
-    for (int i = 0; i < 6; i++)
+    if (opt->ovf_capacity < -1 || opt->ovf_capacity > 2048)
+        return fail(DRK_ERR_INVALID_ARG, "ovf_capacity not in -1..2048");
+    for (int i = 0; i < 5; i++)
         if (opt->reserved[i] != 0) return fail(DRK_ERR_INVALID_ARG, "reserved option fields must be zero");
     for (int i = 0; i < 3; i++)
         if (!std::isfinite(opt->bg[i])) return fail(DRK_ERR_INVALID_ARG, "non-finite bg");
@@ -310,7 +349,7 @@ drk_status_t drk_ctx_create(int device, drk_ctx_t** out) {
     }
     uint64_t thr = ~0ull;
     cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &thr);
-    if (cudaMalloc(&c->counters, 8 * sizeof(unsigned long long)) != cudaSuccess ||
+    if (cudaMalloc(&c->counters, kCtxCounters * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc(&c->zmax_bits, sizeof(int)) != cudaSuccess || cudaMalloc(&c->dq, sizeof(DepthQuant)) != cudaSuccess ||
         cudaMalloc(&c->emit_max, sizeof(int)) != cudaSuccess || cudaMemset(c->emit_max, 0, sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&c->h_total, 2 * sizeof(uint64_t)) != cudaSuccess) {
@@ -326,6 +365,7 @@ void drk_ctx_destroy(drk_ctx_t* c) {
     if (!c) return;
     cudaSetDevice(c->device);
     if (c->last_stream) cudaStreamSynchronize(c->last_stream);
+    if (c->ovf) cudaFree(c->ovf);
     cudaFree(c->counters);
     cudaFree(c->zmax_bits);
     cudaFree(c->dq);
@@ -349,7 +389,7 @@ drk_status_t drk_render(drk_ctx_t* ctx, const drk_params_t* params, const drk_ca
     const int64_t n = params->n;
     Allocs al(ctx->pool, st);
     StageTimer& tm = ctx->timer;
-    DRK_CUDA(cudaMemsetAsync(ctx->counters, 0, 8 * sizeof(unsigned long long), st));
+    DRK_CUDA(cudaMemsetAsync(ctx->counters, 0, kCtxCounters * sizeof(unsigned long long), st));
 
     FrameWork w;
     if ((s = frame_phase_a(w, params, cam, opt, al, ctx->counters, reinterpret_cast<int*>(ctx->counters + 4),
@@ -397,6 +437,7 @@ drk_status_t drk_render(drk_ctx_t* ctx, const drk_params_t* params, const drk_ca
         if ((s = al.get(&R.tile_overflow, (size_t)F.n_tiles)) != DRK_OK) return s;
         DRK_CUDA(cudaMemsetAsync(R.tile_overflow, 0, sizeof(int32_t) * (size_t)F.n_tiles, st));
     }
+    attach_ovf(ctx, opt, F.kmax, opt->kbuf_capacity, false, F.n_tiles, st, R);
     cudaEvent_t ev = tm.begin(st);
     launch_raster(R, F.kmax, opt->kbuf_capacity, false, st);
     tm.end(ST_RASTER, ev, st);
@@ -503,6 +544,7 @@ drk_status_t drk_render_backward(drk_ctx_t* ctx, const drk_params_t* params, con
     R.emit_n = state->emit_n;
     R.tile_overflow = state->tile_overflow;
     R.emit_cap = state->emit_cap;
+    attach_ovf(ctx, opt, F.kmax, state->cap, true, F.n_tiles, st, R);
     StageTimer& tm = ctx->timer;
     cudaEvent_t ev = tm.begin(st);
     launch_raster_backward_list(R, F.kmax, st);          // tiles with complete lists
@@ -577,7 +619,7 @@ drk_status_t drk_sort_pairs(drk_ctx_t* ctx, uint32_t* keys, uint32_t* vals, int6
 drk_status_t drk_get_stats(drk_ctx_t* ctx, drk_stats_t* out) {
     if (!ctx || !out) return fail(DRK_ERR_INVALID_ARG, "null argument");
     DRK_CUDA(cudaSetDevice(ctx->device));
-    unsigned long long c[8];
+    unsigned long long c[kCtxCounters];
     DRK_CUDA(cudaMemcpyAsync(c, ctx->counters, sizeof(c), cudaMemcpyDeviceToHost, ctx->last_stream));
     DRK_CUDA(cudaStreamSynchronize(ctx->last_stream));
     *out = ctx->last;
@@ -587,6 +629,7 @@ drk_status_t drk_get_stats(drk_ctx_t* ctx, drk_stats_t* out) {
     out->n_visible = (int64_t)c[3];
     out->n_contrib_evals = (int64_t)c[5];
     out->n_geo_evals = (int64_t)c[6];
+    out->n_spills = (int64_t)c[8];
     const int bits = (int)(c[4] & 0xffffffffu);
     out->status = DRK_OK;
     for (int b = 1; b < 8; b++)

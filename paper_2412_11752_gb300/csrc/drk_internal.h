@@ -67,6 +67,12 @@ struct RasterArgs {
     int* status;                     // device status bits (may be null)
     unsigned int* task_counter;      // work counter of the persistent raster (zeroed per launch)
     const uint32_t* tile_order;      // tiles by descending list length (may be null)
+    // overflow columns of the depth-order buffers: ovf_slots warps x 2048
+    // entries x 32 lanes (raster_ovf_bytes); without them (null) a pixel
+    // whose buffer fills takes extra passes over the list instead
+    uint4* ovf;
+    int ovf_slots;
+    int ovf_cap;                     // entries used per column (<= 2048)
     // batched forward (serving): when slots != null the kernel renders
     // n_batch_tiles tiles taken from tile_order, each encoding (slot, tile),
     // and reads the frame of each task from slots[slot]
@@ -119,6 +125,10 @@ void launch_tile_order(const uint2* ranges, int n_tiles, uint32_t* order, void* 
 void launch_batch_order_keys(const uint2* ranges, int n_tiles, int slot, uint32_t* keys, uint32_t* vals,
                              cudaStream_t st);
 void launch_raster(const RasterArgs& A, int kmax, int cap, bool bwd, cudaStream_t st);
+// warps the raster launch for n_tiles tiles runs (one overflow slot each),
+// and the bytes of the overflow columns of `slots` warps
+int raster_slots(int kmax, int cap, bool bwd, bool batch, int n_tiles);
+size_t raster_ovf_bytes(int slots);
 void launch_raster_backward_list(const RasterArgs& A, int kmax, cudaStream_t st);
 // batched forward over A.n_batch_tiles tiles of the frames in A.slots
 void launch_raster_batch(const RasterArgs& A, int kmax, int cap, cudaStream_t st);

@@ -58,76 +58,142 @@ __device__ __forceinline__ uint64_t key_of(float t, uint32_t idx) {
     return ((uint64_t)__float_as_uint(t) << 32) | idx;
 }
 
+// Entries of a pixel's overflow column in global memory (16 B each).
+constexpr int kOvfCap = 2048;
+
 // Per-pixel depth-order buffer (the exact form of the paper's cache-sorting,
-// Sec. 4.4 and the supplementary algorithm) as a ring in shared memory:
-// entries (r_t, list position p, alpha), kept sorted ascending by
-// (r_t, primitive index) from `head`; the index of an entry is vals[p] of
-// the tile's list and is only fetched when two depths are exactly equal.
-// Element s of this pixel lives at [s * STRIDE] from its column base, so a
-// warp touching the same slot index hits 32 distinct banks.  Items arrive
-// nearly in depth order, so an insertion usually moves zero or one entry;
-// popping the front is O(1).
+// Sec. 4.4 and the supplementary algorithm): a binary min-heap of pending
+// contributors (r_t, list position p, alpha) ordered by (r_t, primitive
+// index).  Its first CAP slots live in shared memory (element s of this
+// pixel at [s * STRIDE] from its column base, so a warp touching the same
+// slot index hits 32 distinct banks); deeper slots continue in the pixel's
+// overflow column in global memory (lane-contiguous, L1/L2-resident for
+// the usual depths).  Items arrive nearly in depth order, so a push usually
+// stops at the first parent; a pop sifts down O(log n) levels.  The index
+// of an entry is vals[p] of the tile's list and is only fetched when two
+// depths are exactly equal.
 template <int CAP, int STRIDE>
-struct RingBuf {
-    static_assert((CAP & (CAP - 1)) == 0, "capacity must be a power of two");
+struct HeapBuf {
     float* st;
     uint32_t* sp;
     float* sa;
+    uint4* col;             // slots CAP .. CAP + ncol - 1 (may be null)
+    int ncol;
     const uint32_t* vals;   // the tile's list (primitive index of position p)
-    int head, n;
-    float ft;               // r_t of the front entry (+inf when empty), kept in a register
-    __device__ __forceinline__ void init(float* t, uint32_t* p, float* a, const uint32_t* list) {
-        st = t; sp = p; sa = a; vals = list; head = 0; n = 0; ft = __int_as_float(0x7f800000);
+    int n;
+    float ft;               // r_t of the root (+inf when empty), kept in a register
+    __device__ __forceinline__ void init(float* t, uint32_t* p, float* a, uint4* c, int nc, const uint32_t* list) {
+        st = t; sp = p; sa = a; col = c; ncol = c ? nc : 0; vals = list; n = 0; ft = __int_as_float(0x7f800000);
     }
+    __device__ __forceinline__ int capacity() const { return CAP + ncol; }
     __device__ __forceinline__ bool empty() const { return n == 0; }
+    __device__ __forceinline__ bool full() const { return n >= CAP + ncol; }
     __device__ __forceinline__ float front_t() const { return ft; }
-    __device__ __forceinline__ uint32_t front_p() const { return sp[head * STRIDE]; }
-    __device__ __forceinline__ float front_a() const { return sa[head * STRIDE]; }
-    __device__ __forceinline__ void pop_front() {
-        head = (head + 1) & (CAP - 1);
-        n--;
-        ft = n > 0 ? st[head * STRIDE] : __int_as_float(0x7f800000);
+    __device__ __forceinline__ uint32_t front_p() const { return sp[0]; }
+    __device__ __forceinline__ float front_a() const { return sa[0]; }
+    __device__ __forceinline__ void clear() { n = 0; ft = __int_as_float(0x7f800000); }
+    __device__ __forceinline__ void get(int i, float& t, uint32_t& p, float& a) const {
+        if (i < CAP) {
+            t = st[i * STRIDE]; p = sp[i * STRIDE]; a = sa[i * STRIDE];
+        } else {
+            const uint4 v = col[i - CAP];
+            t = __uint_as_float(v.x); p = v.y; a = __uint_as_float(v.z);
+        }
     }
-    __device__ __forceinline__ void clear() { head = 0; n = 0; ft = __int_as_float(0x7f800000); }
-    // (ts, index of ps) > (t, idx)?
-    __device__ __forceinline__ bool after(float ts, uint32_t ps, float t, uint32_t idx) const {
-        return ts > t || (ts == t && __ldg(vals + ps) > idx);
+    __device__ __forceinline__ void put(int i, float t, uint32_t p, float a) {
+        if (i < CAP) {
+            st[i * STRIDE] = t; sp[i * STRIDE] = p; sa[i * STRIDE] = a;
+        } else {
+            col[i - CAP] = make_uint4(__float_as_uint(t), p, __float_as_uint(a), 0u);
+        }
     }
-    // Inserts (t, p, a) whose primitive index is idx.  If the buffer was
-    // full, the largest key among the old entries and the new one does not
-    // stay; its (r_t, index) key is returned (~0 if every entry stays).
-    __device__ __forceinline__ uint64_t insert(float t, uint32_t p, uint32_t idx, float a) {
-        uint64_t out = ~0ull;
-        if (n == CAP) {
-            const int last = (head + CAP - 1) & (CAP - 1);
-            const float lt = st[last * STRIDE];
-            const uint32_t lp = sp[last * STRIDE];
-            if (after(lt, lp, t, idx)) {
-                out = key_of(lt, __ldg(vals + lp));
-                n--;
-            } else {
-                return key_of(t, idx);
+    // (t1, index of p1) < (t2, index of p2)?
+    __device__ __forceinline__ bool less(float t1, uint32_t p1, float t2, uint32_t p2) const {
+        return t1 < t2 || (t1 == t2 && __ldg(vals + p1) < __ldg(vals + p2));
+    }
+    // the root's key is at or after (t, idx)?
+    __device__ __forceinline__ bool front_at_or_after(float t, uint32_t idx) const {
+        return ft > t || (ft == t && __ldg(vals + sp[0]) >= idx);
+    }
+    // requires !full()
+    __device__ __forceinline__ void push(float t, uint32_t p, float a) {
+        int i = n++;
+        while (i > 0) {
+            const int up = (i - 1) >> 1;
+            float ut, ua;
+            uint32_t upp;
+            get(up, ut, upp, ua);
+            if (!less(t, p, ut, upp)) break;
+            put(i, ut, upp, ua);
+            i = up;
+        }
+        put(i, t, p, a);
+        if (i == 0) ft = t;
+    }
+    // Full heap: keeps the smallest keys among the old entries and the new
+    // one, so every pass composites at least one entry.  The largest key is
+    // on a leaf (slots n/2 .. n-1); it leaves unless the new entry is larger.
+    // Returns the key of the entry that does not stay.
+    __device__ __forceinline__ uint64_t push_full(float t, uint32_t p, float a) {
+        int m = n >> 1;
+        float mt, ma;
+        uint32_t mp;
+        get(m, mt, mp, ma);
+        for (int i = m + 1; i < n; i++) {
+            float it, ia;
+            uint32_t ip;
+            get(i, it, ip, ia);
+            if (less(mt, mp, it, ip)) {
+                m = i; mt = it; mp = ip; ma = ia;
             }
         }
-        int i = n;
+        if (!less(t, p, mt, mp)) return key_of(t, __ldg(vals + p));
+        const uint64_t out = key_of(mt, __ldg(vals + mp));
+        int i = m;
         while (i > 0) {
-            const int s = (head + i - 1) & (CAP - 1);
-            const float ts = st[s * STRIDE];
-            const uint32_t ps = sp[s * STRIDE];
-            if (!after(ts, ps, t, idx)) break;
-            const int d = (head + i) & (CAP - 1);
-            st[d * STRIDE] = ts;
-            sp[d * STRIDE] = ps;
-            sa[d * STRIDE] = sa[s * STRIDE];
-            i--;
+            const int up = (i - 1) >> 1;
+            float ut, ua;
+            uint32_t upp;
+            get(up, ut, upp, ua);
+            if (!less(t, p, ut, upp)) break;
+            put(i, ut, upp, ua);
+            i = up;
         }
-        const int d = (head + i) & (CAP - 1);
-        st[d * STRIDE] = t;
-        sp[d * STRIDE] = p;
-        sa[d * STRIDE] = a;
-        n++;
+        put(i, t, p, a);
         if (i == 0) ft = t;
         return out;
+    }
+    // removes the root; requires !empty()
+    __device__ __forceinline__ void pop() {
+        n--;
+        if (n == 0) {
+            ft = __int_as_float(0x7f800000);
+            return;
+        }
+        float lt, la;
+        uint32_t lp;
+        get(n, lt, lp, la);
+        int i = 0;
+        while (true) {
+            int c = 2 * i + 1;
+            if (c >= n) break;
+            float ct, ca;
+            uint32_t cp;
+            get(c, ct, cp, ca);
+            if (c + 1 < n) {
+                float dt, da;
+                uint32_t dp;
+                get(c + 1, dt, dp, da);
+                if (less(dt, dp, ct, cp)) {
+                    c = c + 1; ct = dt; cp = dp; ca = da;
+                }
+            }
+            if (!less(ct, cp, lt, lp)) break;
+            put(i, ct, cp, ca);
+            i = c;
+        }
+        put(i, lt, lp, la);
+        ft = st[0];
     }
 };
 
@@ -276,7 +342,7 @@ __device__ __forceinline__ void add_global(const RasterArgs& A, uint32_t idx, co
 // ---------------------------------------------------------------------------
 // Counters a warp accumulates over its tasks.
 struct WarpCounters {
-    unsigned long long evals = 0, emit = 0, passes = 0, contrib = 0, geo = 0;
+    unsigned long long evals = 0, emit = 0, passes = 0, contrib = 0, geo = 0, spills = 0;
     int max_emit = 0;
 };
 
@@ -287,8 +353,8 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
                                          const float* __restrict__ rgbp, const uint32_t* __restrict__ valsp,
                                          const uint32_t* __restrict__ keysp, const uint2* __restrict__ rangesp,
                                          const DepthQuant* __restrict__ dqp, float* __restrict__ outp, bool batched,
-                                         int tile, uint32_t task, float4* stage, float* ring,
-                                         RingBuf<CAP, kRasterThreads>& kb, WarpCounters& wc) {
+                                         int tile, uint32_t task, float4* stage, float* ring, uint4* ovf,
+                                         HeapBuf<CAP, kRasterThreads>& kb, WarpCounters& wc) {
     constexpr int HDR = Rec<KMAX>::HDR;
     constexpr int STRIDE4 = Rec<KMAX>::STRIDE4;
     constexpr int HDR4 = HDR / 4;
@@ -326,9 +392,28 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
     uint32_t* rec_pos = (!BWD && A.emit_pos) ? A.emit_pos + (size_t)tile * A.emit_cap * kTilePix + tpix
                                              : nullptr;
     kb.init(ring + threadIdx.x, reinterpret_cast<uint32_t*>(ring) + CAP * kRasterThreads + threadIdx.x,
-            ring + 2 * CAP * kRasterThreads + threadIdx.x, list);
-    uint64_t lo = 0ull, horizon = ~0ull;
+            ring + 2 * CAP * kRasterThreads + threadIdx.x, ovf, A.ovf_cap, list);
+    // Exact order with a bounded heap.  When a contributor finds the heap
+    // full, the largest key among the heap and the new entry is dropped;
+    // `lost` is the smallest dropped key (every key in the heap stays below
+    // it).  Keys at or after it are not composited in this pass: the list
+    // is walked again from the start for keys at or above it (an extra
+    // pass), which keeps the order exact for any capacity.
+    uint64_t lo = 0ull;        // keys below lo were composited in earlier passes
+    uint64_t lost = ~0ull;     // smallest dropped key
     bool finished = ps.done;
+
+    // a contributor with key kk at list position j
+    auto offer = [&](float t, uint32_t j, float a, uint64_t kk) {
+        if (kk < lo || kk >= lost) return;
+        if (!kb.full()) {
+            if (kb.n >= CAP) wc.spills++;
+            kb.push(t, j, a);
+        } else {
+            const uint64_t d = kb.push_full(t, j, a);
+            if (d < lost) lost = d;
+        }
+    };
 
     auto emit_front = [&]() {
         const float a = kb.front_a();
@@ -363,6 +448,21 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
         }
         ps.T = Tn;
         ps.n_emit++;
+    };
+
+    // composites every pending entry that no item at or after a list
+    // position with depth bound thr can precede; false when the next entry
+    // to composite is at or after the smallest dropped key (the pass ends)
+    auto drain = [&](float thr) -> bool {
+        const float lt = __uint_as_float((uint32_t)(lost >> 32));
+        while (!kb.empty() && kb.front_t() < thr) {
+            if (lost != ~0ull && kb.front_at_or_after(lt, (uint32_t)lost)) return false;
+            emit_front();
+            if (ps.done) return true;
+            kb.pop();
+        }
+        // nothing left below the smallest dropped key can come before thr
+        return !(lost != ~0ull && lt < thr);
     };
 
     while (true) {   // passes over the list
@@ -400,14 +500,8 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
                 const float4* sg = stage + (buf * 32 + jj) * HDR4;
                 if (!pass_done) {
                     const float thr = fmaf((float)(key & qmask), dq.inv_scale, dq.zmin);
-                    // composite every buffered entry that no later item can precede
-                    while (!kb.empty() && kb.front_t() < thr) {
-                        emit_front();
-                        if (ps.done) break;
-                        kb.pop_front();
-                    }
-                    if (ps.done) pass_done = true;
-                    else if (horizon != ~0ull && thr > __uint_as_float((uint32_t)(horizon >> 32))) pass_done = true;
+                    // composite every pending entry that no later item can precede
+                    if (!drain(thr) || ps.done) pass_done = true;
                     if (!pass_done) {
                         wc.evals++;
 #pragma unroll
@@ -430,11 +524,7 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
                         if (eval_kernel<KMAX, false>(h, recp + (size_t)idx * (STRIDE4 * 4) + HDR, pr, gm,
                                                      fc.alpha_min, fc.alpha_max, a)) {
                             wc.contrib++;
-                            const uint64_t kk = key_of(gm.t, idx);
-                            if (kk >= lo && kk < horizon) {
-                                const uint64_t out = kb.insert(gm.t, j, idx, a);
-                                if (out != ~0ull) horizon = out;
-                            }
+                            offer(gm.t, j, a, key_of(gm.t, idx));
                         }
                     }
                 }
@@ -447,12 +537,8 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
         cp_async_wait_all();
         __syncwarp();
         // end of the list for this pass: composite what is left in order
-        while (!ps.done && !kb.empty()) {
-            emit_front();
-            if (ps.done) break;
-            kb.pop_front();
-        }
-        bool need = !ps.done && horizon != ~0ull;
+        if (!ps.done) drain(__int_as_float(0x7f800000));
+        bool need = !ps.done && lost != ~0ull;
         if (need && wc.passes >= (unsigned long long)kMaxPasses) {
             // every pass composites at least CAP entries, so this bound is
             // never reached by a correct traversal; it only guards the loop
@@ -460,8 +546,8 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
             if (A.status) atomicOr(A.status, 1 << DRK_ERR_CAPACITY);
         }
         if (need) {
-            lo = horizon;
-            horizon = ~0ull;
+            lo = lost;
+            lost = ~0ull;
             kb.clear();
             wc.passes++;
         }
@@ -506,10 +592,16 @@ __global__ void __launch_bounds__(kRasterThreads) raster_kernel(RasterArgs A) {
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float4* stage = stage_all + warp * (2 * 32 * HDR4);
+    const int slot = blockIdx.x * kWarps + warp;
+    // lane-contiguous columns: a lane's deep heap levels are adjacent, and
+    // the footprint is what the pixels actually hold
+    uint4* ovf = (A.ovf && A.ovf_cap > 0 && slot < A.ovf_slots)
+                     ? A.ovf + ((size_t)slot * 32 + lane) * kOvfCap
+                     : nullptr;
     const uint32_t n_tasks = BATCH ? (uint32_t)A.n_batch_tiles * 8u : (uint32_t)(A.fc.tiles_x * A.fc.tiles_y) * 8u;
     WarpCounters wc;
 
-    RingBuf<CAP, kRasterThreads> kb;
+    HeapBuf<CAP, kRasterThreads> kb;
 
     while (true) {
         uint32_t task = 0;
@@ -520,10 +612,10 @@ __global__ void __launch_bounds__(kRasterThreads) raster_kernel(RasterArgs A) {
         if (BATCH) {
             const FrameSlot& sl = A.slots[(uint32_t)tile >> 20];
             run_task<KMAX, CAP, BWD>(A, sl.fc, sl.rec, sl.rgb, sl.vals, sl.keys, sl.ranges, sl.dq, sl.out_rgb, true,
-                                     tile & ((1 << 20) - 1), task, stage, ring, kb, wc);
+                                     tile & ((1 << 20) - 1), task, stage, ring, ovf, kb, wc);
         } else {
             run_task<KMAX, CAP, BWD>(A, A.fc, A.rec, A.rgb, A.vals, A.keys, A.ranges, A.dq, A.out_rgb, false, tile, task,
-                                     stage, ring, kb, wc);
+                                     stage, ring, ovf, kb, wc);
         }
     }
     // counters: one atomic per warp
@@ -534,6 +626,7 @@ __global__ void __launch_bounds__(kRasterThreads) raster_kernel(RasterArgs A) {
             wc.passes += __shfl_down_sync(0xffffffffu, wc.passes, o);
             wc.contrib += __shfl_down_sync(0xffffffffu, wc.contrib, o);
             wc.geo += __shfl_down_sync(0xffffffffu, wc.geo, o);
+            wc.spills += __shfl_down_sync(0xffffffffu, wc.spills, o);
         }
         if (lane == 0) {
             atomicAdd(A.counters + 0, wc.evals);
@@ -541,6 +634,7 @@ __global__ void __launch_bounds__(kRasterThreads) raster_kernel(RasterArgs A) {
             atomicAdd(A.counters + 2, wc.passes);
             atomicAdd(A.counters + 5, wc.contrib);
             atomicAdd(A.counters + 6, wc.geo);
+            atomicAdd(A.counters + 8, wc.spills);
         }
     }
     if (!BWD && A.emit_max) {
@@ -648,13 +742,18 @@ __global__ void __launch_bounds__(kTilePix) raster_backward_list_kernel(RasterAr
     }
 }
 
+template <int KMAX, int CAP>
+constexpr size_t raster_smem() {
+    return (size_t)(kRasterThreads / 32) * 2 * 32 * (Rec<KMAX>::HDR / 4) * sizeof(float4) +
+           (size_t)3 * CAP * kRasterThreads * sizeof(float);
+}
+
+// resident CTAs x SMs of one instantiation (computed once)
 template <int KMAX, int CAP, bool BWD, bool BATCH>
-static void launch_raster_t(const RasterArgs& A, int n_tiles, cudaStream_t st) {
-    constexpr int kWarps = kRasterThreads / 32;
-    const size_t smem = (size_t)kWarps * 2 * 32 * (Rec<KMAX>::HDR / 4) * sizeof(float4) +
-                        (size_t)3 * CAP * kRasterThreads * sizeof(float);
-    static int grid = 0;   // per instantiation: resident blocks x SMs
+static int raster_grid() {
+    static int grid = 0;
     if (grid == 0) {
+        constexpr size_t smem = raster_smem<KMAX, CAP>();
         cudaFuncSetAttribute(raster_kernel<KMAX, CAP, BWD, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
         int dev = 0, sms = 0, per_sm = 0;
@@ -664,12 +763,44 @@ static void launch_raster_t(const RasterArgs& A, int n_tiles, cudaStream_t st) {
                                                       smem);
         grid = sms * (per_sm > 0 ? per_sm : 1);
     }
+    return grid;
+}
+
+template <int KMAX, int CAP, bool BWD, bool BATCH>
+static int raster_blocks(int n_tiles) {
+    constexpr int kWarps = kRasterThreads / 32;
     const int n_tasks = n_tiles * 8;
-    const int blocks = std::min(grid, (n_tasks + kWarps - 1) / kWarps);
+    return std::min(raster_grid<KMAX, CAP, BWD, BATCH>(), (n_tasks + kWarps - 1) / kWarps);
+}
+
+template <int KMAX, int CAP, bool BWD, bool BATCH>
+static void launch_raster_t(const RasterArgs& A, int n_tiles, cudaStream_t st) {
+    const int blocks = raster_blocks<KMAX, CAP, BWD, BATCH>(n_tiles);
     if (blocks <= 0) return;
     cudaMemsetAsync(A.task_counter, 0, sizeof(unsigned int), st);
-    raster_kernel<KMAX, CAP, BWD, BATCH><<<blocks, kRasterThreads, smem, st>>>(A); note_launch();
+    raster_kernel<KMAX, CAP, BWD, BATCH><<<blocks, kRasterThreads, raster_smem<KMAX, CAP>(), st>>>(A); note_launch();
 }
+
+int raster_slots(int kmax, int cap, bool bwd, bool batch, int n_tiles) {
+    if (n_tiles <= 0) return 0;
+    constexpr int kWarps = kRasterThreads / 32;
+#define DRK_SLOTS_CASE(KM, CP)                                                                   \
+    if (kmax == KM && cap == CP) {                                                               \
+        if (batch) return kWarps * raster_blocks<KM, CP, false, true>(n_tiles);                  \
+        if (bwd) return kWarps * raster_blocks<KM, CP, true, false>(n_tiles);                    \
+        return kWarps * raster_blocks<KM, CP, false, false>(n_tiles);                            \
+    }
+    DRK_SLOTS_CASE(8, 8)
+    DRK_SLOTS_CASE(8, 16)
+    DRK_SLOTS_CASE(8, 32)
+    DRK_SLOTS_CASE(16, 8)
+    DRK_SLOTS_CASE(16, 16)
+    DRK_SLOTS_CASE(16, 32)
+#undef DRK_SLOTS_CASE
+    return 0;
+}
+
+size_t raster_ovf_bytes(int slots) { return (size_t)slots * kOvfCap * 32 * sizeof(uint4); }
 
 void launch_raster(const RasterArgs& A, int kmax, int cap, bool bwd, cudaStream_t st) {
     const int n_tiles = A.fc.tiles_x * A.fc.tiles_y;

@@ -13,6 +13,7 @@
 // and records a completion event.  The next batch's phases A/B run on the
 // other stream while this raster runs.  Each pixel's arithmetic and
 // compositing order are those of drk_render, so the images are identical.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -87,6 +88,8 @@ struct drk_serve {
     unsigned long long* d_counters[kStreams] = {nullptr, nullptr};   // max_batch x 8 each
     unsigned long long* h_counters[kStreams] = {nullptr, nullptr};   // pinned copy at batch end
     unsigned int* d_task[kStreams] = {nullptr, nullptr};
+    uint4* ovf[kStreams] = {nullptr, nullptr};           // raster overflow columns per stream
+    size_t ovf_bytes[kStreams] = {0, 0};
     cudaEvent_t ev_phase_a[kStreams] = {nullptr, nullptr};
     cudaEvent_t ev_done[kStreams] = {nullptr, nullptr};
     std::vector<std::unique_ptr<SceneDev>> scenes;
@@ -368,6 +371,24 @@ void run_batch(drk_serve* S, int s, std::vector<Item>& items, int* countdown, st
         R.tile_order = ovals;
         R.slots = S->d_slots[s];
         R.n_batch_tiles = (int)T;
+        // overflow columns of the depth-order buffers, kept per stream
+        R.ovf_cap = S->opt.ovf_capacity == 0 ? 2048 : std::max(0, (int)S->opt.ovf_capacity);
+        const size_t need =
+            R.ovf_cap == 0 ? 0 : raster_ovf_bytes(raster_slots(kmax, S->opt.kbuf_capacity, false, true, (int)T));
+        if (need > S->ovf_bytes[s]) {
+            if (S->ovf[s]) cudaFreeAsync(S->ovf[s], st);
+            S->ovf[s] = nullptr;
+            S->ovf_bytes[s] = 0;
+            void* q = nullptr;
+            if (cudaMallocFromPoolAsync(&q, need, S->pool, st) == cudaSuccess) {
+                S->ovf[s] = reinterpret_cast<uint4*>(q);
+                S->ovf_bytes[s] = need;
+            } else {
+                cudaGetLastError();   // the raster takes extra list passes instead
+            }
+        }
+        R.ovf = R.ovf_cap > 0 ? S->ovf[s] : nullptr;
+        R.ovf_slots = R.ovf ? (int)(S->ovf_bytes[s] / raster_ovf_bytes(1)) : 0;
         launch_raster_batch(R, kmax, S->opt.kbuf_capacity, st);
         bs = check_launch();
     }
@@ -437,6 +458,7 @@ void free_server(drk_serve* S) {
         cudaFree(S->d_slots[s]);
         cudaFree(S->d_counters[s]);
         cudaFree(S->d_task[s]);
+        if (S->ovf[s]) cudaFree(S->ovf[s]);
         if (S->ev_phase_a[s]) cudaEventDestroy(S->ev_phase_a[s]);
         if (S->ev_done[s]) cudaEventDestroy(S->ev_done[s]);
         if (S->streams[s]) cudaStreamDestroy(S->streams[s]);

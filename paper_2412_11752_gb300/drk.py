@@ -48,7 +48,8 @@ class drk_camera_t(C.Structure):
 class drk_options_t(C.Structure):
     _fields_ = [("alpha_min", C.c_float), ("T_min", C.c_float), ("alpha_max", C.c_float),
                 ("lowpass_sl", C.c_float), ("near_plane", C.c_float), ("bg", C.c_float * 3),
-                ("cull_level", C.c_int32), ("kbuf_capacity", C.c_int32), ("reserved", C.c_int32 * 6)]
+                ("cull_level", C.c_int32), ("kbuf_capacity", C.c_int32), ("ovf_capacity", C.c_int32),
+                ("reserved", C.c_int32 * 5)]
 
 
 class drk_image_t(C.Structure):
@@ -58,7 +59,7 @@ class drk_image_t(C.Structure):
 class drk_stats_t(C.Structure):
     _fields_ = [("n_visible", C.c_int64), ("n_pairs", C.c_int64), ("n_evals", C.c_int64), ("n_emitted", C.c_int64),
                 ("n_extra_passes", C.c_int64), ("n_tiles", C.c_int64), ("n_contrib_evals", C.c_int64),
-                ("n_geo_evals", C.c_int64),
+                ("n_spills", C.c_int64), ("n_geo_evals", C.c_int64),
                 ("key_bits_depth", C.c_int32),
                 ("status", C.c_int32)]
 
@@ -137,6 +138,7 @@ class Options:
     bg: tuple = (0.0, 0.0, 0.0)
     cull_level: int = CULL_TILE
     kbuf_capacity: int = 16
+    ovf_capacity: int = 0
 
     def to_c(self) -> drk_options_t:
         o = drk_options_t()
@@ -145,6 +147,7 @@ class Options:
         for i in range(3):
             o.bg[i] = float(self.bg[i])
         o.cull_level, o.kbuf_capacity = int(self.cull_level), int(self.kbuf_capacity)
+        o.ovf_capacity = int(self.ovf_capacity)
         return o
 
 

@@ -77,15 +77,21 @@ def test_cull_levels_bitwise_identical(drk, case):
 
 
 def test_buffer_capacity_does_not_change_the_image(drk):
-    # the depth-order buffer is exact for any capacity: a small one takes
-    # extra passes over the list, never a different order
+    # the depth-order heap is exact for any capacity: a small shared part
+    # spills to the overflow column or, without room there, takes extra
+    # passes over the list, never a different order
     scene = synth.scene_clustered(4000, 8, seed=2100, n_clusters=8)
     cam = synth.camera_front(96, 64)
-    r8, T8, n8, _ = render_gpu(drk, scene, cam, drk.Options(kbuf_capacity=8))
-    s8 = drk.default_context().stats()
-    r16, T16, n16, _ = render_gpu(drk, scene, cam, drk.Options(kbuf_capacity=16))
-    assert np.array_equal(r8, r16) and np.array_equal(T8, T16) and np.array_equal(n8, n16)
-    assert s8["n_extra_passes"] > 0
+    r16, T16, n16, _ = render_gpu(drk, scene, cam, drk.Options(kbuf_capacity=16, ovf_capacity=-1))
+    seen = {}
+    for cap, ovf in ((8, 0), (8, 3), (8, -1), (32, 0), (16, 1)):
+        r, T, n, _ = render_gpu(drk, scene, cam, drk.Options(kbuf_capacity=cap, ovf_capacity=ovf))
+        st = drk.default_context().stats()
+        assert np.array_equal(r, r16) and np.array_equal(T, T16) and np.array_equal(n, n16), (cap, ovf)
+        seen[(cap, ovf)] = (st["n_spills"], st["n_extra_passes"])
+    assert seen[(8, 0)][0] > 0 and seen[(8, 0)][1] == 0      # spills, no extra pass
+    assert seen[(8, 3)][0] > 0 and seen[(8, 3)][1] > 0       # column too small: both
+    assert seen[(8, -1)][0] == 0 and seen[(8, -1)][1] > 0    # no column: passes only
 
 
 def test_gaussian_special_case_k4(drk):
