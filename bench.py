@@ -314,7 +314,7 @@ def run_drk(args):
                 "clocks": clocks,
                 "stages_ms": {k: v[0] / max(1, v[1]) for k, v in stage.items() if v[1]},
                 "counters": {k: stats[k] for k in ("n_pairs", "n_evals", "n_geo_evals", "n_contrib_evals", "n_emitted",
-                                                   "n_spills",
+                                                   "n_spills", "n_replay_evals",
                                                    "n_extra_passes", "n_visible")}}
         print(json.dumps(line), flush=True)
     if world > 1:

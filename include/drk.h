@@ -151,6 +151,9 @@ typedef struct {
     int64_t n_spills;     /* contributors pushed while the shared-memory
                              part of their pixel's depth-order heap was full
                              (they went to the overflow column) */
+    int64_t n_replay_evals;/* evaluations made by the exact replay of the
+                             last drk_render_backward (tiles whose recorded
+                             lists did not fit) */
     int64_t n_geo_evals;  /* evaluations that passed the geometry stage (ray
                              in front, point within the support radius or
                              the filter's reach) */

@@ -81,7 +81,7 @@ struct drk_ctx {
     int* zmax_bits = nullptr;                 // counters[4] holds the device status bits
     DepthQuant* dq = nullptr;
     uint64_t* h_total = nullptr;              // pinned: pair total, largest recorded list
-    int* emit_max = nullptr;                  // largest per-pixel contributor count so far
+    unsigned int* emit_ctr = nullptr;         // list chunks the last recorded forward took
     uint4* ovf = nullptr;                     // overflow columns of the raster's depth-order buffers
     size_t ovf_bytes = 0;
     drk_stats_t last{};
@@ -101,10 +101,10 @@ struct drk_state {
     uint32_t* tile_order = nullptr;
     DepthQuant* dq = nullptr;
     float* Cfin = nullptr;
-    uint32_t* emit_pos = nullptr;
+    uint32_t* emit_pool = nullptr;
+    uint32_t* emit_hdr = nullptr;
     int32_t* emit_n = nullptr;
     int32_t* tile_overflow = nullptr;
-    int emit_cap = 0;
     std::vector<void*> allocs;
 };
 
@@ -139,14 +139,11 @@ void attach_ovf(drk_ctx* c, const drk_options_t* opt, int kmax, int cap, bool bw
 
 // device counters of a context: 0 evaluations, 1 composited, 2 extra
 // passes, 3 visible primitives, 4 status bits, 5 contributing evaluations,
-// 6 geometry passes, 7 raster task counter, 8 spills to overflow columns
-constexpr int kCtxCounters = 16;
+// 6 geometry passes, 7 raster task counter, 8 spills to overflow columns;
+// 16.. the same for the exact replay of the last backward
+constexpr int kCtxCounters = 32;
+constexpr int kBwdCounters = 16;
 
-// per-pixel capacity of the recorded contributor lists (entries beyond it
-// send the tile to the exact replay in the backward); it grows with the
-// largest list seen on the context
-constexpr int kEmitCap = 256;
-constexpr int kEmitCapMax = 4096;
 
 namespace drk {
 
@@ -351,7 +348,8 @@ drk_status_t drk_ctx_create(int device, drk_ctx_t** out) {
     cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &thr);
     if (cudaMalloc(&c->counters, kCtxCounters * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc(&c->zmax_bits, sizeof(int)) != cudaSuccess || cudaMalloc(&c->dq, sizeof(DepthQuant)) != cudaSuccess ||
-        cudaMalloc(&c->emit_max, sizeof(int)) != cudaSuccess || cudaMemset(c->emit_max, 0, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&c->emit_ctr, sizeof(unsigned int)) != cudaSuccess ||
+        cudaMemset(c->emit_ctr, 0, sizeof(unsigned int)) != cudaSuccess ||
         cudaMallocHost(&c->h_total, 2 * sizeof(uint64_t)) != cudaSuccess) {
         cudaGetLastError();
         drk_ctx_destroy(c);
@@ -370,7 +368,7 @@ void drk_ctx_destroy(drk_ctx_t* c) {
     cudaFree(c->zmax_bits);
     cudaFree(c->dq);
     if (c->h_total) cudaFreeHost(c->h_total);
-    cudaFree(c->emit_max);
+    cudaFree(c->emit_ctr);
     c->timer.destroy();
     if (c->pool) cudaMemPoolDestroy(c->pool);
     delete c;
@@ -389,7 +387,7 @@ drk_status_t drk_render(drk_ctx_t* ctx, const drk_params_t* params, const drk_ca
     const int64_t n = params->n;
     Allocs al(ctx->pool, st);
     StageTimer& tm = ctx->timer;
-    DRK_CUDA(cudaMemsetAsync(ctx->counters, 0, kCtxCounters * sizeof(unsigned long long), st));
+    DRK_CUDA(cudaMemsetAsync(ctx->counters, 0, kBwdCounters * sizeof(unsigned long long), st));
 
     FrameWork w;
     if ((s = frame_phase_a(w, params, cam, opt, al, ctx->counters, reinterpret_cast<int*>(ctx->counters + 4),
@@ -397,7 +395,7 @@ drk_status_t drk_render(drk_ctx_t* ctx, const drk_params_t* params, const drk_ca
         return s;
     if (state) {
         ctx->h_total[1] = 0;
-        DRK_CUDA(cudaMemcpyAsync(ctx->h_total + 1, ctx->emit_max, sizeof(int), cudaMemcpyDeviceToHost, st));
+        DRK_CUDA(cudaMemcpyAsync(ctx->h_total + 1, ctx->emit_ctr, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
     }
     DRK_CUDA(cudaStreamSynchronize(st));   // the pair total sizes the sort
     w.P = (int64_t)ctx->h_total[0];
@@ -424,15 +422,21 @@ drk_status_t drk_render(drk_ctx_t* ctx, const drk_params_t* params, const drk_ca
     R.out_n = out->n_emitted;
     R.p = *params;
     if (state) {
-        // the backward walks these per-pixel contributor lists
-        // capacity: the largest list seen so far on this context, with a
-        // quarter of headroom, as a power of two in [kEmitCap, kEmitCapMax]
-        const int64_t seen = (int64_t)(int)(ctx->h_total[1] & 0xffffffffu);
-        int cap = kEmitCap;
-        while (cap < kEmitCapMax && cap < seen + seen / 4 + 1) cap *= 2;
-        R.emit_cap = cap;
-        R.emit_max = ctx->emit_max;
-        if ((s = al.get(&R.emit_pos, (size_t)F.n_tiles * cap * kTilePix)) != DRK_OK) return s;
+        // the backward walks these per-pixel contributor lists; the chunk
+        // pool is sized from the chunks the previous recorded forward on
+        // this context took (a quarter of headroom), else 8 chunks (256
+        // contributors per pixel) per block; a list that does not fit sends
+        // its tile to the exact replay
+        const uint64_t blocks = (uint64_t)F.n_tiles * 8;
+        const uint64_t prev = ctx->h_total[1] & 0xffffffffu;
+        uint64_t chunks = prev > 0 ? prev + prev / 4 + blocks : 8 * blocks;
+        chunks = std::min<uint64_t>(chunks, 0xfffffff0u);
+        R.emit_pool_chunks = (uint32_t)chunks;
+        R.emit_ctr = ctx->emit_ctr;
+        if ((s = al.get(&R.emit_pool, (size_t)chunks * kEmitChunkWords)) != DRK_OK) return s;
+        if ((s = al.get(&R.emit_hdr, (size_t)blocks * kEmitChunks)) != DRK_OK) return s;
+        DRK_CUDA(cudaMemsetAsync(R.emit_hdr, 0xff, sizeof(uint32_t) * (size_t)blocks * kEmitChunks, st));
+        DRK_CUDA(cudaMemsetAsync(ctx->emit_ctr, 0, sizeof(unsigned int), st));
         if ((s = al.get(&R.emit_n, (size_t)F.n_tiles * kTilePix)) != DRK_OK) return s;
         if ((s = al.get(&R.tile_overflow, (size_t)F.n_tiles)) != DRK_OK) return s;
         DRK_CUDA(cudaMemsetAsync(R.tile_overflow, 0, sizeof(int32_t) * (size_t)F.n_tiles, st));
@@ -469,10 +473,10 @@ drk_status_t drk_render(drk_ctx_t* ctx, const drk_params_t* params, const drk_ca
         S->ranges = w.ranges;
         S->tile_order = w.tile_order;
         S->dq = A.dq;
-        S->emit_pos = R.emit_pos;
+        S->emit_pool = R.emit_pool;
+        S->emit_hdr = R.emit_hdr;
         S->emit_n = R.emit_n;
         S->tile_overflow = R.tile_overflow;
-        S->emit_cap = R.emit_cap;
         const size_t npix = (size_t)cam->width * cam->height;
         float* cf = nullptr;
         if ((s = al.get(&cf, 3 * npix)) != DRK_OK) {
@@ -532,7 +536,8 @@ drk_status_t drk_render_backward(drk_ctx_t* ctx, const drk_params_t* params, con
     R.ranges = state->ranges;
     R.tile_order = state->tile_order;
     R.dq = state->dq;
-    R.counters = nullptr;
+    R.counters = ctx->counters + kBwdCounters;
+    DRK_CUDA(cudaMemsetAsync(R.counters, 0, 8 * sizeof(unsigned long long), st));
     R.status = reinterpret_cast<int*>(ctx->counters + 4);
     R.task_counter = reinterpret_cast<unsigned int*>(ctx->counters + 7);
     R.p = *params;
@@ -540,16 +545,18 @@ drk_status_t drk_render_backward(drk_ctx_t* ctx, const drk_params_t* params, con
     R.Cfin = state->Cfin;
     R.gtmp = gtmp;
     R.grads = *grads;
-    R.emit_pos = state->emit_pos;
+    R.emit_pool = state->emit_pool;
+    R.emit_hdr = state->emit_hdr;
     R.emit_n = state->emit_n;
     R.tile_overflow = state->tile_overflow;
-    R.emit_cap = state->emit_cap;
     attach_ovf(ctx, opt, F.kmax, state->cap, true, F.n_tiles, st, R);
     StageTimer& tm = ctx->timer;
     cudaEvent_t ev = tm.begin(st);
     launch_raster_backward_list(R, F.kmax, st);          // tiles with complete lists
-    launch_raster(R, F.kmax, state->cap, true, st);      // exact replay of the others
     tm.end(ST_RASTER_BWD, ev, st);
+    ev = tm.begin(st);
+    launch_raster(R, F.kmax, state->cap, true, st);      // exact replay of the others
+    tm.end(ST_REPLAY, ev, st);
 
     PreArgs A;
     std::memset(&A, 0, sizeof(A));
@@ -630,6 +637,7 @@ drk_status_t drk_get_stats(drk_ctx_t* ctx, drk_stats_t* out) {
     out->n_contrib_evals = (int64_t)c[5];
     out->n_geo_evals = (int64_t)c[6];
     out->n_spills = (int64_t)c[8];
+    out->n_replay_evals = (int64_t)c[kBwdCounters + 0];
     const int bits = (int)(c[4] & 0xffffffffu);
     out->status = DRK_OK;
     for (int b = 1; b < 8; b++)

@@ -82,15 +82,20 @@ struct RasterArgs {
     float* out_rgb;
     float* out_T;
     int32_t* out_n;
-    // contributor lists recorded by the forward for the backward (may be null):
-    // emit_pos[(tile * emit_cap + s) * kTilePix + thread] = list position of
-    // the s-th composited contributor; emit_n[tile * kTilePix + thread] =
-    // count; tile_overflow[tile] != 0 if some pixel had more than emit_cap
-    uint32_t* emit_pos;
+    // contributor lists recorded by the forward for the backward (may be
+    // null).  The list position of the s-th composited contributor of lane
+    // `lane` of block `blk` of `tile` is
+    //   emit_pool[((c * 32) + (s % 32)) * 32 + lane],
+    //   c = emit_hdr[(tile * 8 + blk) * kEmitChunks + s / 32]
+    // (chunks of 32 slots x 32 lanes taken from the pool on demand);
+    // emit_n[tile * kTilePix + blk * 32 + lane] = count; tile_overflow[tile]
+    // != 0 if a list did not fit (the backward replays that tile exactly)
+    uint32_t* emit_pool;
+    uint32_t* emit_hdr;              // filled with kEmitEmpty before the forward
+    unsigned int* emit_ctr;          // chunks taken (zeroed before the forward)
+    uint32_t emit_pool_chunks;
     int32_t* emit_n;
     int32_t* tile_overflow;
-    int emit_cap;
-    int* emit_max;                   // running maximum of per-pixel counts (sizes later lists)
     // backward
     drk_params_t p;
     const float* dL;
@@ -98,6 +103,11 @@ struct RasterArgs {
     float* gtmp;                     // n x G_STRIDE
     drk_params_grad_t grads;
 };
+
+// chunked contributor lists (see RasterArgs)
+constexpr int kEmitChunks = 256;                 // chunks per 8 x 4 block: 8192 contributors per pixel
+constexpr uint32_t kEmitEmpty = 0xffffffffu;
+constexpr size_t kEmitChunkWords = 32 * 32;
 
 // host-side count of kernel launches made by the library (all threads)
 void note_launch();

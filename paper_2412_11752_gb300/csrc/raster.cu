@@ -280,15 +280,16 @@ __device__ __forceinline__ void grad_from_info(const RasterArgs& A, const float*
         const float wy = sec[S_M01] * sa + sec[S_M11] * sb;
         dL_du += d_r1 * wx;
         dL_dv += d_r1 * wy;
-        const float tk = sec[S_TH];
-        const float tk1 = (k + 1 == K) ? kTwoPi : r[R_TH + k];
-        float snk, csk, snk1, csk1;
-        sincosf(tk, &snk, &csk);
-        sincosf(tk1, &snk1, &csk1);
-        ds_k += d_r1 * (-e.a) * (wx * csk + wy * snk);
-        dth_k += d_r1 * (-e.a) * sk * (-wx * snk + wy * csk);
-        ds_k1 += d_r1 * (-e.b) * (wx * csk1 + wy * snk1);
-        dth_k1 += d_r1 * (-e.b) * sk1 * (-wx * snk1 + wy * csk1);
+        // the basis vectors e_k = s_k (cos theta'_k, sin theta'_k) and e_k1
+        // are the columns of Minv^-1
+        const float m00 = sec[S_M00], m01 = sec[S_M01], m10 = sec[S_M10], m11 = sec[S_M11];
+        const float idet = 1.f / (m00 * m11 - m01 * m10);
+        const float ekx = m11 * idet, eky = -m10 * idet;
+        const float e1x = -m01 * idet, e1y = m00 * idet;
+        ds_k += d_r1 * (-e.a) * (wx * ekx + wy * eky) / sk;
+        dth_k += d_r1 * (-e.a) * (wy * ekx - wx * eky);
+        ds_k1 += d_r1 * (-e.b) * (wx * e1x + wy * e1y) / sk1;
+        dth_k1 += d_r1 * (-e.b) * (wy * e1x - wx * e1y);
         out.k = k;
         out.k1 = k1;
         out.ds_k = ds_k;
@@ -339,11 +340,24 @@ __device__ __forceinline__ void add_global(const RasterArgs& A, uint32_t idx, co
     if (g.has_k1 && g.dth_k1 != 0.f) atomicAdd(A.grads.theta + base + g.k + 1, g.dth_k1);
 }
 
+// Chunk of an 8 x 4 block's contributor lists (slots 32k .. 32k + 31 of all
+// its lanes): taken from the pool by the first lane that needs it.  Lanes
+// that race for the same chunk agree through the compare-and-swap (the
+// loser's chunk stays unused); no lane waits for another.  Returns
+// kEmitEmpty when the pool is exhausted.
+__device__ __forceinline__ uint32_t take_chunk(const RasterArgs& A, uint32_t* hdr) {
+    uint32_t c = *reinterpret_cast<volatile uint32_t*>(hdr);
+    if (c != kEmitEmpty) return c;
+    const uint32_t cand = atomicAdd(A.emit_ctr, 1u);
+    if (cand >= A.emit_pool_chunks) return kEmitEmpty;
+    const uint32_t old = atomicCAS(hdr, kEmitEmpty, cand);
+    return old == kEmitEmpty ? cand : old;
+}
+
 // ---------------------------------------------------------------------------
 // Counters a warp accumulates over its tasks.
 struct WarpCounters {
     unsigned long long evals = 0, emit = 0, passes = 0, contrib = 0, geo = 0, spills = 0;
-    int max_emit = 0;
 };
 
 // One task of the forward (or replay) traversal: the 8 x 4 block `blk` of
@@ -389,8 +403,10 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
             Cf[c] = A.Cfin[c * npix + pix];
         }
     }
-    uint32_t* rec_pos = (!BWD && A.emit_pos) ? A.emit_pos + (size_t)tile * A.emit_cap * kTilePix + tpix
-                                             : nullptr;
+    // contributor list of this pixel for the backward (chunks of 32 slots)
+    const bool rec_list = !BWD && A.emit_pool != nullptr;
+    uint32_t* const chunk_hdr = rec_list ? A.emit_hdr + ((size_t)tile * 8 + blk) * kEmitChunks : nullptr;
+    uint32_t cur_chunk = kEmitEmpty;
     kb.init(ring + threadIdx.x, reinterpret_cast<uint32_t*>(ring) + CAP * kRasterThreads + threadIdx.x,
             ring + 2 * CAP * kRasterThreads + threadIdx.x, ovf, A.ovf_cap, list);
     // Exact order with a bounded heap.  When a contributor finds the heap
@@ -429,9 +445,14 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
         const float wgt = __fmul_rn(a, ps.T);
         if (!BWD) {
             for (int c = 0; c < 3; c++) ps.C[c] = fmaf(wgt, col[c], ps.C[c]);
-            if (rec_pos) {
-                if (ps.n_emit < A.emit_cap) rec_pos[(size_t)ps.n_emit * kTilePix] = p;
-                else A.tile_overflow[tile] = 1;
+            if (rec_list) {
+                const int sl = ps.n_emit;
+                if ((sl & 31) == 0)
+                    cur_chunk = sl < kEmitChunks * 32 ? take_chunk(A, chunk_hdr + (sl >> 5)) : kEmitEmpty;
+                if (cur_chunk != kEmitEmpty)
+                    A.emit_pool[((size_t)cur_chunk * 32 + (sl & 31)) * 32 + lane] = p;
+                else
+                    A.tile_overflow[tile] = 1;   // exact replay in the backward
             }
         } else {
             float G = 0.f;
@@ -562,7 +583,6 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
     }
     if (!BWD && A.emit_n) A.emit_n[(size_t)tile * kTilePix + tpix] = inside ? ps.n_emit : 0;
     wc.emit += (unsigned long long)ps.n_emit;
-    wc.max_emit = max(wc.max_emit, ps.n_emit);
 }
 
 // Forward traversal; with BWD it is the exact replay used by the backward of
@@ -637,10 +657,14 @@ __global__ void __launch_bounds__(kRasterThreads) raster_kernel(RasterArgs A) {
             atomicAdd(A.counters + 8, wc.spills);
         }
     }
-    if (!BWD && A.emit_max) {
-        for (int o = 16; o > 0; o >>= 1) wc.max_emit = max(wc.max_emit, __shfl_down_sync(0xffffffffu, wc.max_emit, o));
-        if (lane == 0) atomicMax(A.emit_max, wc.max_emit);
-    }
+
+}
+
+// Sum of v over all 32 lanes (every lane of the warp calls it).
+__device__ __forceinline__ float warp_sum32(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
 }
 
 // ---------------------------------------------------------------------------
@@ -669,7 +693,12 @@ __global__ void __launch_bounds__(kTilePix) raster_backward_list_kernel(RasterAr
     const size_t npix = (size_t)fc.width * fc.height;
     const size_t pix = (size_t)y * fc.width + x;
     const int n = inside ? A.emit_n[(size_t)tile * kTilePix + threadIdx.x] : 0;
-    const uint32_t* pos = A.emit_pos + (size_t)tile * A.emit_cap * kTilePix + threadIdx.x;
+    const uint32_t* hdr = A.emit_hdr + ((size_t)tile * 8 + warp) * kEmitChunks;
+    uint32_t chunk = n > 0 ? hdr[0] : kEmitEmpty;
+    auto position = [&](int sl) -> uint32_t {
+        if ((sl & 31) == 0) chunk = hdr[sl >> 5];
+        return A.emit_pool[((size_t)chunk * 32 + (sl & 31)) * 32 + lane];
+    };
     float dL[3] = {0.f, 0.f, 0.f}, Cf[3] = {0.f, 0.f, 0.f};
     if (inside) {
         for (int c = 0; c < 3; c++) {
@@ -679,7 +708,7 @@ __global__ void __launch_bounds__(kTilePix) raster_backward_list_kernel(RasterAr
     }
     float T = 1.f, P[3] = {0.f, 0.f, 0.f};
     int s = 0;
-    uint32_t next = n > 0 ? pos[0] : 0xffffffffu;
+    uint32_t next = n > 0 ? position(0) : 0xffffffffu;
     const int K = A.K;
     while (true) {
         if (threadIdx.x == 0) s_min = 0xffffffffu;
@@ -710,6 +739,31 @@ __global__ void __launch_bounds__(kTilePix) raster_backward_list_kernel(RasterAr
             for (int c = 0; c < 3; c++) g.v[A_RGB + c] = dL[c] * wgt;
             if (p >= w0) {
                 float* slot = acc + (size_t)(p - w0) * AS;
+                // neighbouring pixels usually composite the same primitive at
+                // the same step: when the whole warp works on one list
+                // position, sum in registers and let lane 0 add (the sector
+                // terms too when every lane is in the same sector)
+                const unsigned act = __activemask();
+                if (act == 0xffffffffu && __match_any_sync(act, p) == act) {
+#pragma unroll
+                    for (int j = 0; j < A_NFIX; j++) {
+                        const float v = warp_sum32(g.v[j]);
+                        g.v[j] = lane == 0 ? v : 0.f;
+                    }
+                    // every lane takes part in every shuffle (no short-circuit)
+                    const int k0 = __shfl_sync(act, g.k, 0);
+                    const int hk0 = __shfl_sync(act, (int)g.has_k, 0);
+                    const int hk10 = __shfl_sync(act, (int)g.has_k1, 0);
+                    const bool same_sector = g.k == k0 && (int)g.has_k == hk0 && (int)g.has_k1 == hk10;
+                    if (__all_sync(act, same_sector)) {
+                        const float a0 = warp_sum32(g.ds_k), a1 = warp_sum32(g.ds_k1);
+                        const float a2 = warp_sum32(g.dth_k), a3 = warp_sum32(g.dth_k1);
+                        g.ds_k = lane == 0 ? a0 : 0.f;
+                        g.ds_k1 = lane == 0 ? a1 : 0.f;
+                        g.dth_k = lane == 0 ? a2 : 0.f;
+                        g.dth_k1 = lane == 0 ? a3 : 0.f;
+                    }
+                }
 #pragma unroll
                 for (int j = 0; j < A_NFIX; j++)
                     if (g.v[j] != 0.f) atomicAdd(slot + j, g.v[j]);
@@ -722,7 +776,7 @@ __global__ void __launch_bounds__(kTilePix) raster_backward_list_kernel(RasterAr
             }
             T = __fmul_rn(T, __fsub_rn(1.f, a));
             s++;
-            next = s < n ? pos[(size_t)s * kTilePix] : 0xffffffffu;
+            next = s < n ? position(s) : 0xffffffffu;
         }
         __syncthreads();
         // flush the window: one global atomic per non-zero component

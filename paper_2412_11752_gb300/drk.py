@@ -59,7 +59,7 @@ class drk_image_t(C.Structure):
 class drk_stats_t(C.Structure):
     _fields_ = [("n_visible", C.c_int64), ("n_pairs", C.c_int64), ("n_evals", C.c_int64), ("n_emitted", C.c_int64),
                 ("n_extra_passes", C.c_int64), ("n_tiles", C.c_int64), ("n_contrib_evals", C.c_int64),
-                ("n_spills", C.c_int64), ("n_geo_evals", C.c_int64),
+                ("n_spills", C.c_int64), ("n_replay_evals", C.c_int64), ("n_geo_evals", C.c_int64),
                 ("key_bits_depth", C.c_int32),
                 ("status", C.c_int32)]
 
@@ -214,7 +214,7 @@ class Context:
         return {name: (ms[i], cnt[i]) for i, name in enumerate(STAGES)}
 
 
-STAGES = ("preprocess", "emit", "sort", "raster", "raster_bwd", "preprocess_bwd", "unused6", "unused7")
+STAGES = ("preprocess", "emit", "sort", "raster", "raster_bwd", "preprocess_bwd", "replay_bwd", "unused7")
 
 
 def launch_count() -> int:
