@@ -112,6 +112,31 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+RASTER_SOURCES = ("paper_2412_11752_gb300/csrc/raster.cu", "paper_2412_11752_gb300/csrc/drk_common.cuh",
+                  "paper_2412_11752_gb300/csrc/drk_internal.h")
+
+
+def raster_traffic(workload: str):
+    """DRAM bytes of one forward raster launch from the committed ncu summary
+    of this workload, or None if there is none or the raster sources changed
+    since it was captured (the summary records their hash)."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", f"raster_fwd_dram_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"source hash \| `([0-9a-f]+)`", text)
+    t = re.search(r"traffic per launch \| ([0-9.]+) GB", text)
+    if not m or not t:
+        return None
+    h = hashlib.sha256()
+    for f in RASTER_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return float(t.group(1)) * 1e9 if h.hexdigest()[:16] == m.group(1) else None
+
+
 def measured_peaks() -> dict:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -262,11 +287,15 @@ def run_drk(args):
     if fwd_ms >= bwd_ms:
         dom, dom_ms, ops = "raster_fwd", fwd_ms, stats["n_evals"] * OPS_PER_EVAL
     else:
-        dom, dom_ms, ops = "raster_bwd", bwd_ms, stats["n_evals"] * OPS_PER_EVAL + stats["n_emitted"] * OPS_PER_EMIT_BWD
+        # the list kernel re-evaluates each composited pair and chains its gradient
+        dom, dom_ms, ops = "raster_bwd", bwd_ms, stats["n_emitted"] * (OPS_PER_EVAL + OPS_PER_EMIT_BWD)
     achieved = ops / (dom_ms / 1e3) / 1e12
+    sm_load = float(clocks.get("sm_mhz") or smax)
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tops, "unit": "Top/s",
-                "frac": achieved / peak_tops, "traffic": None,
-                "peak_basis": f"{sms} SMs x 128 FP32 lanes x {smax:.0f} MHz (max SM clock, MEASURED_PEAKS.json)"}
+                "frac": achieved / peak_tops, "traffic": raster_traffic(args.workload) if dom == "raster_fwd" else None,
+                "peak_basis": f"{sms} SMs x 128 FP32 lanes x {smax:.0f} MHz (max SM clock, MEASURED_PEAKS.json)",
+                "frac_at_load_clock": achieved / (sms * 128 * sm_load * 1e6 / 1e12),
+                "load_clock_mhz": sm_load}
 
     # ---- end to end through the public API with host buffers
     e2e = None
