@@ -511,19 +511,25 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
             cp_async_wait_1();
             __syncwarp();
             const uint32_t cn = min(32u, L - c0);
+            // Composite, once per chunk and with every lane together, each
+            // pending entry that no item of this chunk or later can precede
+            // (the chunk's first bound is the smallest).  Compositing later
+            // than possible never changes the order; a pixel that finishes
+            // inside the chunk only evaluates a few items more.
+            const uint32_t key0 = __shfl_sync(0xffffffffu, key_a, 0);
+            if (!pass_done) {
+                const float thr0 = fmaf((float)(key0 & qmask), dq.inv_scale, dq.zmin);
+                if (!drain(thr0) || ps.done) pass_done = true;
+            }
             for (uint32_t jj = 0; jj < cn; jj++) {
                 const uint32_t idx = __shfl_sync(0xffffffffu, idx_a, jj);
-                const uint32_t key = __shfl_sync(0xffffffffu, key_a, jj);
                 const uint32_t j = c0 + jj;
                 float h[HDR];
                 Geo gm;
                 bool geo = false;
                 const float4* sg = stage + (buf * 32 + jj) * HDR4;
                 if (!pass_done) {
-                    const float thr = fmaf((float)(key & qmask), dq.inv_scale, dq.zmin);
-                    // composite every pending entry that no later item can precede
-                    if (!drain(thr) || ps.done) pass_done = true;
-                    if (!pass_done) {
+                    {
                         wc.evals++;
 #pragma unroll
                         for (int q = 0; q < R_GEO4; q++) {
@@ -599,14 +605,13 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
 // when some lane of the warp passes the geometry stage.  Tasks are taken
 // heaviest tile first (longest list), which keeps the tail short.
 template <int KMAX, int CAP, bool BWD, bool BATCH>
-__global__ void __launch_bounds__(kRasterThreads) raster_kernel(RasterArgs A) {
+__global__ void __launch_bounds__(kRasterThreads, 4) raster_kernel(RasterArgs A) {
     constexpr int HDR = Rec<KMAX>::HDR;
-    constexpr int STRIDE4 = Rec<KMAX>::STRIDE4;
     constexpr int kWarps = kRasterThreads / 32;
     constexpr int HDR4 = HDR / 4;
     extern __shared__ float4 smem4[];
     // [kWarps][2 chunks][32 items][HDR4] float4 staging of record headers,
-    // then the rings
+    // then the shared part of the depth-order heaps
     float4* stage_all = smem4;
     float* ring = reinterpret_cast<float*>(smem4 + kWarps * 2 * 32 * HDR4);
 
