@@ -80,8 +80,8 @@ struct drk_ctx {
     unsigned long long* counters = nullptr;   // evals, emitted, extra passes, visible
     int* zmax_bits = nullptr;                 // counters[4] holds the device status bits
     DepthQuant* dq = nullptr;
-    uint64_t* h_total = nullptr;              // pinned: pair total, largest recorded list
-    unsigned int* emit_ctr = nullptr;         // list chunks the last recorded forward took
+    uint64_t* h_total = nullptr;              // pinned: pair total, record chunks of the last forward, backward record chunks
+    unsigned int* rec_ctr = nullptr;          // record chunks the last recording forward took
     uint4* ovf = nullptr;                     // overflow columns of the raster's depth-order buffers
     size_t ovf_bytes = 0;
     drk_stats_t last{};
@@ -101,9 +101,11 @@ struct drk_state {
     uint32_t* tile_order = nullptr;
     DepthQuant* dq = nullptr;
     float* Cfin = nullptr;
-    uint32_t* emit_pool = nullptr;
-    uint32_t* emit_hdr = nullptr;
-    int32_t* emit_n = nullptr;
+    uint32_t* rec_key = nullptr;
+    uint32_t* rec_pix = nullptr;
+    float4* rec_tp = nullptr;
+    uint32_t rec_cap = 0;
+    unsigned int* rec_chunks = nullptr;       // device: chunks this forward took
     int32_t* tile_overflow = nullptr;
     std::vector<void*> allocs;
 };
@@ -348,9 +350,9 @@ drk_status_t drk_ctx_create(int device, drk_ctx_t** out) {
     cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &thr);
     if (cudaMalloc(&c->counters, kCtxCounters * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc(&c->zmax_bits, sizeof(int)) != cudaSuccess || cudaMalloc(&c->dq, sizeof(DepthQuant)) != cudaSuccess ||
-        cudaMalloc(&c->emit_ctr, sizeof(unsigned int)) != cudaSuccess ||
-        cudaMemset(c->emit_ctr, 0, sizeof(unsigned int)) != cudaSuccess ||
-        cudaMallocHost(&c->h_total, 2 * sizeof(uint64_t)) != cudaSuccess) {
+        cudaMalloc(&c->rec_ctr, sizeof(unsigned int)) != cudaSuccess ||
+        cudaMemset(c->rec_ctr, 0, sizeof(unsigned int)) != cudaSuccess ||
+        cudaMallocHost(&c->h_total, 4 * sizeof(uint64_t)) != cudaSuccess) {
         cudaGetLastError();
         drk_ctx_destroy(c);
         return fail(DRK_ERR_OOM, "context buffers");
@@ -368,7 +370,7 @@ void drk_ctx_destroy(drk_ctx_t* c) {
     cudaFree(c->zmax_bits);
     cudaFree(c->dq);
     if (c->h_total) cudaFreeHost(c->h_total);
-    cudaFree(c->emit_ctr);
+    cudaFree(c->rec_ctr);
     c->timer.destroy();
     if (c->pool) cudaMemPoolDestroy(c->pool);
     delete c;
@@ -395,7 +397,7 @@ drk_status_t drk_render(drk_ctx_t* ctx, const drk_params_t* params, const drk_ca
         return s;
     if (state) {
         ctx->h_total[1] = 0;
-        DRK_CUDA(cudaMemcpyAsync(ctx->h_total + 1, ctx->emit_ctr, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+        DRK_CUDA(cudaMemcpyAsync(ctx->h_total + 1, ctx->rec_ctr, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
     }
     DRK_CUDA(cudaStreamSynchronize(st));   // the pair total sizes the sort
     w.P = (int64_t)ctx->h_total[0];
@@ -422,22 +424,23 @@ drk_status_t drk_render(drk_ctx_t* ctx, const drk_params_t* params, const drk_ca
     R.out_n = out->n_emitted;
     R.p = *params;
     if (state) {
-        // the backward walks these per-pixel contributor lists; the chunk
-        // pool is sized from the chunks the previous recorded forward on
-        // this context took (a quarter of headroom), else 8 chunks (256
-        // contributors per pixel) per block; a list that does not fit sends
-        // its tile to the exact replay
-        const uint64_t blocks = (uint64_t)F.n_tiles * 8;
+        // one record per composited contributor for the backward; the pool
+        // is sized from the chunks the previous recording forward on this
+        // context took (a quarter of headroom, plus one chunk per warp of the
+        // launch), else 128 records per pixel; a record that does not fit
+        // sends its tile to the exact replay
+        const uint64_t warps = (uint64_t)raster_slots(F.kmax, opt->kbuf_capacity, false, false, F.n_tiles);
         const uint64_t prev = ctx->h_total[1] & 0xffffffffu;
-        uint64_t chunks = prev > 0 ? prev + prev / 4 + blocks : 8 * blocks;
-        chunks = std::min<uint64_t>(chunks, 0xfffffff0u);
-        R.emit_pool_chunks = (uint32_t)chunks;
-        R.emit_ctr = ctx->emit_ctr;
-        if ((s = al.get(&R.emit_pool, (size_t)chunks * kEmitChunkWords)) != DRK_OK) return s;
-        if ((s = al.get(&R.emit_hdr, (size_t)blocks * kEmitChunks)) != DRK_OK) return s;
-        DRK_CUDA(cudaMemsetAsync(R.emit_hdr, 0xff, sizeof(uint32_t) * (size_t)blocks * kEmitChunks, st));
-        DRK_CUDA(cudaMemsetAsync(ctx->emit_ctr, 0, sizeof(unsigned int), st));
-        if ((s = al.get(&R.emit_n, (size_t)F.n_tiles * kTilePix)) != DRK_OK) return s;
+        const uint64_t npix = (uint64_t)cam->width * cam->height;
+        uint64_t chunks = prev > 0 ? prev + prev / 4 + warps : (npix * 128 + kRecChunk - 1) / kRecChunk + warps;
+        chunks = std::min<uint64_t>(chunks, (0xffffffffull / kRecChunk) - 1);
+        R.rec_cap = (uint32_t)(chunks * kRecChunk);
+        R.rec_ctr = ctx->rec_ctr;
+        if ((s = al.get(&R.rec_key, (size_t)R.rec_cap)) != DRK_OK) return s;
+        if ((s = al.get(&R.rec_pix, (size_t)R.rec_cap)) != DRK_OK) return s;
+        if ((s = al.get(&R.rec_tp, (size_t)R.rec_cap)) != DRK_OK) return s;
+        DRK_CUDA(cudaMemsetAsync(R.rec_key, 0xff, sizeof(uint32_t) * (size_t)R.rec_cap, st));
+        DRK_CUDA(cudaMemsetAsync(ctx->rec_ctr, 0, sizeof(unsigned int), st));
         if ((s = al.get(&R.tile_overflow, (size_t)F.n_tiles)) != DRK_OK) return s;
         DRK_CUDA(cudaMemsetAsync(R.tile_overflow, 0, sizeof(int32_t) * (size_t)F.n_tiles, st));
     }
@@ -473,9 +476,10 @@ drk_status_t drk_render(drk_ctx_t* ctx, const drk_params_t* params, const drk_ca
         S->ranges = w.ranges;
         S->tile_order = w.tile_order;
         S->dq = A.dq;
-        S->emit_pool = R.emit_pool;
-        S->emit_hdr = R.emit_hdr;
-        S->emit_n = R.emit_n;
+        S->rec_key = R.rec_key;
+        S->rec_pix = R.rec_pix;
+        S->rec_tp = R.rec_tp;
+        S->rec_cap = R.rec_cap;
         S->tile_overflow = R.tile_overflow;
         const size_t npix = (size_t)cam->width * cam->height;
         float* cf = nullptr;
@@ -485,6 +489,13 @@ drk_status_t drk_render(drk_ctx_t* ctx, const drk_params_t* params, const drk_ca
         }
         DRK_CUDA(cudaMemcpyAsync(cf, out->rgb, 3 * npix * sizeof(float), cudaMemcpyDeviceToDevice, st));
         S->Cfin = cf;
+        unsigned int* rch = nullptr;
+        if ((s = al.get(&rch, 1)) != DRK_OK) {
+            delete S;
+            return s;
+        }
+        DRK_CUDA(cudaMemcpyAsync(rch, ctx->rec_ctr, sizeof(unsigned int), cudaMemcpyDeviceToDevice, st));
+        S->rec_chunks = rch;
         S->allocs = al.ptrs;
         al.keep = true;
         *state = S;
@@ -545,14 +556,37 @@ drk_status_t drk_render_backward(drk_ctx_t* ctx, const drk_params_t* params, con
     R.Cfin = state->Cfin;
     R.gtmp = gtmp;
     R.grads = *grads;
-    R.emit_pool = state->emit_pool;
-    R.emit_hdr = state->emit_hdr;
-    R.emit_n = state->emit_n;
+    R.rec_key = state->rec_key;
+    R.rec_pix = state->rec_pix;
+    R.rec_tp = state->rec_tp;
+    R.rec_cap = state->rec_cap;
     R.tile_overflow = state->tile_overflow;
     attach_ovf(ctx, opt, F.kmax, state->cap, true, F.n_tiles, st, R);
+
+    // records taken by the forward (one readback; the sort is sized by it)
+    DRK_CUDA(cudaMemcpyAsync(ctx->h_total + 2, state->rec_chunks, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+    DRK_CUDA(cudaStreamSynchronize(st));
+    const uint64_t nrec = std::min<uint64_t>((uint64_t)(uint32_t)ctx->h_total[2] * kRecChunk, state->rec_cap);
+    uint32_t *skey = nullptr, *sslot = nullptr, *kalt = nullptr, *valt = nullptr;
+    uint8_t* sort_scr = nullptr;
+    if ((s = al.get(&skey, (size_t)nrec)) != DRK_OK) return s;
+    if ((s = al.get(&sslot, (size_t)nrec)) != DRK_OK) return s;
+    if ((s = al.get(&kalt, (size_t)nrec)) != DRK_OK) return s;
+    if ((s = al.get(&valt, (size_t)nrec)) != DRK_OK) return s;
+    if ((s = al.get(&sort_scr, radix_sort_scratch_bytes((int64_t)nrec))) != DRK_OK) return s;
+    // keys below 2^bits - 1 sort before the unused slots (kNoSlot)
+    int bits = 1;
+    while (bits < 32 && (uint64_t(1) << bits) - 1 <= (uint64_t)state->pairs) bits++;
     StageTimer& tm = ctx->timer;
     cudaEvent_t ev = tm.begin(st);
-    launch_raster_backward_list(R, F.kmax, st);          // tiles with complete lists
+    if (nrec > 0) {
+        DRK_CUDA(cudaMemcpyAsync(skey, state->rec_key, sizeof(uint32_t) * nrec, cudaMemcpyDeviceToDevice, st));
+        launch_iota(sslot, (uint32_t)nrec, st);
+        radix_sort_pairs(skey, sslot, kalt, valt, (int64_t)nrec, bits, sort_scr, st);
+    }
+    tm.end(ST_REC_SORT, ev, st);
+    ev = tm.begin(st);
+    launch_raster_backward_records(R, skey, sslot, (uint32_t)nrec, F.kmax, st);
     tm.end(ST_RASTER_BWD, ev, st);
     ev = tm.begin(st);
     launch_raster(R, F.kmax, state->cap, true, st);      // exact replay of the others

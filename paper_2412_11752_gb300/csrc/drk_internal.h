@@ -82,19 +82,18 @@ struct RasterArgs {
     float* out_rgb;
     float* out_T;
     int32_t* out_n;
-    // contributor lists recorded by the forward for the backward (may be
-    // null).  The list position of the s-th composited contributor of lane
-    // `lane` of block `blk` of `tile` is
-    //   emit_pool[((c * 32) + (s % 32)) * 32 + lane],
-    //   c = emit_hdr[(tile * 8 + blk) * kEmitChunks + s / 32]
-    // (chunks of 32 slots x 32 lanes taken from the pool on demand);
-    // emit_n[tile * kTilePix + blk * 32 + lane] = count; tile_overflow[tile]
-    // != 0 if a list did not fit (the backward replays that tile exactly)
-    uint32_t* emit_pool;
-    uint32_t* emit_hdr;              // filled with kEmitEmpty before the forward
-    unsigned int* emit_ctr;          // chunks taken (zeroed before the forward)
-    uint32_t emit_pool_chunks;
-    int32_t* emit_n;
+    // contributor records written by the forward for the backward (may be
+    // null): one per composited contributor, in rec_cap slots handed out in
+    // chunks of kRecChunk; rec_key = global pair index (ranges[tile].x + list
+    // position; kNoSlot for an unused slot), rec_pix = y * width + x,
+    // rec_tp = (T before the contributor, composited colour after it).
+    // tile_overflow[tile] != 0 if a record did not fit (the backward replays
+    // that tile exactly)
+    uint32_t* rec_key;               // filled with kNoSlot before the forward
+    uint32_t* rec_pix;
+    float4* rec_tp;
+    uint32_t rec_cap;
+    unsigned int* rec_ctr;           // chunks taken (zeroed before the forward)
     int32_t* tile_overflow;
     // backward
     drk_params_t p;
@@ -104,10 +103,9 @@ struct RasterArgs {
     drk_params_grad_t grads;
 };
 
-// chunked contributor lists (see RasterArgs)
-constexpr int kEmitChunks = 256;                 // chunks per 8 x 4 block: 8192 contributors per pixel
-constexpr uint32_t kEmitEmpty = 0xffffffffu;
-constexpr size_t kEmitChunkWords = 32 * 32;
+// contributor records (see RasterArgs)
+constexpr uint32_t kRecChunk = 1024;
+constexpr uint32_t kNoSlot = 0xffffffffu;
 
 // host-side count of kernel launches made by the library (all threads)
 void note_launch();
@@ -139,7 +137,11 @@ void launch_raster(const RasterArgs& A, int kmax, int cap, bool bwd, cudaStream_
 // and the bytes of the overflow columns of `slots` warps
 int raster_slots(int kmax, int cap, bool bwd, bool batch, int n_tiles);
 size_t raster_ovf_bytes(int slots);
-void launch_raster_backward_list(const RasterArgs& A, int kmax, cudaStream_t st);
+// backward over n records sorted by key (skey, with their slots sslot)
+void launch_raster_backward_records(const RasterArgs& A, const uint32_t* skey, const uint32_t* sslot, uint32_t n,
+                                    int kmax, cudaStream_t st);
+// v[i] = i for i < n
+void launch_iota(uint32_t* v, uint32_t n, cudaStream_t st);
 // batched forward over A.n_batch_tiles tiles of the frames in A.slots
 void launch_raster_batch(const RasterArgs& A, int kmax, int cap, cudaStream_t st);
 

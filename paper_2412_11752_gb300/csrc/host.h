@@ -50,7 +50,8 @@ struct Allocs {
 };
 
 // CUDA-event timing of the pipeline stages (off unless enabled)
-enum { ST_PREPROCESS = 0, ST_EMIT, ST_SORT, ST_RASTER, ST_RASTER_BWD, ST_PREPROCESS_BWD, ST_REPLAY, ST_COUNT = 8 };
+enum { ST_PREPROCESS = 0, ST_EMIT, ST_SORT, ST_RASTER, ST_RASTER_BWD, ST_PREPROCESS_BWD, ST_REPLAY, ST_REC_SORT,
+       ST_COUNT = 8 };
 struct StageTimer {
     bool on = false;
     std::vector<cudaEvent_t> pool;

@@ -14,15 +14,16 @@
 // Reverse.  For a composited contributor i of a pixel,
 //   dC/dc_i = T_i alpha_i,  dC/dalpha_i = T_i c_i - S_i / (1 - alpha_i),
 // with S_i = C_final - P_i the colour composited behind i (P_i the prefix
-// including i); the pixel walks its contributors front to back, as the
-// supplementary "Cache-Sorting" paragraph prescribes for a cache-sorted
-// forward.  The derivative flows through Eq. 10 - Eq. 4 to the record
-// quantities of the primitive.  The list kernel walks the recorded
-// positions and sums the gradients of each list item over the tile's
-// pixels in a shared-memory window of list positions before one global
-// atomic per (tile, item, component).  Tiles where a pixel composited more
-// entries than were recorded use the replay kernel instead, which re-runs
-// the forward traversal exactly and accumulates with global atomics.
+// including i).  The forward writes one record per composited contributor
+// (list pair, pixel, T_i, P_i) in the order it composites, which is the
+// front-to-back order the supplementary "Cache-Sorting" paragraph asks the
+// backward to follow; each record then carries its own T_i and P_i, so the
+// backward treats records independently: sorted by list pair, a warp
+// recomputes 32 of them and sums the gradients of equal pairs with
+// segmented shuffles before one global atomic per pair and component.
+// Tiles whose records did not fit the pool use the replay kernel instead,
+// which re-runs the forward traversal exactly and accumulates with global
+// atomics.
 #include <algorithm>
 
 #include "drk_internal.h"
@@ -39,7 +40,6 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 constexpr int kMaxPasses = 1 << 20;
 constexpr int kRasterThreads = 128;   // persistent raster CTAs: 4 independent warps
-constexpr int kWin = 128;          // list positions per backward accumulation window
 
 // per-item gradient accumulator layout (floats)
 enum : int { A_H = 0, A_FPX = 9, A_FPY = 10, A_FCOEF = 11, A_RGB = 12, A_OPA = 15, A_TAU = 16, A_ETA = 17, A_NFIX = 18 };
@@ -340,18 +340,25 @@ __device__ __forceinline__ void add_global(const RasterArgs& A, uint32_t idx, co
     if (g.has_k1 && g.dth_k1 != 0.f) atomicAdd(A.grads.theta + base + g.k + 1, g.dth_k1);
 }
 
-// Chunk of an 8 x 4 block's contributor lists (slots 32k .. 32k + 31 of all
-// its lanes): taken from the pool by the first lane that needs it.  Lanes
-// that race for the same chunk agree through the compare-and-swap (the
-// loser's chunk stays unused); no lane waits for another.  Returns
-// kEmitEmpty when the pool is exhausted.
-__device__ __forceinline__ uint32_t take_chunk(const RasterArgs& A, uint32_t* hdr) {
-    uint32_t c = *reinterpret_cast<volatile uint32_t*>(hdr);
-    if (c != kEmitEmpty) return c;
-    const uint32_t cand = atomicAdd(A.emit_ctr, 1u);
-    if (cand >= A.emit_pool_chunks) return kEmitEmpty;
-    const uint32_t old = atomicCAS(hdr, kEmitEmpty, cand);
-    return old == kEmitEmpty ? cand : old;
+// The warp's current chunk of contributor-record slots [base, end).
+struct RecChunk {
+    uint32_t base, end;
+};
+
+// Called by all 32 lanes: takes the next chunk of kRecChunk record slots
+// from the pool (one atomic per chunk).  When the pool is exhausted the
+// chunk stays empty and the tile is marked for the exact replay.
+__device__ __forceinline__ void take_record_chunk(const RasterArgs& A, RecChunk& rc, int tile) {
+    uint32_t c = 0;
+    if ((threadIdx.x & 31) == 0) c = atomicAdd(A.rec_ctr, 1u);
+    c = __shfl_sync(0xffffffffu, c, 0);
+    if ((uint64_t)(c + 1) * kRecChunk <= (uint64_t)A.rec_cap) {
+        rc.base = c * kRecChunk;
+        rc.end = rc.base + kRecChunk;
+    } else {
+        rc.base = rc.end = 0;
+        if ((threadIdx.x & 31) == 0) A.tile_overflow[tile] = 1;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -368,7 +375,7 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
                                          const uint32_t* __restrict__ keysp, const uint2* __restrict__ rangesp,
                                          const DepthQuant* __restrict__ dqp, float* __restrict__ outp, bool batched,
                                          int tile, uint32_t task, float4* stage, float* ring, uint4* ovf,
-                                         HeapBuf<CAP, kRasterThreads>& kb, WarpCounters& wc) {
+                                         HeapBuf<CAP, kRasterThreads>& kb, WarpCounters& wc, RecChunk& rc) {
     constexpr int HDR = Rec<KMAX>::HDR;
     constexpr int STRIDE4 = Rec<KMAX>::STRIDE4;
     constexpr int HDR4 = HDR / 4;
@@ -382,7 +389,6 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
     const int tx = tile % fc.tiles_x, ty = tile / fc.tiles_x;
     const int x = tx * kTile + (blk & 1) * 8 + (lane & 7);
     const int y = ty * kTile + (blk >> 1) * 4 + (lane >> 3);
-    const int tpix = blk * 32 + lane;          // pixel slot within the tile
     const bool inside = x < fc.width && y < fc.height;
     const uint2 rg = rangesp[tile];
     const uint32_t L = rg.y - rg.x;
@@ -403,10 +409,8 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
             Cf[c] = A.Cfin[c * npix + pix];
         }
     }
-    // contributor list of this pixel for the backward (chunks of 32 slots)
-    const bool rec_list = !BWD && A.emit_pool != nullptr;
-    uint32_t* const chunk_hdr = rec_list ? A.emit_hdr + ((size_t)tile * 8 + blk) * kEmitChunks : nullptr;
-    uint32_t cur_chunk = kEmitEmpty;
+    // contributor records for the backward
+    const bool rec_on = !BWD && A.rec_key != nullptr;
     kb.init(ring + threadIdx.x, reinterpret_cast<uint32_t*>(ring) + CAP * kRasterThreads + threadIdx.x,
             ring + 2 * CAP * kRasterThreads + threadIdx.x, ovf, A.ovf_cap, list);
     // Exact order with a bounded heap.  When a contributor finds the heap
@@ -431,7 +435,9 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
         }
     };
 
-    auto emit_front = [&]() {
+    // composites the root of this lane's heap; `slot` is the record slot of
+    // the composited contributor (kNoSlot: not recorded)
+    auto emit_front = [&](uint32_t slot) {
         const float a = kb.front_a();
         const float Tn = __fmul_rn(ps.T, __fsub_rn(1.f, a));
         if (Tn < fc.T_min) {
@@ -444,15 +450,12 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
                               __ldg(rgbp + 3 * (size_t)idx + 2)};
         const float wgt = __fmul_rn(a, ps.T);
         if (!BWD) {
+            const float T_i = ps.T;
             for (int c = 0; c < 3; c++) ps.C[c] = fmaf(wgt, col[c], ps.C[c]);
-            if (rec_list) {
-                const int sl = ps.n_emit;
-                if ((sl & 31) == 0)
-                    cur_chunk = sl < kEmitChunks * 32 ? take_chunk(A, chunk_hdr + (sl >> 5)) : kEmitEmpty;
-                if (cur_chunk != kEmitEmpty)
-                    A.emit_pool[((size_t)cur_chunk * 32 + (sl & 31)) * 32 + lane] = p;
-                else
-                    A.tile_overflow[tile] = 1;   // exact replay in the backward
+            if (slot != kNoSlot) {
+                A.rec_key[slot] = rg.x + p;
+                A.rec_pix[slot] = (uint32_t)pix;
+                A.rec_tp[slot] = make_float4(T_i, ps.C[0], ps.C[1], ps.C[2]);
             }
         } else {
             float G = 0.f;
@@ -471,19 +474,40 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
         ps.n_emit++;
     };
 
-    // composites every pending entry that no item at or after a list
-    // position with depth bound thr can precede; false when the next entry
-    // to composite is at or after the smallest dropped key (the pass ends)
-    auto drain = [&](float thr) -> bool {
+    // Called by all 32 lanes.  For each lane with `go`, composites every
+    // pending entry that no item at or after a list position with depth
+    // bound thr can precede, in rounds in which every lane that still has
+    // one composites one entry; the round's records take consecutive slots
+    // of the warp's record chunk.  Returns false for a lane whose next entry
+    // is at or after its smallest dropped key (its pass ends).
+    auto drain = [&](bool go, float thr) -> bool {
         const float lt = __uint_as_float((uint32_t)(lost >> 32));
-        while (!kb.empty() && kb.front_t() < thr) {
-            if (lost != ~0ull && kb.front_at_or_after(lt, (uint32_t)lost)) return false;
-            emit_front();
-            if (ps.done) return true;
-            kb.pop();
+        bool ok = true;
+        while (true) {
+            bool want = go && ok && !ps.done && !kb.empty() && kb.front_t() < thr;
+            if (want && lost != ~0ull && kb.front_at_or_after(lt, (uint32_t)lost)) {
+                ok = false;
+                want = false;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, want);
+            if (m == 0) break;
+            uint32_t slot = kNoSlot;
+            if (rec_on) {
+                const uint32_t cnt = (uint32_t)__popc(m);
+                if (rc.end - rc.base < cnt) take_record_chunk(A, rc, tile);
+                if (rc.end - rc.base >= cnt) {
+                    slot = rc.base + (uint32_t)__popc(m & ((1u << lane) - 1u));
+                    rc.base += cnt;
+                }
+            }
+            if (want) {
+                emit_front(slot);
+                if (!ps.done) kb.pop();
+            }
         }
         // nothing left below the smallest dropped key can come before thr
-        return !(lost != ~0ull && lt < thr);
+        if (go && ok) ok = !(lost != ~0ull && lt < thr);
+        return ok;
     };
 
     while (true) {   // passes over the list
@@ -517,9 +541,10 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
             // than possible never changes the order; a pixel that finishes
             // inside the chunk only evaluates a few items more.
             const uint32_t key0 = __shfl_sync(0xffffffffu, key_a, 0);
-            if (!pass_done) {
+            {
                 const float thr0 = fmaf((float)(key0 & qmask), dq.inv_scale, dq.zmin);
-                if (!drain(thr0) || ps.done) pass_done = true;
+                const bool ok = drain(!pass_done, thr0);
+                if (!pass_done && (!ok || ps.done)) pass_done = true;
             }
             for (uint32_t jj = 0; jj < cn; jj++) {
                 const uint32_t idx = __shfl_sync(0xffffffffu, idx_a, jj);
@@ -564,7 +589,7 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
         cp_async_wait_all();
         __syncwarp();
         // end of the list for this pass: composite what is left in order
-        if (!ps.done) drain(__int_as_float(0x7f800000));
+        drain(!ps.done, __int_as_float(0x7f800000));
         bool need = !ps.done && lost != ~0ull;
         if (need && wc.passes >= (unsigned long long)kMaxPasses) {
             // every pass composites at least CAP entries, so this bound is
@@ -587,7 +612,6 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
         if (!batched && A.out_T) A.out_T[pix] = ps.T;
         if (!batched && A.out_n) A.out_n[pix] = ps.n_emit;
     }
-    if (!BWD && A.emit_n) A.emit_n[(size_t)tile * kTilePix + tpix] = inside ? ps.n_emit : 0;
     wc.emit += (unsigned long long)ps.n_emit;
 }
 
@@ -627,6 +651,7 @@ __global__ void __launch_bounds__(kRasterThreads, 4) raster_kernel(RasterArgs A)
     WarpCounters wc;
 
     HeapBuf<CAP, kRasterThreads> kb;
+    RecChunk rc{0u, 0u};
 
     while (true) {
         uint32_t task = 0;
@@ -637,10 +662,10 @@ __global__ void __launch_bounds__(kRasterThreads, 4) raster_kernel(RasterArgs A)
         if (BATCH) {
             const FrameSlot& sl = A.slots[(uint32_t)tile >> 20];
             run_task<KMAX, CAP, BWD>(A, sl.fc, sl.rec, sl.rgb, sl.vals, sl.keys, sl.ranges, sl.dq, sl.out_rgb, true,
-                                     tile & ((1 << 20) - 1), task, stage, ring, ovf, kb, wc);
+                                     tile & ((1 << 20) - 1), task, stage, ring, ovf, kb, wc, rc);
         } else {
             run_task<KMAX, CAP, BWD>(A, A.fc, A.rec, A.rgb, A.vals, A.keys, A.ranges, A.dq, A.out_rgb, false, tile, task,
-                                     stage, ring, ovf, kb, wc);
+                                     stage, ring, ovf, kb, wc, rc);
         }
     }
     // counters: one atomic per warp
@@ -673,131 +698,109 @@ __device__ __forceinline__ float warp_sum32(float v) {
 }
 
 // ---------------------------------------------------------------------------
-// Backward over the recorded contributor lists.  Each pixel walks its
-// composited list positions front to back; gradients of list positions in
-// the current window [w0, w0 + kWin) are summed over the tile's pixels in
-// shared memory and flushed with one global atomic per non-zero component;
-// a position below the window (a late entry of a pixel) goes straight to
-// global atomics.  The window start jumps to the smallest pending position.
-template <int KMAX>
-__global__ void __launch_bounds__(kTilePix) raster_backward_list_kernel(RasterArgs A) {
-    constexpr int AS = A_NFIX + 2 * KMAX;   // + scale[KMAX], theta[KMAX]
-    __shared__ float acc[kWin * AS];
-    __shared__ uint32_t s_min;
-    const FrameConst& fc = A.fc;
-    const int tile = A.tile_order ? (int)A.tile_order[blockIdx.x] : (int)blockIdx.x;
-    if (A.tile_overflow[tile] != 0) return;                     // replayed exactly instead
-    const int tx = tile % fc.tiles_x, ty = tile / fc.tiles_x;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int x = tx * kTile + (warp & 1) * 8 + (lane & 7);
-    const int y = ty * kTile + (warp >> 1) * 4 + (lane >> 3);
-    const bool inside = x < fc.width && y < fc.height;
-    const uint2 rg = A.ranges[tile];
-    const uint32_t* list = A.vals + rg.x;
-    const PixelRay pr = make_ray(fc, x, y);
-    const size_t npix = (size_t)fc.width * fc.height;
-    const size_t pix = (size_t)y * fc.width + x;
-    const int n = inside ? A.emit_n[(size_t)tile * kTilePix + threadIdx.x] : 0;
-    const uint32_t* hdr = A.emit_hdr + ((size_t)tile * 8 + warp) * kEmitChunks;
-    uint32_t chunk = n > 0 ? hdr[0] : kEmitEmpty;
-    auto position = [&](int sl) -> uint32_t {
-        if ((sl & 31) == 0) chunk = hdr[sl >> 5];
-        return A.emit_pool[((size_t)chunk * 32 + (sl & 31)) * 32 + lane];
-    };
-    float dL[3] = {0.f, 0.f, 0.f}, Cf[3] = {0.f, 0.f, 0.f};
-    if (inside) {
-        for (int c = 0; c < 3; c++) {
-            dL[c] = A.dL[c * npix + pix];
-            Cf[c] = A.Cfin[c * npix + pix];
-        }
+// Backward over the contributor records, sorted by list pair (tile, item).
+// Each record (pixel, T before, colour prefix after) is independent: the
+// warp takes 32 consecutive records, recomputes each pair with all
+// intermediates, forms dC/dalpha = T c - S / (1 - alpha) with
+// S = C_final - P, chains through Eq. 10 - Eq. 4 to the record quantities,
+// and sums over runs of equal keys (the pixels of one tile that composited
+// one item) with segmented shuffles; the last lane of a run adds the sums
+// to global memory.  Sector terms are summed over runs of equal
+// (key, sector).  Records of tiles marked for the replay are skipped.
+
+// inclusive sum over lanes [start, lane] (start <= lane; every lane calls it)
+__device__ __forceinline__ float seg_sum(float v, int start) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float w = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane - o >= start) v += w;
     }
-    float T = 1.f, P[3] = {0.f, 0.f, 0.f};
-    int s = 0;
-    uint32_t next = n > 0 ? position(0) : 0xffffffffu;
+    return v;
+}
+
+template <int KMAX>
+__global__ void __launch_bounds__(256) raster_backward_records_kernel(RasterArgs A, const uint32_t* __restrict__ skey,
+                                                                      const uint32_t* __restrict__ sslot, uint32_t n) {
+    const int lane = threadIdx.x & 31;
+    const FrameConst& fc = A.fc;
+    const size_t npix = (size_t)fc.width * fc.height;
     const int K = A.K;
-    while (true) {
-        if (threadIdx.x == 0) s_min = 0xffffffffu;
-        __syncthreads();
-        if (next != 0xffffffffu) atomicMin(&s_min, next);
-        for (int i = threadIdx.x; i < kWin * AS; i += kTilePix) acc[i] = 0.f;
-        __syncthreads();
-        const uint32_t w0 = s_min;
-        if (w0 == 0xffffffffu) break;                           // every pixel is through
-        while (next < w0 + (uint32_t)kWin) {
-            const uint32_t p = next;
-            const uint32_t idx = __ldg(list + p);
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t g = i < n ? skey[i] : kNoSlot;
+    PairGrad pg;
+#pragma unroll
+    for (int j = 0; j < A_NFIX; j++) pg.v[j] = 0.f;
+    pg.k = 0; pg.k1 = 0;
+    pg.ds_k = pg.ds_k1 = pg.dth_k = pg.dth_k1 = 0.f;
+    uint32_t idx = 0;
+    if (g != kNoSlot) {
+        const uint32_t slot = sslot[i];
+        const uint32_t pix = A.rec_pix[slot];
+        const int y = (int)(pix / (uint32_t)fc.width), x = (int)(pix - (uint32_t)y * fc.width);
+        const int tile = (y / kTile) * fc.tiles_x + x / kTile;
+        if (A.tile_overflow[tile] != 0) {
+            g = kNoSlot;                      // replayed exactly instead
+        } else {
+            const float4 tp = A.rec_tp[slot];
+            idx = __ldg(A.vals + g);
             const float* r = A.rec + (size_t)Rec<KMAX>::STRIDE * idx;
+            const PixelRay pr = make_ray(fc, x, y);
             float t, a;
             EvalInfo e;
             eval_pair<KMAX, true>(r, pr, fc.near_plane, fc.alpha_min, fc.alpha_max, t, a, &e);
             const float col[3] = {__ldg(A.rgb + 3 * (size_t)idx), __ldg(A.rgb + 3 * (size_t)idx + 1),
                                   __ldg(A.rgb + 3 * (size_t)idx + 2)};
+            const float T = tp.x;
+            const float P[3] = {tp.y, tp.z, tp.w};
             const float wgt = __fmul_rn(a, T);
             const float inv1ma = 1.f / (1.f - a);
-            float G = 0.f;
+            float G = 0.f, dL[3];
             for (int c = 0; c < 3; c++) {
-                P[c] = fmaf(wgt, col[c], P[c]);
-                G += dL[c] * (T * col[c] - (Cf[c] - P[c]) * inv1ma);
+                dL[c] = A.dL[c * npix + pix];
+                G += dL[c] * (T * col[c] - (A.Cfin[c * npix + pix] - P[c]) * inv1ma);
             }
-            PairGrad g;
-            grad_from_info<KMAX>(A, r, idx, pr, e, G, g);
-            for (int c = 0; c < 3; c++) g.v[A_RGB + c] = dL[c] * wgt;
-            if (p >= w0) {
-                float* slot = acc + (size_t)(p - w0) * AS;
-                // neighbouring pixels usually composite the same primitive at
-                // the same step: when the whole warp works on one list
-                // position, sum in registers and let lane 0 add (the sector
-                // terms too when every lane is in the same sector)
-                const unsigned act = __activemask();
-                if (act == 0xffffffffu && __match_any_sync(act, p) == act) {
-#pragma unroll
-                    for (int j = 0; j < A_NFIX; j++) {
-                        const float v = warp_sum32(g.v[j]);
-                        g.v[j] = lane == 0 ? v : 0.f;
-                    }
-                    // every lane takes part in every shuffle (no short-circuit)
-                    const int k0 = __shfl_sync(act, g.k, 0);
-                    const int hk0 = __shfl_sync(act, (int)g.has_k, 0);
-                    const int hk10 = __shfl_sync(act, (int)g.has_k1, 0);
-                    const bool same_sector = g.k == k0 && (int)g.has_k == hk0 && (int)g.has_k1 == hk10;
-                    if (__all_sync(act, same_sector)) {
-                        const float a0 = warp_sum32(g.ds_k), a1 = warp_sum32(g.ds_k1);
-                        const float a2 = warp_sum32(g.dth_k), a3 = warp_sum32(g.dth_k1);
-                        g.ds_k = lane == 0 ? a0 : 0.f;
-                        g.ds_k1 = lane == 0 ? a1 : 0.f;
-                        g.dth_k = lane == 0 ? a2 : 0.f;
-                        g.dth_k1 = lane == 0 ? a3 : 0.f;
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < A_NFIX; j++)
-                    if (g.v[j] != 0.f) atomicAdd(slot + j, g.v[j]);
-                if (g.ds_k != 0.f) atomicAdd(slot + A_NFIX + g.k, g.ds_k);
-                if (g.ds_k1 != 0.f) atomicAdd(slot + A_NFIX + g.k1, g.ds_k1);
-                if (g.has_k && g.dth_k != 0.f) atomicAdd(slot + A_NFIX + KMAX + g.k, g.dth_k);
-                if (g.has_k1 && g.dth_k1 != 0.f) atomicAdd(slot + A_NFIX + KMAX + g.k + 1, g.dth_k1);
-            } else {
-                add_global(A, idx, g);
-            }
-            T = __fmul_rn(T, __fsub_rn(1.f, a));
-            s++;
-            next = s < n ? position(s) : 0xffffffffu;
+            grad_from_info<KMAX>(A, r, idx, pr, e, G, pg);
+            for (int c = 0; c < 3; c++) pg.v[A_RGB + c] = dL[c] * wgt;
         }
-        __syncthreads();
-        // flush the window: one global atomic per non-zero component
-        for (int i = threadIdx.x; i < kWin * AS; i += kTilePix) {
-            const float v = acc[i];
-            if (v == 0.f) continue;
-            const int slot = i / AS, j = i - slot * AS;
-            const uint32_t idx = __ldg(list + w0 + slot);
-            if (j < A_OPA) atomicAdd(A.gtmp + (size_t)G_STRIDE * idx + j, v);
-            else if (j == A_OPA) atomicAdd(A.grads.opacity + idx, v);
-            else if (j == A_TAU) atomicAdd(A.grads.tau + idx, v);
-            else if (j == A_ETA) atomicAdd(A.grads.eta + idx, v);
-            else if (j < A_NFIX + KMAX) atomicAdd(A.grads.scale + (size_t)K * idx + (j - A_NFIX), v);
-            else atomicAdd(A.grads.theta + (size_t)K * idx + (j - A_NFIX - KMAX), v);
-        }
-        __syncthreads();
+    }
+    // runs of equal keys are contiguous (sorted); kNoSlot lanes carry zeros
+    const unsigned le = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
+    const uint32_t gp = __shfl_up_sync(0xffffffffu, g, 1);
+    const uint32_t gn = __shfl_down_sync(0xffffffffu, g, 1);
+    const bool head = lane == 0 || g != gp;
+    const bool tail = lane == 31 || g != gn;
+    const int start = 31 - __clz(__ballot_sync(0xffffffffu, head) & le);
+#pragma unroll
+    for (int j = 0; j < A_NFIX; j++) pg.v[j] = seg_sum(pg.v[j], start);
+    // sector terms: runs of equal (key, sector)
+    const int kp = __shfl_up_sync(0xffffffffu, pg.k, 1);
+    const int kn = __shfl_down_sync(0xffffffffu, pg.k, 1);
+    const bool head2 = head || pg.k != kp;
+    const bool tail2 = tail || pg.k != kn;
+    const int start2 = 31 - __clz(__ballot_sync(0xffffffffu, head2) & le);
+    pg.ds_k = seg_sum(pg.ds_k, start2);
+    pg.ds_k1 = seg_sum(pg.ds_k1, start2);
+    pg.dth_k = seg_sum(pg.dth_k, start2);
+    pg.dth_k1 = seg_sum(pg.dth_k1, start2);
+    if (g == kNoSlot) return;
+    if (tail) {
+        float* gt = A.gtmp + (size_t)G_STRIDE * idx;
+#pragma unroll
+        for (int j = 0; j < A_OPA; j++)
+            if (pg.v[j] != 0.f) atomicAdd(gt + j, pg.v[j]);
+        if (pg.v[A_OPA] != 0.f) atomicAdd(A.grads.opacity + idx, pg.v[A_OPA]);
+        if (pg.v[A_TAU] != 0.f) atomicAdd(A.grads.tau + idx, pg.v[A_TAU]);
+        if (pg.v[A_ETA] != 0.f) atomicAdd(A.grads.eta + idx, pg.v[A_ETA]);
+    }
+    if (tail2) {
+        // theta'_0 = 0 and theta'_K = 2 pi are constants of the frame
+        const int k = pg.k, k1 = (k + 1 == K) ? 0 : k + 1;
+        const size_t base = (size_t)K * idx;
+        if (pg.ds_k != 0.f) atomicAdd(A.grads.scale + base + k, pg.ds_k);
+        if (pg.ds_k1 != 0.f) atomicAdd(A.grads.scale + base + k1, pg.ds_k1);
+        if (k >= 1 && pg.dth_k != 0.f) atomicAdd(A.grads.theta + base + k, pg.dth_k);
+        if (k + 1 < K && pg.dth_k1 != 0.f) atomicAdd(A.grads.theta + base + k + 1, pg.dth_k1);
     }
 }
 
@@ -895,11 +898,12 @@ void launch_raster_batch(const RasterArgs& A, int kmax, int cap, cudaStream_t st
 #undef DRK_RASTER_CASE
 }
 
-void launch_raster_backward_list(const RasterArgs& A, int kmax, cudaStream_t st) {
-    const int n_tiles = A.fc.tiles_x * A.fc.tiles_y;
-    if (n_tiles == 0) return;
-    if (kmax == 8) raster_backward_list_kernel<8><<<n_tiles, kTilePix, 0, st>>>(A);
-    else raster_backward_list_kernel<16><<<n_tiles, kTilePix, 0, st>>>(A);
+void launch_raster_backward_records(const RasterArgs& A, const uint32_t* skey, const uint32_t* sslot, uint32_t n,
+                                    int kmax, cudaStream_t st) {
+    if (n == 0) return;
+    const unsigned blocks = (unsigned)((n + 255u) / 256u);
+    if (kmax == 8) raster_backward_records_kernel<8><<<blocks, 256, 0, st>>>(A, skey, sslot, n);
+    else raster_backward_records_kernel<16><<<blocks, 256, 0, st>>>(A, skey, sslot, n);
     note_launch();
 }
 

@@ -292,6 +292,17 @@ void launch_batch_order_keys(const uint2* ranges, int n_tiles, int slot, uint32_
     note_launch();
 }
 
+__global__ void iota_kernel(uint32_t* __restrict__ v, uint32_t n) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = i;
+}
+
+void launch_iota(uint32_t* v, uint32_t n, cudaStream_t st) {
+    if (n == 0) return;
+    iota_kernel<<<(n + 255u) / 256u, 256, 0, st>>>(v, n);
+    note_launch();
+}
+
 size_t tile_order_work_bytes(int n_tiles) {
     return 4 * sizeof(uint32_t) * (size_t)n_tiles + radix_sort_scratch_bytes(n_tiles) + 64;
 }

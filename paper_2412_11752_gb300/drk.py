@@ -214,7 +214,7 @@ class Context:
         return {name: (ms[i], cnt[i]) for i, name in enumerate(STAGES)}
 
 
-STAGES = ("preprocess", "emit", "sort", "raster", "raster_bwd", "preprocess_bwd", "replay_bwd", "unused7")
+STAGES = ("preprocess", "emit", "sort", "raster", "raster_bwd", "preprocess_bwd", "replay_bwd", "record_sort")
 
 
 def launch_count() -> int:
