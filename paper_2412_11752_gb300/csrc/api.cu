@@ -567,23 +567,16 @@ drk_status_t drk_render_backward(drk_ctx_t* ctx, const drk_params_t* params, con
     DRK_CUDA(cudaMemcpyAsync(ctx->h_total + 2, state->rec_chunks, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
     DRK_CUDA(cudaStreamSynchronize(st));
     const uint64_t nrec = std::min<uint64_t>((uint64_t)(uint32_t)ctx->h_total[2] * kRecChunk, state->rec_cap);
-    uint32_t *skey = nullptr, *sslot = nullptr, *kalt = nullptr, *valt = nullptr;
+    // records grouped by list pair: counting sort over the pair index
+    uint32_t *skey = nullptr, *sslot = nullptr;
     uint8_t* sort_scr = nullptr;
+    const uint32_t n_keys = (uint32_t)state->pairs;
     if ((s = al.get(&skey, (size_t)nrec)) != DRK_OK) return s;
     if ((s = al.get(&sslot, (size_t)nrec)) != DRK_OK) return s;
-    if ((s = al.get(&kalt, (size_t)nrec)) != DRK_OK) return s;
-    if ((s = al.get(&valt, (size_t)nrec)) != DRK_OK) return s;
-    if ((s = al.get(&sort_scr, radix_sort_scratch_bytes((int64_t)nrec))) != DRK_OK) return s;
-    // keys below 2^bits - 1 sort before the unused slots (kNoSlot)
-    int bits = 1;
-    while (bits < 32 && (uint64_t(1) << bits) - 1 <= (uint64_t)state->pairs) bits++;
+    if ((s = al.get(&sort_scr, counting_sort_scratch_bytes(n_keys))) != DRK_OK) return s;
     StageTimer& tm = ctx->timer;
     cudaEvent_t ev = tm.begin(st);
-    if (nrec > 0) {
-        DRK_CUDA(cudaMemcpyAsync(skey, state->rec_key, sizeof(uint32_t) * nrec, cudaMemcpyDeviceToDevice, st));
-        launch_iota(sslot, (uint32_t)nrec, st);
-        radix_sort_pairs(skey, sslot, kalt, valt, (int64_t)nrec, bits, sort_scr, st);
-    }
+    counting_sort_keys(state->rec_key, (uint32_t)nrec, n_keys, skey, sslot, sort_scr, st);
     tm.end(ST_REC_SORT, ev, st);
     ev = tm.begin(st);
     launch_raster_backward_records(R, skey, sslot, (uint32_t)nrec, F.kmax, st);

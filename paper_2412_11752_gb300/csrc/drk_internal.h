@@ -142,6 +142,12 @@ void launch_raster_backward_records(const RasterArgs& A, const uint32_t* skey, c
                                     int kmax, cudaStream_t st);
 // v[i] = i for i < n
 void launch_iota(uint32_t* v, uint32_t n, cudaStream_t st);
+// counting sort of n keys below n_keys (others dropped): out_keys/out_idx
+// hold the kept keys grouped by key (order within a key unspecified) and
+// their input positions, then kNoSlot
+size_t counting_sort_scratch_bytes(uint32_t n_keys);
+void counting_sort_keys(const uint32_t* keys, uint32_t n, uint32_t n_keys, uint32_t* out_keys, uint32_t* out_idx,
+                        void* scratch, cudaStream_t st);
 // batched forward over A.n_batch_tiles tiles of the frames in A.slots
 void launch_raster_batch(const RasterArgs& A, int kmax, int cap, cudaStream_t st);
 

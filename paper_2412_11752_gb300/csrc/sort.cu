@@ -292,6 +292,50 @@ void launch_batch_order_keys(const uint2* ranges, int n_tiles, int slot, uint32_
     note_launch();
 }
 
+// ---------------------------------------------------------------------------
+// Counting sort of n dense keys (< n_keys; other keys are dropped): count,
+// exclusive scan, scatter.  Entries of one key end up contiguous in an
+// unspecified order; out_keys/out_idx beyond the kept entries hold kNoSlot.
+__global__ void key_count_kernel(const uint32_t* __restrict__ keys, uint32_t n, uint32_t n_keys,
+                                 uint32_t* __restrict__ count) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t k = keys[i];
+    if (k < n_keys) atomicAdd(count + k, 1u);
+}
+
+__global__ void key_scatter_kernel(const uint32_t* __restrict__ keys, uint32_t n, uint32_t n_keys,
+                                   unsigned long long* __restrict__ cursor, uint32_t* __restrict__ out_keys,
+                                   uint32_t* __restrict__ out_idx) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t k = keys[i];
+    if (k >= n_keys) return;
+    const unsigned long long pos = atomicAdd(cursor + k, 1ull);
+    out_keys[pos] = k;
+    out_idx[pos] = i;
+}
+
+size_t counting_sort_scratch_bytes(uint32_t n_keys) {
+    return ((size_t)n_keys + 1) * (sizeof(uint32_t) + sizeof(uint64_t)) + scan_scratch_bytes((int64_t)n_keys + 1) + 64;
+}
+
+void counting_sort_keys(const uint32_t* keys, uint32_t n, uint32_t n_keys, uint32_t* out_keys, uint32_t* out_idx,
+                        void* scratch, cudaStream_t st) {
+    cudaMemsetAsync(out_keys, 0xff, sizeof(uint32_t) * (size_t)n, st);
+    if (n == 0 || n_keys == 0) return;
+    uint32_t* count = reinterpret_cast<uint32_t*>(scratch);
+    uint64_t* offs = reinterpret_cast<uint64_t*>(
+        (reinterpret_cast<uintptr_t>(count + (size_t)n_keys + 1) + 15) & ~uintptr_t(15));
+    void* sscr = reinterpret_cast<void*>((reinterpret_cast<uintptr_t>(offs + (size_t)n_keys + 1) + 15) & ~uintptr_t(15));
+    cudaMemsetAsync(count, 0, sizeof(uint32_t) * ((size_t)n_keys + 1), st);
+    const unsigned blocks = (n + 255u) / 256u;
+    key_count_kernel<<<blocks, 256, 0, st>>>(keys, n, n_keys, count); note_launch();
+    exclusive_scan_u32_u64(count, offs, (int64_t)n_keys, sscr, st);
+    key_scatter_kernel<<<blocks, 256, 0, st>>>(keys, n, n_keys, reinterpret_cast<unsigned long long*>(offs), out_keys,
+                                                out_idx); note_launch();
+}
+
 __global__ void iota_kernel(uint32_t* __restrict__ v, uint32_t n) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) v[i] = i;
