@@ -53,11 +53,14 @@ constexpr double csqrt(double x) { return csqrt_iter(x, x > 1.0 ? x : 1.0, 60); 
 //   21     -o tau/(1 - tau)           middle offset (x o)
 //   22     2 o tau/(1 + tau)          upper offset (x o)
 //   23     tau
-//   24..   theta'_1 .. theta'_{KMAX-1}, padded with +1e30
-// then KMAX sectors of 8 floats:
-//   theta'_k, pi / gap_k, A_k + A_k1, A_k - A_k1, Minv (row-major, 4)
-//   with A_j = 1 / (2 s_j^2) (Eq. 6) and Minv = [e_k e_k1]^-1 (Eq. 7),
-//   e_j = s_j (cos theta'_j, sin theta'_j).
+//   24 .. 24+KMAX-1           theta'_1 .. theta'_{K-1}, then theta'_K = 2 pi,
+//                             padded with +1e30 (sector thresholds)
+//   EX = 24+KMAX .. +KMAX-1   e_j.x = s_j cos theta'_j   (Eq. 7 basis)
+//   EY = EX+KMAX ..           e_j.y = s_j sin theta'_j
+//   AA = EY+KMAX ..           A_j = 1 / (2 s_j^2)         (Eq. 6)
+// The sector constants (pi / gap, A_k +- A_k1, the inverse of
+// [e_k e_k1]) are formed from these during the evaluation, so the whole
+// evaluation reads the record header only.
 // ---------------------------------------------------------------------------
 enum : int {
     R_HU0 = 0, R_HU1, R_HU2, R_HV0, R_HV1, R_HV2, R_HW0, R_HW1, R_HW2,
@@ -66,12 +69,16 @@ enum : int {
     R_TH = 24
 };
 constexpr int R_GEO4 = 4;   // float4 count of the geometry part
-enum : int { S_TH = 0, S_PG, S_SUM, S_DIF, S_M00, S_M01, S_M10, S_M11, S_STRIDE };
+constexpr int R_FIX4 = 6;   // float4 count of the fixed part (floats 0-23)
 
 template <int KMAX>
 struct Rec {
-    static constexpr int HDR = ((R_TH + KMAX - 1) + 3) / 4 * 4;
-    static constexpr int STRIDE = HDR + S_STRIDE * KMAX;      // floats
+    static constexpr int TH = R_TH;
+    static constexpr int EX = TH + KMAX;
+    static constexpr int EY = EX + KMAX;
+    static constexpr int AA = EY + KMAX;
+    static constexpr int HDR = AA + KMAX;                     // floats
+    static constexpr int STRIDE = HDR;
     static constexpr int STRIDE4 = STRIDE / 4;                // float4
     static_assert(STRIDE % 4 == 0, "record must be float4 aligned");
 };
@@ -121,13 +128,14 @@ struct PixelRay {
 // Intermediate values of one evaluation, kept when the derivative is needed.
 struct EvalInfo {
     float t, u, v, phi, r2sq, dth, c, Q, a, b, r1, X, g, al_k, Xf, f;
+    float pg, dif;                  // pi / gap_k, A_k - A_k1
+    float ekx, eky, e1x, e1y, idet; // e_k, e_k1 and 1 / det [e_k e_k1]
     int k;
     bool filt_eval, use_filter, clamped;
 };
 
-// Record header loads (16-byte, read-only path).  The geometry stage needs
-// the first R_GEO4 float4; the kernel stage the rest of the header.
-template <int KMAX>
+// Record header loads (16-byte, read-only path): the fixed part (floats
+// 0-23) into registers; the geometry stage needs the first R_GEO4 float4.
 __device__ __forceinline__ void load_head_geo(const float4* __restrict__ r4, float* h) {
 #pragma unroll
     for (int q = 0; q < R_GEO4; q++) {
@@ -135,18 +143,13 @@ __device__ __forceinline__ void load_head_geo(const float4* __restrict__ r4, flo
         h[4 * q] = v.x; h[4 * q + 1] = v.y; h[4 * q + 2] = v.z; h[4 * q + 3] = v.w;
     }
 }
-template <int KMAX>
-__device__ __forceinline__ void load_head_rest(const float4* __restrict__ r4, float* h) {
+__device__ __forceinline__ void load_head_fix(const float4* __restrict__ r4, float* h) {
+    load_head_geo(r4, h);
 #pragma unroll
-    for (int q = R_GEO4; q < Rec<KMAX>::HDR / 4; q++) {
+    for (int q = R_GEO4; q < R_FIX4; q++) {
         const float4 v = __ldg(r4 + q);
         h[4 * q] = v.x; h[4 * q + 1] = v.y; h[4 * q + 2] = v.z; h[4 * q + 3] = v.w;
     }
-}
-template <int KMAX>
-__device__ __forceinline__ void load_head(const float4* __restrict__ r4, float* h) {
-    load_head_geo<KMAX>(r4, h);
-    load_head_rest<KMAX>(r4, h);
 }
 
 // Geometry of one (pixel, primitive) pair: ray-plane intersection and local
@@ -184,28 +187,45 @@ __device__ __forceinline__ bool eval_geometry(const float* h, const PixelRay& pr
 }
 
 // Stage 2: the deformable radial kernel (Eq. 6 - Eq. 9), the low-pass
-// filter (Eq. 10) and the clamp.  `sec` points to the record's sector
-// array in global memory.  Returns true iff alpha_tilde >= alpha_min.
+// filter (Eq. 10) and the clamp.  h holds header floats 0-23; hb points to
+// the whole header (staged shared memory or the record in global memory)
+// for the thresholds and the basis table; K is the basis count.  Returns
+// true iff alpha_tilde >= alpha_min.
 template <int KMAX, bool INFO>
-__device__ __forceinline__ bool eval_kernel(const float* h, const float* __restrict__ sec, const PixelRay& pr,
+__device__ __forceinline__ bool eval_kernel(const float* h, const float* hb, int K, const PixelRay& pr,
                                             const Geo& gm, float alpha_min, float alpha_max, float& a_out,
                                             EvalInfo* info = nullptr) {
+    using RK = Rec<KMAX>;
     const float t = gm.t, u = gm.u, v = gm.v, r2sq = gm.r2sq;
     // polar angle from the first basis (Eq. 6 with reading: full circle)
     float phi = atan2f(v, u);
     phi = phi < 0.0f ? __fadd_rn(phi, kTwoPi) : phi;
+    // sector k: theta'_k <= phi < theta'_k1 (thresholds 1 .. K-1; the K-th is 2 pi)
     int k = 0;
 #pragma unroll
-    for (int j = 1; j < KMAX; j++) k += (h[R_TH + j - 1] < phi) ? 1 : 0;
-    const float4 s0 = __ldg(reinterpret_cast<const float4*>(sec + S_STRIDE * k));
-    const float4 s1 = __ldg(reinterpret_cast<const float4*>(sec + S_STRIDE * k + 4));
+    for (int q = 0; q < KMAX / 4; q++) {
+        const float4 th4 = *reinterpret_cast<const float4*>(hb + RK::TH + 4 * q);
+        if (4 * q + 1 < KMAX) k += (th4.x < phi) ? 1 : 0;
+        if (4 * q + 2 < KMAX) k += (th4.y < phi) ? 1 : 0;
+        if (4 * q + 3 < KMAX) k += (th4.z < phi) ? 1 : 0;
+        if (4 * q + 4 < KMAX) k += (th4.w < phi) ? 1 : 0;
+    }
+    const int k1 = (k + 1 == K) ? 0 : k + 1;
+    const float thk = k == 0 ? 0.0f : hb[RK::TH + k - 1];
+    const float thk1 = hb[RK::TH + k];
+    const float Ak = hb[RK::AA + k], Ak1 = hb[RK::AA + k1];
+    const float ekx = hb[RK::EX + k], eky = hb[RK::EY + k];
+    const float e1x = hb[RK::EX + k1], e1y = hb[RK::EY + k1];
     // Eq. 6: relative angle, cosine weight, inverse squared radius
-    const float dth = __fmul_rn(__fadd_rn(phi, -s0.x), s0.y);
+    const float pg = __fmul_rn(kPi, rcp_approx(__fadd_rn(thk1, -thk)));
+    const float dth = __fmul_rn(__fadd_rn(phi, -thk), pg);
     const float c = __cosf(dth);
-    const float Q = fmaf(c, s0.w, s0.z);
-    // Eq. 7: L1 norm in the endpoint basis
-    const float a = fmaf(s1.x, u, __fmul_rn(s1.y, v));
-    const float b = fmaf(s1.z, u, __fmul_rn(s1.w, v));
+    const float dif = __fadd_rn(Ak, -Ak1);
+    const float Q = fmaf(c, dif, __fadd_rn(Ak, Ak1));
+    // Eq. 7: L1 norm in the endpoint basis, (a, b) = [e_k e_k1]^-1 (u, v)
+    const float idet = rcp_approx(fmaf(ekx, e1y, -__fmul_rn(eky, e1x)));
+    const float a = __fmul_rn(fmaf(e1y, u, -__fmul_rn(e1x, v)), idet);
+    const float b = __fmul_rn(fmaf(ekx, v, -__fmul_rn(eky, u)), idet);
     const float r1 = __fadd_rn(fabsf(a), fabsf(b));
     // Eq. 8 in base 2: g = 2^-X, X = log2(e)/2 (eta r1^2 + (1 - eta) r2^2 Q)
     const float X = fmaf(h[R_ETA2], __fmul_rn(r1, r1), __fmul_rn(h[R_ETA2C], __fmul_rn(r2sq, Q)));
@@ -237,22 +257,24 @@ __device__ __forceinline__ bool eval_kernel(const float* h, const float* __restr
         info->t = t; info->u = u; info->v = v; info->phi = phi; info->r2sq = r2sq; info->dth = dth;
         info->c = c; info->Q = Q; info->a = a; info->b = b; info->r1 = r1; info->X = X; info->g = g;
         info->al_k = al_k; info->Xf = Xf; info->f = f; info->k = k;
+        info->pg = pg; info->dif = dif;
+        info->ekx = ekx; info->eky = eky; info->e1x = e1x; info->e1y = e1y; info->idet = idet;
         info->filt_eval = filt_eval; info->use_filter = use_filter; info->clamped = clamped;
     }
     return al >= alpha_min;
 }
 
-// Both stages for a record in global memory (header loaded into registers).
+// Both stages for a record in global memory.
 template <int KMAX, bool INFO>
-__device__ __forceinline__ bool eval_pair(const float* __restrict__ rec, const PixelRay& pr, float near_plane,
+__device__ __forceinline__ bool eval_pair(const float* __restrict__ rec, int K, const PixelRay& pr, float near_plane,
                                           float alpha_min, float alpha_max, float& t_out, float& a_out,
                                           EvalInfo* info = nullptr) {
-    float h[Rec<KMAX>::HDR];
-    load_head<KMAX>(reinterpret_cast<const float4*>(rec), h);
+    float h[R_FIX4 * 4];
+    load_head_fix(reinterpret_cast<const float4*>(rec), h);
     Geo gm;
     if (!eval_geometry(h, pr, near_plane, gm)) return false;
     t_out = gm.t;
-    return eval_kernel<KMAX, INFO>(h, rec + Rec<KMAX>::HDR, pr, gm, alpha_min, alpha_max, a_out, info);
+    return eval_kernel<KMAX, INFO>(h, rec, K, pr, gm, alpha_min, alpha_max, a_out, info);
 }
 
 // Launch-wide constants of one render.

@@ -217,35 +217,22 @@ __global__ void __launch_bounds__(128) preprocess_kernel(PreArgs A) {
         rec[R_FPX] = 0.f; rec[R_FPY] = 0.f; rec[R_FCOEF] = 0.f; rec[R_FCUT] = -1.f;
     }
 
-    // angles relative to theta_0 and per-sector constants (Eq. 6, Eq. 7)
-    constexpr int HDR = Rec<KMAX>::HDR;
-    for (int j = 1; j < KMAX; j++) rec[R_TH + j - 1] = (j < K) ? th[j] - th[0] : 1e30f;
-    for (int j = R_TH + KMAX - 1; j < HDR; j++) rec[j] = 0.f;
-    for (int k = 0; k < KMAX; k++) {
-        float* sec = rec + HDR + S_STRIDE * k;
-        if (k >= K) {
-            for (int j = 0; j < S_STRIDE; j++) sec[j] = 0.f;
+    // angles relative to theta_0 (sector thresholds, the K-th is 2 pi) and
+    // the basis table e_j, A_j the evaluation forms sector constants from
+    // (Eq. 6, Eq. 7)
+    using RK = Rec<KMAX>;
+    for (int j = 1; j <= KMAX; j++) rec[RK::TH + j - 1] = (j < K) ? th[j] - th[0] : (j == K ? kTwoPi : 1e30f);
+    for (int j = 0; j < KMAX; j++) {
+        if (j >= K) {
+            rec[RK::EX + j] = 0.f; rec[RK::EY + j] = 0.f; rec[RK::AA + j] = 0.f;
             continue;
         }
-        const int k1 = (k + 1 == K) ? 0 : k + 1;
-        const float tk = (k == 0) ? 0.f : th[k] - th[0];
-        const float tk1 = (k + 1 == K) ? kTwoPi : th[k + 1] - th[0];
-        const float gap = tk1 - tk;
-        const float Ak = 1.f / (2.f * s[k] * s[k]);
-        const float Ak1 = 1.f / (2.f * s[k1] * s[k1]);
-        float sk, ck, sk1, ck1;
-        sincosf(tk, &sk, &ck);
-        sincosf(tk1, &sk1, &ck1);
-        const float e0x = s[k] * ck, e0y = s[k] * sk, e1x = s[k1] * ck1, e1y = s[k1] * sk1;
-        const float det = e0x * e1y - e1x * e0y;
-        sec[S_TH] = tk;
-        sec[S_PG] = kPi / gap;
-        sec[S_SUM] = Ak + Ak1;
-        sec[S_DIF] = Ak - Ak1;
-        sec[S_M00] = e1y / det;
-        sec[S_M01] = -e1x / det;
-        sec[S_M10] = -e0y / det;
-        sec[S_M11] = e0x / det;
+        const float tj = (j == 0) ? 0.f : th[j] - th[0];
+        float sn, cs;
+        sincosf(tj, &sn, &cs);
+        rec[RK::EX + j] = s[j] * cs;
+        rec[RK::EY + j] = s[j] * sn;
+        rec[RK::AA + j] = 1.f / (2.f * s[j] * s[j]);
     }
 
     // colour (Eq. 1's SH term), clamped below at 0

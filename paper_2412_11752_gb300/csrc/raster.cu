@@ -40,6 +40,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 constexpr int kMaxPasses = 1 << 20;
 constexpr int kRasterThreads = 128;   // persistent raster CTAs: 4 independent warps
+constexpr int kChunk = 16;            // list items staged and composited per step
 
 // per-item gradient accumulator layout (floats)
 enum : int { A_H = 0, A_FPX = 9, A_FPY = 10, A_FCOEF = 11, A_RGB = 12, A_OPA = 15, A_TAU = 16, A_ETA = 17, A_NFIX = 18 };
@@ -210,7 +211,6 @@ struct PairGrad {
 template <int KMAX>
 __device__ __forceinline__ void grad_from_info(const RasterArgs& A, const float* __restrict__ r, uint32_t idx,
                                                const PixelRay& pr, const EvalInfo& e, float G, PairGrad& out) {
-    constexpr int HDR = Rec<KMAX>::HDR;
 #pragma unroll
     for (int j = 0; j < A_NFIX; j++) out.v[j] = 0.f;
     out.k = 0; out.k1 = 0;
@@ -256,14 +256,13 @@ __device__ __forceinline__ void grad_from_info(const RasterArgs& A, const float*
         const int k = e.k, k1 = (k + 1 == K) ? 0 : k + 1;
         const float* sc = A.p.scale + (size_t)K * idx;
         const float sk = __ldg(sc + k), sk1 = __ldg(sc + k1);
-        const float* sec = r + HDR + S_STRIDE * k;
         // Q = (A_k + A_k1) + c (A_k - A_k1), A = 1/(2 s^2)
         float ds_k = d_Q * (1.f + e.c) * (-1.f / (sk * sk * sk));
         float ds_k1 = d_Q * (1.f - e.c) * (-1.f / (sk1 * sk1 * sk1));
-        const float d_c = d_Q * sec[S_DIF];
+        const float d_c = d_Q * e.dif;
         // c = cos(dth), dth = (phi - th_k) pi / gap
         const float d_dth = -d_c * __sinf(e.dth);
-        const float pg = sec[S_PG];
+        const float pg = e.pg;
         const float d_phi = d_dth * pg;
         float dth_k = d_dth * pg * (e.dth * (1.f / kPi) - 1.f);
         float dth_k1 = -d_dth * pg * e.dth * (1.f / kPi);
@@ -276,16 +275,12 @@ __device__ __forceinline__ void grad_from_info(const RasterArgs& A, const float*
         // r1 = |a| + |b|, (a, b) = Minv (u, v), Minv = [e_k e_k1]^-1
         const float sa = e.a > 0.f ? 1.f : (e.a < 0.f ? -1.f : 0.f);
         const float sb = e.b > 0.f ? 1.f : (e.b < 0.f ? -1.f : 0.f);
-        const float wx = sec[S_M00] * sa + sec[S_M10] * sb;
-        const float wy = sec[S_M01] * sa + sec[S_M11] * sb;
+        // Minv = [e_k e_k1]^-1 = [[e1y, -e1x], [-eky, ekx]] / det
+        const float ekx = e.ekx, eky = e.eky, e1x = e.e1x, e1y = e.e1y;
+        const float wx = (e1y * sa - eky * sb) * e.idet;
+        const float wy = (-e1x * sa + ekx * sb) * e.idet;
         dL_du += d_r1 * wx;
         dL_dv += d_r1 * wy;
-        // the basis vectors e_k = s_k (cos theta'_k, sin theta'_k) and e_k1
-        // are the columns of Minv^-1
-        const float m00 = sec[S_M00], m01 = sec[S_M01], m10 = sec[S_M10], m11 = sec[S_M11];
-        const float idet = 1.f / (m00 * m11 - m01 * m10);
-        const float ekx = m11 * idet, eky = -m10 * idet;
-        const float e1x = -m01 * idet, e1y = m00 * idet;
         ds_k += d_r1 * (-e.a) * (wx * ekx + wy * eky) / sk;
         dth_k += d_r1 * (-e.a) * (wy * ekx - wx * eky);
         ds_k1 += d_r1 * (-e.b) * (wx * e1x + wy * e1y) / sk1;
@@ -321,7 +316,7 @@ __device__ __forceinline__ void pair_grad(const RasterArgs& A, const float* __re
                                           const PixelRay& pr, float G, PairGrad& out) {
     float t, al;
     EvalInfo e;
-    eval_pair<KMAX, true>(r, pr, A.fc.near_plane, A.fc.alpha_min, A.fc.alpha_max, t, al, &e);
+    eval_pair<KMAX, true>(r, A.K, pr, A.fc.near_plane, A.fc.alpha_min, A.fc.alpha_max, t, al, &e);
     grad_from_info<KMAX>(A, r, idx, pr, e, G, out);
 }
 
@@ -374,11 +369,11 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
                                          const float* __restrict__ rgbp, const uint32_t* __restrict__ valsp,
                                          const uint32_t* __restrict__ keysp, const uint2* __restrict__ rangesp,
                                          const DepthQuant* __restrict__ dqp, float* __restrict__ outp, bool batched,
-                                         int tile, uint32_t task, float4* stage, float* ring, uint4* ovf,
+                                         int K, int tile, uint32_t task, float4* stage, float* ring, uint4* ovf,
                                          HeapBuf<CAP, kRasterThreads>& kb, WarpCounters& wc, RecChunk& rc) {
-    constexpr int HDR = Rec<KMAX>::HDR;
+    constexpr int HDR4 = Rec<KMAX>::HDR / 4;
     constexpr int STRIDE4 = Rec<KMAX>::STRIDE4;
-    constexpr int HDR4 = HDR / 4;
+    constexpr int kHalf4 = (HDR4 + 1) / 2;
     const int lane = threadIdx.x & 31;
     const DepthQuant dq = *dqp;
     const uint32_t qmask = (1u << dq.depth_bits) - 1u;
@@ -453,9 +448,11 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
             const float T_i = ps.T;
             for (int c = 0; c < 3; c++) ps.C[c] = fmaf(wgt, col[c], ps.C[c]);
             if (slot != kNoSlot) {
-                A.rec_key[slot] = rg.x + p;
-                A.rec_pix[slot] = (uint32_t)pix;
-                A.rec_tp[slot] = make_float4(T_i, ps.C[0], ps.C[1], ps.C[2]);
+                // read only by the backward: streaming stores keep them from
+                // evicting the primitive records this kernel re-reads from L2
+                __stcs(A.rec_key + slot, rg.x + p);
+                __stcs(A.rec_pix + slot, (uint32_t)pix);
+                __stcs(A.rec_tp + slot, make_float4(T_i, ps.C[0], ps.C[1], ps.C[2]));
             }
         } else {
             float G = 0.f;
@@ -510,31 +507,41 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
         return ok;
     };
 
+    // copies the headers of the chunk starting at list position base, whose
+    // indices lanes 0 .. kChunk-1 hold in idxv, into the stage buffer bufp
+    // (two lanes per item)
+    auto stage_chunk = [&](uint32_t base, uint32_t idxv, float4* bufp) {
+        const int it = lane >> 1, half = lane & 1;
+        const uint32_t id = __shfl_sync(0xffffffffu, idxv, it);
+        if (base + (uint32_t)it < L) {
+            const float4* src = rec4 + (size_t)id * STRIDE4;
+#pragma unroll
+            for (int q = half * kHalf4; q < (half + 1) * kHalf4; q++)
+                if (q < HDR4) cp_async16(bufp + it * HDR4 + q, src + q);
+        }
+    };
+
     while (true) {   // passes over the list
         bool pass_done = finished;
-        // chunk c covers list positions [32 c, 32 c + 32); lane l holds item 32 c + l
-        uint32_t idx_a = lane < L ? __ldg(list + lane) : 0u;
-        uint32_t key_a = lane < L ? __ldg(lkeys + lane) : 0u;
-        uint32_t idx_b = 32 + lane < L ? __ldg(list + 32 + lane) : 0u;
-        uint32_t key_b = 32 + lane < L ? __ldg(lkeys + 32 + lane) : 0u;
-        if ((uint32_t)lane < L)
-            for (int q = 0; q < HDR4; q++)
-                cp_async16(stage + lane * HDR4 + q, rec4 + (size_t)idx_a * STRIDE4 + q);
+        // chunk c covers list positions [kChunk c, kChunk (c + 1)); lane l < kChunk holds item kChunk c + l
+        const bool lo_lane = lane < kChunk;
+        uint32_t idx_a = lo_lane && (uint32_t)lane < L ? __ldg(list + lane) : 0u;
+        uint32_t key_a = lo_lane && (uint32_t)lane < L ? __ldg(lkeys + lane) : 0u;
+        uint32_t idx_b = lo_lane && kChunk + (uint32_t)lane < L ? __ldg(list + kChunk + lane) : 0u;
+        uint32_t key_b = lo_lane && kChunk + (uint32_t)lane < L ? __ldg(lkeys + kChunk + lane) : 0u;
+        stage_chunk(0u, idx_a, stage);
         cp_async_commit();
-        for (uint32_t c0 = 0; c0 < L; c0 += 32) {
-            const int buf = (c0 >> 5) & 1;
-            // stage the next chunk's geometry, fetch the one after's entries
-            const uint32_t n1 = c0 + 32 + lane;
-            if (n1 < L)
-                for (int q = 0; q < HDR4; q++)
-                    cp_async16(stage + ((buf ^ 1) * 32 + lane) * HDR4 + q, rec4 + (size_t)idx_b * STRIDE4 + q);
+        for (uint32_t c0 = 0; c0 < L; c0 += kChunk) {
+            const int buf = (int)((c0 / kChunk) & 1u);
+            // stage the next chunk's headers, fetch the one after's entries
+            stage_chunk(c0 + kChunk, idx_b, stage + (buf ^ 1) * kChunk * HDR4);
             cp_async_commit();
-            const uint32_t n2 = c0 + 64 + lane;
-            const uint32_t idx_c = n2 < L ? __ldg(list + n2) : 0u;
-            const uint32_t key_c = n2 < L ? __ldg(lkeys + n2) : 0u;
+            const uint32_t n2 = c0 + 2 * kChunk + lane;
+            const uint32_t idx_c = lo_lane && n2 < L ? __ldg(list + n2) : 0u;
+            const uint32_t key_c = lo_lane && n2 < L ? __ldg(lkeys + n2) : 0u;
             cp_async_wait_1();
             __syncwarp();
-            const uint32_t cn = min(32u, L - c0);
+            const uint32_t cn = min((uint32_t)kChunk, L - c0);
             // Composite, once per chunk and with every lane together, each
             // pending entry that no item of this chunk or later can precede
             // (the chunk's first bound is the smallest).  Compositing later
@@ -549,32 +556,30 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
             for (uint32_t jj = 0; jj < cn; jj++) {
                 const uint32_t idx = __shfl_sync(0xffffffffu, idx_a, jj);
                 const uint32_t j = c0 + jj;
-                float h[HDR];
+                float h[R_FIX4 * 4];
                 Geo gm;
                 bool geo = false;
-                const float4* sg = stage + (buf * 32 + jj) * HDR4;
+                const float4* sg = stage + (buf * kChunk + jj) * HDR4;
                 if (!pass_done) {
-                    {
-                        wc.evals++;
+                    wc.evals++;
 #pragma unroll
-                        for (int q = 0; q < R_GEO4; q++) {
-                            const float4 v = sg[q];
-                            h[4 * q] = v.x; h[4 * q + 1] = v.y; h[4 * q + 2] = v.z; h[4 * q + 3] = v.w;
-                        }
-                        geo = eval_geometry(h, pr, fc.near_plane, gm);
+                    for (int q = 0; q < R_GEO4; q++) {
+                        const float4 v = sg[q];
+                        h[4 * q] = v.x; h[4 * q + 1] = v.y; h[4 * q + 2] = v.z; h[4 * q + 3] = v.w;
                     }
+                    geo = eval_geometry(h, pr, fc.near_plane, gm);
                 }
                 if (__any_sync(0xffffffffu, geo)) {
                     if (geo) {
                         wc.geo++;
 #pragma unroll
-                        for (int q = R_GEO4; q < HDR4; q++) {
+                        for (int q = R_GEO4; q < R_FIX4; q++) {
                             const float4 v = sg[q];
                             h[4 * q] = v.x; h[4 * q + 1] = v.y; h[4 * q + 2] = v.z; h[4 * q + 3] = v.w;
                         }
                         float a;
-                        if (eval_kernel<KMAX, false>(h, recp + (size_t)idx * (STRIDE4 * 4) + HDR, pr, gm,
-                                                     fc.alpha_min, fc.alpha_max, a)) {
+                        if (eval_kernel<KMAX, false>(h, reinterpret_cast<const float*>(sg), K, pr, gm, fc.alpha_min,
+                                                     fc.alpha_max, a)) {
                             wc.contrib++;
                             offer(gm.t, j, a, key_of(gm.t, idx));
                         }
@@ -630,17 +635,16 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
 // heaviest tile first (longest list), which keeps the tail short.
 template <int KMAX, int CAP, bool BWD, bool BATCH>
 __global__ void __launch_bounds__(kRasterThreads, 4) raster_kernel(RasterArgs A) {
-    constexpr int HDR = Rec<KMAX>::HDR;
     constexpr int kWarps = kRasterThreads / 32;
-    constexpr int HDR4 = HDR / 4;
+    constexpr int HDR4 = Rec<KMAX>::HDR / 4;
     extern __shared__ float4 smem4[];
-    // [kWarps][2 chunks][32 items][HDR4] float4 staging of record headers,
-    // then the shared part of the depth-order heaps
+    // [kWarps][2 chunks][kChunk items][HDR4] float4 staging of record
+    // headers, then the shared part of the depth-order heaps
     float4* stage_all = smem4;
-    float* ring = reinterpret_cast<float*>(smem4 + kWarps * 2 * 32 * HDR4);
+    float* ring = reinterpret_cast<float*>(smem4 + kWarps * 2 * kChunk * HDR4);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float4* stage = stage_all + warp * (2 * 32 * HDR4);
+    float4* stage = stage_all + warp * (2 * kChunk * HDR4);
     const int slot = blockIdx.x * kWarps + warp;
     // lane-contiguous columns: a lane's deep heap levels are adjacent, and
     // the footprint is what the pixels actually hold
@@ -662,10 +666,10 @@ __global__ void __launch_bounds__(kRasterThreads, 4) raster_kernel(RasterArgs A)
         if (BATCH) {
             const FrameSlot& sl = A.slots[(uint32_t)tile >> 20];
             run_task<KMAX, CAP, BWD>(A, sl.fc, sl.rec, sl.rgb, sl.vals, sl.keys, sl.ranges, sl.dq, sl.out_rgb, true,
-                                     tile & ((1 << 20) - 1), task, stage, ring, ovf, kb, wc, rc);
+                                     sl.K, tile & ((1 << 20) - 1), task, stage, ring, ovf, kb, wc, rc);
         } else {
-            run_task<KMAX, CAP, BWD>(A, A.fc, A.rec, A.rgb, A.vals, A.keys, A.ranges, A.dq, A.out_rgb, false, tile, task,
-                                     stage, ring, ovf, kb, wc, rc);
+            run_task<KMAX, CAP, BWD>(A, A.fc, A.rec, A.rgb, A.vals, A.keys, A.ranges, A.dq, A.out_rgb, false, A.K, tile,
+                                     task, stage, ring, ovf, kb, wc, rc);
         }
     }
     // counters: one atomic per warp
@@ -748,7 +752,7 @@ __global__ void __launch_bounds__(256) raster_backward_records_kernel(RasterArgs
             const PixelRay pr = make_ray(fc, x, y);
             float t, a;
             EvalInfo e;
-            eval_pair<KMAX, true>(r, pr, fc.near_plane, fc.alpha_min, fc.alpha_max, t, a, &e);
+            eval_pair<KMAX, true>(r, K, pr, fc.near_plane, fc.alpha_min, fc.alpha_max, t, a, &e);
             const float col[3] = {__ldg(A.rgb + 3 * (size_t)idx), __ldg(A.rgb + 3 * (size_t)idx + 1),
                                   __ldg(A.rgb + 3 * (size_t)idx + 2)};
             const float T = tp.x;
@@ -806,7 +810,7 @@ __global__ void __launch_bounds__(256) raster_backward_records_kernel(RasterArgs
 
 template <int KMAX, int CAP>
 constexpr size_t raster_smem() {
-    return (size_t)(kRasterThreads / 32) * 2 * 32 * (Rec<KMAX>::HDR / 4) * sizeof(float4) +
+    return (size_t)(kRasterThreads / 32) * 2 * kChunk * (Rec<KMAX>::HDR / 4) * sizeof(float4) +
            (size_t)3 * CAP * kRasterThreads * sizeof(float);
 }
 
