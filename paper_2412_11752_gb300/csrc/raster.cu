@@ -634,7 +634,7 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
 // when some lane of the warp passes the geometry stage.  Tasks are taken
 // heaviest tile first (longest list), which keeps the tail short.
 template <int KMAX, int CAP, bool BWD, bool BATCH>
-__global__ void __launch_bounds__(kRasterThreads, 4) raster_kernel(RasterArgs A) {
+__global__ void __launch_bounds__(kRasterThreads, 5) raster_kernel(RasterArgs A) {
     constexpr int kWarps = kRasterThreads / 32;
     constexpr int HDR4 = Rec<KMAX>::HDR / 4;
     extern __shared__ float4 smem4[];

@@ -95,6 +95,8 @@ def test_autograd_function_l1_loss(drk):
     dL = torch.sign(rgb.detach() - target) / rgb.numel()
     g = drk.drk_render_backward(ds, cam, opt, st, dL)
     torch.cuda.synchronize()
+    # the two backward runs sum their float atomics in different orders
     for k in NAMES:
         assert params[k].grad is not None
-        assert torch.allclose(params[k].grad, g[k], rtol=1e-5, atol=1e-7), k
+        scale = float(g[k].abs().max())
+        assert torch.allclose(params[k].grad, g[k], rtol=1e-3, atol=1e-5 * scale), k
