@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-pixels", type=int, default=1024, help="oracle sample size (pixels, fwd+bwd)")
-    ap.add_argument("--kbuf-capacity", type=int, default=16, choices=(8, 16, 32),
+    ap.add_argument("--kbuf-capacity", type=int, default=8, choices=(8, 16, 32),
                     help="per-pixel depth-order buffer entries (any value gives the same image)")
     ap.add_argument("--serve", action="store_true",
                     help="serving mode: Poisson request mix through drk_serve (batched vs one at a time)")

@@ -385,6 +385,9 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
     const int x = tx * kTile + (blk & 1) * 8 + (lane & 7);
     const int y = ty * kTile + (blk >> 1) * 4 + (lane >> 3);
     const bool inside = x < fc.width && y < fc.height;
+    // pixel-index corners of this 8 x 4 block (for the depth bounds of the items)
+    const float bx0 = (float)(tx * kTile + (blk & 1) * 8), by0 = (float)(ty * kTile + (blk >> 1) * 4);
+    const float2 bxs = make_float2(bx0, bx0 + 7.0f), bys = make_float2(by0, by0 + 3.0f);
     const uint2 rg = rangesp[tile];
     const uint32_t L = rg.y - rg.x;
     const uint32_t* list = valsp + rg.x;
@@ -547,9 +550,28 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
             // (the chunk's first bound is the smallest).  Compositing later
             // than possible never changes the order; a pixel that finishes
             // inside the chunk only evaluates a few items more.
-            const uint32_t key0 = __shfl_sync(0xffffffffu, key_a, 0);
+            // The threshold is a lower bound of r_t over this block's pixels
+            // for every item still to come: for this chunk's items the
+            // larger of the item's key bound and 1 / max w over the block's
+            // corners (w is affine in the pixel indices), deflated for FP32;
+            // for the items after the chunk the next chunk's first key bound.
             {
-                const float thr0 = fmaf((float)(key0 & qmask), dq.inv_scale, dq.zmin);
+                float bb = __int_as_float(0x7f800000);
+                if (lo_lane && c0 + (uint32_t)lane < L) {
+                    const float* hs = reinterpret_cast<const float*>(stage + (buf * kChunk + lane) * HDR4);
+                    const float W0 = hs[R_HW0], W1 = hs[R_HW1], W2 = hs[R_HW2];
+                    const float wy0 = fmaf(W1, bys.x, W2), wy1 = fmaf(W1, bys.y, W2);
+                    const float mw = fmaxf(fmaxf(fmaf(W0, bxs.x, wy0), fmaf(W0, bxs.y, wy0)),
+                                           fmaxf(fmaf(W0, bxs.x, wy1), fmaf(W0, bxs.y, wy1)));
+                    const float kb = fmaf((float)(key_a & qmask), dq.inv_scale, dq.zmin);
+                    bb = mw > 0.0f ? fmaxf(kb, __fmul_rn(rcp_approx(mw), 1.0f - 2e-5f)) : __int_as_float(0x7f800000);
+                }
+                for (int o = 8; o > 0; o >>= 1) bb = fminf(bb, __shfl_xor_sync(0xffffffffu, bb, o));
+                bb = __shfl_sync(0xffffffffu, bb, 0);
+                const uint32_t keyn = __shfl_sync(0xffffffffu, key_b, 0);
+                const float thr_next = c0 + kChunk < L ? fmaf((float)(keyn & qmask), dq.inv_scale, dq.zmin)
+                                                      : __int_as_float(0x7f800000);
+                const float thr0 = fminf(bb, thr_next);
                 const bool ok = drain(!pass_done, thr0);
                 if (!pass_done && (!ok || ps.done)) pass_done = true;
             }

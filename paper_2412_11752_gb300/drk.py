@@ -137,7 +137,7 @@ class Options:
     near_plane: float = 0.2
     bg: tuple = (0.0, 0.0, 0.0)
     cull_level: int = CULL_TILE
-    kbuf_capacity: int = 16
+    kbuf_capacity: int = 8
     ovf_capacity: int = 0
 
     def to_c(self) -> drk_options_t:
