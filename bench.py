@@ -168,6 +168,13 @@ def max_over_ranks(x: float, world: int, device) -> float:
     return float(t.item())
 
 
+def replica_rate(units_per_step: float, ms_step_local: float, world: int, device) -> tuple[float, float]:
+    """Whole-job rate of `world` independent replicas: the units of all ranks
+    divided by the slowest rank's step time (ms), and that step time."""
+    ms = max_over_ranks(ms_step_local, world, device)
+    return world * units_per_step / (ms / 1e3), ms
+
+
 # ---------------------------------------------------------------------------
 def oracle_rate(scene, cam, pixels: int, seed: int = 7) -> tuple[float, dict]:
     """Oracle (FP64 CPU) forward + backward over a seeded pixel sample: Mpix/s."""
@@ -274,8 +281,7 @@ def run_drk(args):
     ctx.timing_enable(False)
     stats = ctx.stats()
     ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    ms_step = max_over_ranks(float(np.mean(ms)), world, dev)
-    value = world * H * W / (ms_step / 1e3) / 1e6
+    value, ms_step = replica_rate(H * W / 1e6, float(np.mean(ms)), world, dev)
 
     # ---- roofline of the dominant kernel (FP32 ALU bound)
     peaks = measured_peaks()

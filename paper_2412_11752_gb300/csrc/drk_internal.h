@@ -129,7 +129,7 @@ void launch_tile_ranges(const uint32_t* keys, int64_t n, int depth_bits, uint2* 
 size_t tile_order_work_bytes(int n_tiles);
 void launch_tile_order(const uint2* ranges, int n_tiles, uint32_t* order, void* work, cudaStream_t st);
 // batch tile order: writes n_tiles (key, slot << 20 | tile) entries; sorting
-// them by 24-bit key gives the heaviest-first order over all frames
+// them by 26-bit key gives frame order, heaviest tile first within a frame
 void launch_batch_order_keys(const uint2* ranges, int n_tiles, int slot, uint32_t* keys, uint32_t* vals,
                              cudaStream_t st);
 void launch_raster(const RasterArgs& A, int kmax, int cap, bool bwd, cudaStream_t st);

@@ -8,7 +8,7 @@
 //   phase A per request   preprocess, culling count, scan (pair totals -> host)
 //   wait for the totals   (the worker keeps retiring the other stream's batch)
 //   phase B per request   emission, radix sort, tile ranges
-//   batch tile order      (len key, slot << 20 | tile) over all frames, sorted
+//   batch tile order      frame by frame, heaviest tile first within a frame
 //   one raster launch     persistent warps over every tile of every frame
 // and records a completion event.  The next batch's phases A/B run on the
 // other stream while this raster runs.  Each pixel's arithmetic and
@@ -323,7 +323,7 @@ void run_batch(drk_serve* S, int s, std::vector<Item>& items, int* countdown, st
         if (e != DRK_OK) { b->ok[i] = 0; status[i] = e; }
     }
 
-    // heaviest-first order over every tile of every live frame, and the slot
+    // frame-major, heaviest-first order over every tile of every live frame, and the slot
     // table the raster reads each task's frame from
     int live = 0;
     int64_t T = 0;
@@ -361,7 +361,7 @@ void run_batch(drk_serve* S, int s, std::vector<Item>& items, int* countdown, st
             slot++;
         }
         cudaMemcpyAsync(S->d_slots[s], S->h_slots[s], sizeof(FrameSlot) * (size_t)live, cudaMemcpyHostToDevice, st);
-        radix_sort_pairs(okeys, ovals, okalt, ovalt, T, 24, oscr, st);
+        radix_sort_pairs(okeys, ovals, okalt, ovalt, T, 26, oscr, st);
         RasterArgs R;
         std::memset(&R, 0, sizeof(R));
         R.fc = S->h_slots[s][0].fc;

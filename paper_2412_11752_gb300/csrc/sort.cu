@@ -281,7 +281,10 @@ __global__ void batch_order_keys_kernel(const uint2* __restrict__ ranges, int n_
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n_tiles) return;
     const uint2 r = ranges[t];
-    keys[t] = 0xffffffu - min(r.y - r.x, 0xffffffu);
+    // frame-major, heaviest tile first within a frame: a frame's tail runs
+    // beside the next frame's heaviest tiles while at most two frames'
+    // records compete for L2
+    keys[t] = (slot << 20) | (0xfffffu - min(r.y - r.x, 0xfffffu));
     vals[t] = (slot << 20) | (uint32_t)t;
 }
 
