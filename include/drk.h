@@ -245,10 +245,13 @@ int64_t drk_launch_count(void);
  * free (at most max_batch requests, while their estimated device memory
  * fits in mem_budget beside the batch already running), renders every
  * request of the batch with one preprocess/sort phase per request and ONE
- * rasterizer launch over all tiles of all of them, and marks the tickets
- * done when the batch's completion event fires.  Requests that arrive while
- * a batch runs join the next batch, whose preprocess and sort overlap the
- * running batch's rasterizer.  Each image is bit-identical to a
+ * rasterizer launch over all tiles of all of them.  A ticket is marked
+ * done as soon as its frame is complete: the rasterizer runs the batch
+ * frame by frame (heaviest tiles first within a frame), and the warp that
+ * finishes a frame's last tile sets a flag in host-mapped memory that the
+ * worker polls; at the latest when the batch's completion event fires.
+ * Requests that arrive while a batch runs join the next batch, whose
+ * preprocess and sort overlap the running batch's rasterizer.  Each image is bit-identical to a
  * drk_render of the same scene and camera (the batch does not change any
  * pixel's arithmetic or order).  All requests of a batch share one basis
  * count class (K <= 8 or K <= 16).  The rendering options are the server's.
@@ -258,7 +261,8 @@ typedef struct drk_serve drk_serve_t;
 typedef struct {
     double arrival_ms;    /* submit time, ms since the server was created */
     double start_ms;      /* its batch was launched */
-    double end_ms;        /* its batch completed (worker saw the event) */
+    double end_ms;        /* its frame was complete (worker saw the flag or
+                             the batch's event) */
     int32_t batch_size;   /* requests in its batch */
     int32_t status;       /* drk_status_t of the request */
 } drk_serve_timing_t;

@@ -51,6 +51,8 @@ struct FrameSlot {
     const DepthQuant* dq;
     float* out_rgb;
     int K;
+    unsigned int* task_left;         // device: tasks of this frame not yet finished
+    unsigned int* done_flag;         // host-mapped: set to 1 when the last task finished
 };
 
 // arguments of the raster kernels

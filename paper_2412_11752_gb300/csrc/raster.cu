@@ -689,6 +689,16 @@ __global__ void __launch_bounds__(kRasterThreads, 5) raster_kernel(RasterArgs A)
             const FrameSlot& sl = A.slots[(uint32_t)tile >> 20];
             run_task<KMAX, CAP, BWD>(A, sl.fc, sl.rec, sl.rgb, sl.vals, sl.keys, sl.ranges, sl.dq, sl.out_rgb, true,
                                      sl.K, tile & ((1 << 20) - 1), task, stage, ring, ovf, kb, wc, rc);
+            // the warp that finishes a frame's last task publishes it: its
+            // image is complete in device memory once the flag is visible
+            __syncwarp();
+            if (lane == 0 && sl.task_left) {
+                __threadfence();
+                if (atomicSub(sl.task_left, 1u) == 1u) {
+                    __threadfence_system();
+                    *reinterpret_cast<volatile unsigned int*>(sl.done_flag) = 1u;
+                }
+            }
         } else {
             run_task<KMAX, CAP, BWD>(A, A.fc, A.rec, A.rgb, A.vals, A.keys, A.ranges, A.dq, A.out_rgb, false, A.K, tile,
                                      task, stage, ring, ovf, kb, wc, rc);

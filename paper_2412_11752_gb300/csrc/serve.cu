@@ -58,6 +58,8 @@ struct Batch {
     int stream = 0;
     std::vector<uint64_t> tickets;
     std::vector<int> ok;             // request still live after phase A/B
+    std::vector<int> slot;           // its frame slot in the raster (-1: none)
+    std::vector<int> early;          // completed before the batch (frame flag)
     std::unique_ptr<Allocs> al;
     cudaEvent_t ev = nullptr;
     size_t bytes = 0;
@@ -88,6 +90,10 @@ struct drk_serve {
     unsigned long long* d_counters[kStreams] = {nullptr, nullptr};   // max_batch x 8 each
     unsigned long long* h_counters[kStreams] = {nullptr, nullptr};   // pinned copy at batch end
     unsigned int* d_task[kStreams] = {nullptr, nullptr};
+    unsigned int* d_left[kStreams] = {nullptr, nullptr};      // tasks left per frame slot
+    unsigned int* h_left[kStreams] = {nullptr, nullptr};      // pinned staging of d_left
+    unsigned int* h_done[kStreams] = {nullptr, nullptr};      // host-mapped frame-done flags
+    unsigned int* d_done[kStreams] = {nullptr, nullptr};      // their device address
     uint4* ovf[kStreams] = {nullptr, nullptr};           // raster overflow columns per stream
     size_t ovf_bytes[kStreams] = {0, 0};
     cudaEvent_t ev_phase_a[kStreams] = {nullptr, nullptr};
@@ -140,7 +146,25 @@ void retire(drk_serve* S, std::unique_ptr<BatchInfo>* info) {
         Batch* b = S->running[s];
         if (!b) continue;
         const cudaError_t e = cudaEventQuery(b->ev);
-        if (e == cudaErrorNotReady) continue;
+        if (e == cudaErrorNotReady) {
+            // frames of the running batch whose last task finished
+            bool any = false;
+            const double t = S->now_ms();
+            for (size_t i = 0; i < b->tickets.size(); i++) {
+                if (b->early[i] || b->slot[i] < 0) continue;
+                if (reinterpret_cast<volatile unsigned int*>(S->h_done[s])[b->slot[i]] == 0u) continue;
+                b->early[i] = 1;
+                std::lock_guard<std::mutex> lk(S->mu);
+                auto it = S->reqs.find(b->tickets[i]);
+                if (it == S->reqs.end()) continue;
+                it->second.t.status = DRK_OK;
+                it->second.t.end_ms = t;
+                it->second.done = true;
+                any = true;
+            }
+            if (any) S->cv_done.notify_all();
+            continue;
+        }
         if (e != cudaSuccess) cudaGetLastError();
         const double t = S->now_ms();
         const int m = (int)b->tickets.size();
@@ -163,7 +187,7 @@ void retire(drk_serve* S, std::unique_ptr<BatchInfo>* info) {
                     const double ppp = bi.npix[i] > 0 ? (double)bi.pairs[i] / bi.npix[i] : 0.0;
                     sc.pairs_per_pixel = sc.pairs_per_pixel < 0 ? ppp : std::max(ppp, 0.9 * sc.pairs_per_pixel);
                 }
-                r.t.end_ms = t;
+                if (!b->early[i]) r.t.end_ms = t;
                 r.done = true;
             }
             S->inflight_bytes -= std::min(S->inflight_bytes, b->bytes);
@@ -249,6 +273,8 @@ void run_batch(drk_serve* S, int s, std::vector<Item>& items, int* countdown, st
     b->stream = s;
     b->tickets.resize(m);
     b->ok.assign(m, 1);
+    b->slot.assign(m, -1);
+    b->early.assign(m, 0);
     std::vector<int> status(m, DRK_OK);
     b->al.reset(new Allocs(S->pool, st));
     if (*countdown >= 0) b->al->fail_countdown = countdown;
@@ -357,10 +383,16 @@ void run_batch(drk_serve* S, int s, std::vector<Item>& items, int* countdown, st
             fs.dq = w.A.dq;
             fs.out_rgb = items[i].out;
             fs.K = items[i].p.K;
+            fs.task_left = S->d_left[s] + slot;
+            fs.done_flag = S->d_done[s] + slot;
+            S->h_left[s][slot] = (unsigned int)w.F.n_tiles * 8u;
+            S->h_done[s][slot] = 0u;
+            b->slot[i] = slot;
             off += w.F.n_tiles;
             slot++;
         }
         cudaMemcpyAsync(S->d_slots[s], S->h_slots[s], sizeof(FrameSlot) * (size_t)live, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(S->d_left[s], S->h_left[s], sizeof(unsigned int) * (size_t)live, cudaMemcpyHostToDevice, st);
         radix_sort_pairs(okeys, ovals, okalt, ovalt, T, 26, oscr, st);
         RasterArgs R;
         std::memset(&R, 0, sizeof(R));
@@ -459,6 +491,9 @@ void free_server(drk_serve* S) {
         cudaFree(S->d_counters[s]);
         cudaFree(S->d_task[s]);
         if (S->ovf[s]) cudaFree(S->ovf[s]);
+        cudaFree(S->d_left[s]);
+        if (S->h_left[s]) cudaFreeHost(S->h_left[s]);
+        if (S->h_done[s]) cudaFreeHost(S->h_done[s]);
         if (S->ev_phase_a[s]) cudaEventDestroy(S->ev_phase_a[s]);
         if (S->ev_done[s]) cudaEventDestroy(S->ev_done[s]);
         if (S->streams[s]) cudaStreamDestroy(S->streams[s]);
@@ -522,7 +557,11 @@ drk_status_t drk_serve_create(int device, size_t mem_budget, int max_batch, cons
              cudaMalloc(&S->d_counters[s], sizeof(unsigned long long) * nctr) == cudaSuccess &&
              cudaMalloc(&S->d_task[s], sizeof(unsigned int)) == cudaSuccess &&
              cudaEventCreateWithFlags(&S->ev_phase_a[s], cudaEventDisableTiming) == cudaSuccess &&
-             cudaEventCreateWithFlags(&S->ev_done[s], cudaEventDisableTiming) == cudaSuccess;
+             cudaEventCreateWithFlags(&S->ev_done[s], cudaEventDisableTiming) == cudaSuccess &&
+             cudaMalloc(&S->d_left[s], sizeof(unsigned int) * kMaxBatch) == cudaSuccess &&
+             cudaMallocHost(&S->h_left[s], sizeof(unsigned int) * kMaxBatch) == cudaSuccess &&
+             cudaHostAlloc(&S->h_done[s], sizeof(unsigned int) * kMaxBatch, cudaHostAllocMapped) == cudaSuccess &&
+             cudaHostGetDevicePointer(reinterpret_cast<void**>(&S->d_done[s]), S->h_done[s], 0) == cudaSuccess;
     }
     if (!ok) {
         cudaGetLastError();
