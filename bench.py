@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-pixels", type=int, default=1024, help="oracle sample size (pixels, fwd+bwd)")
+    ap.add_argument("--cull-level", type=int, default=2, choices=(0, 1, 2),
+                    help="tile culling: 0 none, 1 screen rectangle, 2 per-tile test (same image)")
     ap.add_argument("--kbuf-capacity", type=int, default=8, choices=(8, 16, 32),
                     help="per-pixel depth-order buffer entries (any value gives the same image)")
     ap.add_argument("--serve", action="store_true",
@@ -239,7 +241,7 @@ def run_drk(args):
     H, W = cam.height, cam.width
     ds = drk.DeviceScene.from_scene(scene, dev)
     target = torch.from_numpy(synth.target_image(H, W)).to(dev)
-    opt = drk.Options(kbuf_capacity=args.kbuf_capacity)
+    opt = drk.Options(kbuf_capacity=args.kbuf_capacity, cull_level=args.cull_level)
     ctx = drk.Context(local)
     out = dict(rgb=torch.empty((3, H, W), device=dev), T=None, n=None)
     inv_n = 1.0 / float(3 * H * W)
