@@ -41,6 +41,10 @@
  *   R7  colour: plain RGB, or real spherical harmonics of degree <= 3 in the
  *       view direction camera centre -> mu, plus 0.5, clamped below at 0.
  *   R8  background colour bg is added with the final transmittance.
+ *   R9  order_mode 1 composites in the order of the paper's cache-sorting
+ *       (Sec. 4.4 "Cache Sorting", supplementary Algorithm 1) instead of the
+ *       exact order: pre-sort by centre depth, a cache of cache_len entries
+ *       sorted by r_t whose smallest is composited when it overflows.
  */
 #include <math.h>
 #include <stdint.h>
@@ -81,6 +85,8 @@ typedef struct {
 typedef struct {
     double alpha_min, T_min, alpha_max, lowpass_sl, near_plane;
     double bg[3];
+    int order_mode;         /* 0: exact (r_t, index) order; 1: the paper's cache-sorting */
+    int cache_len;          /* cache length of order_mode 1 (the paper uses 8) */
 } ord_options;
 
 /* parity flags written per pixel by ord_render */
@@ -478,6 +484,65 @@ static int contrib_cmp(const void *pa, const void *pb)
     return (a->idx > b->idx) - (a->idx < b->idx);
 }
 
+/* view-space depth of the primitive centre (the pre-sort key of the paper's
+ * cache-sorting study, "vanilla" 3D-GS ordering)                           */
+static double centre_depth(const ord_params *P, const ord_camera *cam, int64_t i)
+{
+    const double *m = P->mu + 3 * i, *M = cam->w2c;
+    return M[8] * m[0] + M[9] * m[1] + M[10] * m[2] + M[11];
+}
+
+typedef struct { double zc; int64_t idx; int64_t pos; } presort_key;
+
+static int presort_cmp(const void *pa, const void *pb)
+{
+    const presort_key *a = (const presort_key *)pa, *b = (const presort_key *)pb;
+    if (a->zc < b->zc) return -1;
+    if (a->zc > b->zc) return 1;
+    return (a->idx > b->idx) - (a->idx < b->idx);
+}
+
+/* The paper's cache-sorting (Sec. 4.4 "Cache Sorting", supplementary
+ * Algorithm 1) applied to the contributors of one pixel, which buf holds
+ * sorted by (r_t, index): the pixel meets them in the order of the pre-sort
+ * (centre depth, index); each is inserted into a cache kept sorted by
+ * (r_t, index); when the cache holds more than cache_len entries, its
+ * smallest is composited (reading: Sec. 4.4 pops "the kernel with the
+ * smallest r_t" once the array is full); at the end of the list the cache
+ * is composited in order.  Rewrites buf in compositing order.  Returns 1
+ * if two contributors have centre depths within 1e-6 (relative), where a
+ * float32 pre-sort may order them differently.                            */
+static int cache_sort_order(const ord_params *P, const ord_camera *cam, contrib *buf, int64_t cnt, int cache_len,
+                            contrib *out, presort_key *keys)
+{
+    for (int64_t j = 0; j < cnt; j++) {
+        keys[j].zc = centre_depth(P, cam, buf[j].idx);
+        keys[j].idx = buf[j].idx;
+        keys[j].pos = j;
+    }
+    qsort(keys, (size_t)cnt, sizeof(presort_key), presort_cmp);
+    int tie = 0;
+    for (int64_t j = 1; j < cnt; j++)
+        if (keys[j].zc - keys[j - 1].zc <= 1e-6 * fabs(keys[j].zc)) tie = 1;
+    /* cache: positions into buf (buf's order is (r_t, index)), kept sorted */
+    int64_t *cache = (int64_t *)malloc(sizeof(int64_t) * (size_t)(cache_len + 1));
+    int64_t nc = 0, no = 0;
+    for (int64_t j = 0; j < cnt; j++) {
+        int64_t q = keys[j].pos, w = nc++;
+        while (w > 0 && cache[w - 1] > q) { cache[w] = cache[w - 1]; w--; }
+        cache[w] = q;
+        if (nc > cache_len) {
+            out[no++] = buf[cache[0]];
+            for (int64_t l = 1; l < nc; l++) cache[l - 1] = cache[l];
+            nc--;
+        }
+    }
+    for (int64_t l = 0; l < nc; l++) out[no++] = buf[cache[l]];
+    free(cache);
+    memcpy(buf, out, sizeof(contrib) * (size_t)cnt);
+    return tie;
+}
+
 static int64_t gather_contributors(const ord_params *P, const ord_camera *cam, const ord_options *opt,
                                    const double *ocam, int px, int py, contrib *buf, int *near_amin)
 {
@@ -497,6 +562,14 @@ static int64_t gather_contributors(const ord_params *P, const ord_camera *cam, c
         }
     }
     qsort(buf, (size_t)cnt, sizeof(contrib), contrib_cmp);
+    if (opt->order_mode == 1 && cnt > 0) {
+        contrib *out = (contrib *)malloc(sizeof(contrib) * (size_t)cnt);
+        presort_key *keys = (presort_key *)malloc(sizeof(presort_key) * (size_t)cnt);
+        if (out && keys && cache_sort_order(P, cam, buf, cnt, opt->cache_len > 0 ? opt->cache_len : 8, out, keys))
+            *near_amin |= 2;
+        free(out);
+        free(keys);
+    }
     return cnt;
 }
 
@@ -546,7 +619,8 @@ int ord_render(const ord_params *P, const ord_camera *cam, const ord_options *op
             int64_t cnt = gather_contributors(P, cam, opt, ocam, px, py, buf, &near_amin);
             int64_t nc = composite_count(buf, cnt, opt->T_min);
             double C[3] = {0, 0, 0}, T = 1.0;
-            int flag = near_amin ? ORD_FLAG_ALPHA_MIN : 0;
+            int flag = (near_amin & 1) ? ORD_FLAG_ALPHA_MIN : 0;
+            if (near_amin & 2) flag |= ORD_FLAG_DEPTH_TIE;
             double cmax = 1.0;
             for (int c = 0; c < 3; c++) cmax = fmax(cmax, fabs(opt->bg[c]));
             double dT_rel = 0.0;     /* float32 error estimate of T (relative) */
@@ -565,7 +639,7 @@ int ord_render(const ord_params *P, const ord_camera *cam, const ord_options *op
                     flag |= ORD_FLAG_T_MIN;
                 if (j == nc) break;
                 /* near-equal depths whose swap is visible */
-                for (int64_t l = j + 1; l < cnt && buf[l].t - buf[j].t <= 2e-6 * buf[l].t; l++) {
+                for (int64_t l = j + 1; opt->order_mode == 0 && l < cnt && buf[l].t - buf[j].t <= 2e-6 * buf[l].t; l++) {
                     double cl_rgb[3];
                     int cl2[3];
                     prim_color(P, buf[l].idx, ocam, cl_rgb, cl2);

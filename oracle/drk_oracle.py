@@ -42,6 +42,8 @@ class Options:
     lowpass_sl: float = 1.0 / math.sqrt(2.0)
     near: float = 0.2
     bg: tuple = (0.0, 0.0, 0.0)
+    order_mode: int = 0          # 0 exact (r_t, index) order; 1 the paper's cache-sorting
+    cache_len: int = 8
 
 
 class _Params(C.Structure):
@@ -61,7 +63,8 @@ class _Camera(C.Structure):
 
 class _Options(C.Structure):
     _fields_ = [("alpha_min", C.c_double), ("T_min", C.c_double), ("alpha_max", C.c_double),
-                ("lowpass_sl", C.c_double), ("near_plane", C.c_double), ("bg", C.c_double * 3)]
+                ("lowpass_sl", C.c_double), ("near_plane", C.c_double), ("bg", C.c_double * 3),
+                ("order_mode", C.c_int), ("cache_len", C.c_int)]
 
 
 def build(force: bool = False) -> str:
@@ -154,6 +157,7 @@ def _options(opt: Options) -> _Options:
     o.lowpass_sl, o.near_plane = opt.lowpass_sl, opt.near
     for i in range(3):
         o.bg[i] = float(opt.bg[i])
+    o.order_mode, o.cache_len = int(opt.order_mode), int(opt.cache_len)
     return o
 
 

@@ -378,3 +378,57 @@ def test_backward_matches_central_differences(sh_degree, sl):
                 assert an == pytest.approx(fd, rel=2e-5, abs=2e-7 * (1 + abs(fd))), (name, index, an, fd)
                 checked += 1
     assert checked > 100
+
+
+# ---------------------------------------------------------------------------
+# the paper's cache-sorting (Sec. 4.4 "Cache Sorting", supplementary
+# Algorithm 1) as an alternative compositing order
+
+def _literal(opt, cache_len=8):
+    import dataclasses
+    return dataclasses.replace(opt, order_mode=1, cache_len=cache_len)
+
+
+def test_cache_sort_with_a_long_cache_is_the_exact_order():
+    scene = synth.scene_clustered(1500, 8, seed=2200, n_clusters=6, sh_degree=-1)
+    cam = synth.camera_front(40, 32)
+    opt = O.Options()
+    exact = O.render(scene, cam, opt)
+    lit = O.render(scene, cam, _literal(opt, cache_len=100000))
+    np.testing.assert_array_equal(exact["rgb"], lit["rgb"])
+    np.testing.assert_array_equal(exact["T"], lit["T"])
+
+
+def test_cache_sort_order_matches_an_independent_simulation():
+    import bisect
+    scene = synth.scene_clustered(1500, 8, seed=2201, n_clusters=6, sh_degree=-1)
+    cam = synth.camera_front(40, 32)
+    opt = O.Options()
+    w2c = np.asarray(cam.world_to_cam, np.float64).reshape(3, 4)
+    zc = np.asarray(scene.mu, np.float64) @ w2c[2, :3] + w2c[2, 3]
+    rng = np.random.default_rng(5)
+    checked = 0
+    for _ in range(30):
+        px, py = int(rng.integers(0, 40)), int(rng.integers(0, 32))
+        idx, t, _, _ = O.contributors(scene, cam, opt, px, py)          # exact (r_t, index) order
+        lidx, _, _, _ = O.contributors(scene, cam, _literal(opt, 2), px, py)
+        rank = {int(i): k for k, i in enumerate(idx)}                     # position in the exact order
+        pre = sorted(idx, key=lambda i: (zc[i], i))                       # pre-sort by centre depth
+        cache, out = [], []
+        for i in pre:
+            bisect.insort(cache, rank[int(i)])
+            if len(cache) > 2:
+                out.append(int(idx[cache.pop(0)]))
+        out += [int(idx[k]) for k in cache]
+        assert out == [int(i) for i in lidx]
+        checked += len(out) > 2
+    assert checked >= 8     # pixels whose cache overflowed
+
+
+def test_cache_sort_weights_sum_to_one_minus_T():
+    scene = synth.scene_clustered(1500, 8, seed=2202, n_clusters=6, sh_degree=-1)
+    scene.color[:] = 1.0                                                 # white: C = sum of weights
+    cam = synth.camera_front(32, 24)
+    opt = _literal(O.Options(bg=(0.0, 0.0, 0.0)), cache_len=2)
+    r = O.render(scene, cam, opt)
+    np.testing.assert_allclose(r["rgb"][0], 1.0 - r["T"], atol=1e-12)
