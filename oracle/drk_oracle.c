@@ -505,31 +505,20 @@ static int presort_cmp(const void *pa, const void *pb)
 /* The paper's cache-sorting (Sec. 4.4 "Cache Sorting", supplementary
  * Algorithm 1) applied to the contributors of one pixel, which buf holds
  * sorted by (r_t, index): the pixel meets them in the order of the pre-sort
- * (centre depth, index); each is inserted into a cache kept sorted by
+ * (keys: centre depth, index); each is inserted into a cache kept sorted by
  * (r_t, index); when the cache holds more than cache_len entries, its
  * smallest is composited (reading: Sec. 4.4 pops "the kernel with the
  * smallest r_t" once the array is full); at the end of the list the cache
- * is composited in order.  Rewrites buf in compositing order.  Returns 1
- * if two contributors have centre depths within 1e-6 (relative), where a
- * float32 pre-sort may order them differently.                            */
-static int cache_sort_order(const ord_params *P, const ord_camera *cam, contrib *buf, int64_t cnt, int cache_len,
-                            contrib *out, presort_key *keys)
+ * is composited in order.  rank[j] is the (r_t, index) rank of buf[j]
+ * (NULL: j itself).  Writes the compositing order to out.                  */
+static void cache_sort_order(const contrib *buf, int64_t cnt, int cache_len, const presort_key *keys,
+                             const int64_t *rank, int64_t *cache, contrib *out)
 {
-    for (int64_t j = 0; j < cnt; j++) {
-        keys[j].zc = centre_depth(P, cam, buf[j].idx);
-        keys[j].idx = buf[j].idx;
-        keys[j].pos = j;
-    }
-    qsort(keys, (size_t)cnt, sizeof(presort_key), presort_cmp);
-    int tie = 0;
-    for (int64_t j = 1; j < cnt; j++)
-        if (keys[j].zc - keys[j - 1].zc <= 1e-6 * fabs(keys[j].zc)) tie = 1;
-    /* cache: positions into buf (buf's order is (r_t, index)), kept sorted */
-    int64_t *cache = (int64_t *)malloc(sizeof(int64_t) * (size_t)(cache_len + 1));
     int64_t nc = 0, no = 0;
     for (int64_t j = 0; j < cnt; j++) {
         int64_t q = keys[j].pos, w = nc++;
-        while (w > 0 && cache[w - 1] > q) { cache[w] = cache[w - 1]; w--; }
+        int64_t rq = rank ? rank[q] : q;
+        while (w > 0 && (rank ? rank[cache[w - 1]] : cache[w - 1]) > rq) { cache[w] = cache[w - 1]; w--; }
         cache[w] = q;
         if (nc > cache_len) {
             out[no++] = buf[cache[0]];
@@ -538,8 +527,87 @@ static int cache_sort_order(const ord_params *P, const ord_camera *cam, contrib 
         }
     }
     for (int64_t l = 0; l < nc; l++) out[no++] = buf[cache[l]];
-    free(cache);
+}
+
+/* colour of a compositing order (Eq. 1 with the T_min stop of reading R5) */
+static void order_colour(const ord_params *P, const double *ocam, const ord_options *opt, const contrib *buf,
+                         int64_t cnt, double *rgb)
+{
+    double T = 1.0;
+    rgb[0] = rgb[1] = rgb[2] = 0.0;
+    for (int64_t j = 0; j < cnt; j++) {
+        double Tn = T * (1.0 - buf[j].alpha);
+        if (Tn < opt->T_min) break;
+        double cj[3];
+        int cl[3];
+        prim_color(P, buf[j].idx, ocam, cj, cl);
+        for (int c = 0; c < 3; c++) rgb[c] += T * buf[j].alpha * cj[c];
+        T = Tn;
+    }
+    for (int c = 0; c < 3; c++) rgb[c] += T * opt->bg[c];
+}
+
+static double max_abs_diff3(const double *a, const double *b);
+
+/* Rewrites buf (sorted by (r_t, index)) in the cache-sorting order.
+ * Returns 1 where float32 may take another order with a visible effect:
+ * two neighbours in the pre-sort with centre depths within 1e-6
+ * (relative), or two r_t within 2e-6 (relative), whose exchange moves the
+ * colour by more than 5e-5.  Each tie is tested by re-running the cache
+ * with the pair exchanged: an exchange changes which entries the cache
+ * pops later, so its effect is not bounded by the two contributors alone.
+ * Returns -1 on allocation failure.                                        */
+static int cache_sort_pixel(const ord_params *P, const ord_camera *cam, const ord_options *opt,
+                            const double *ocam, contrib *buf, int64_t cnt)
+{
+    const int cache_len = opt->cache_len > 0 ? opt->cache_len : 8;
+    presort_key *keys = (presort_key *)malloc(sizeof(presort_key) * (size_t)cnt);
+    contrib *out = (contrib *)malloc(sizeof(contrib) * (size_t)cnt);
+    int64_t *rank = (int64_t *)malloc(sizeof(int64_t) * (size_t)cnt);
+    int64_t *cache = (int64_t *)malloc(sizeof(int64_t) * (size_t)(cache_len + 1));
+    int tie = 0;
+    if (!keys || !out || !rank || !cache) {
+        tie = -1;
+        goto done;
+    }
+    for (int64_t j = 0; j < cnt; j++) {
+        keys[j].zc = centre_depth(P, cam, buf[j].idx);
+        keys[j].idx = buf[j].idx;
+        keys[j].pos = j;
+        rank[j] = j;
+    }
+    qsort(keys, (size_t)cnt, sizeof(presort_key), presort_cmp);
+    double base[3], alt[3];
+    cache_sort_order(buf, cnt, cache_len, keys, NULL, cache, out);
+    order_colour(P, ocam, opt, out, cnt, base);
+    for (int64_t j = 1; j < cnt && !tie; j++) {
+        if (keys[j].zc - keys[j - 1].zc > 1e-6 * fabs(keys[j].zc)) continue;
+        presort_key k = keys[j];
+        keys[j] = keys[j - 1];
+        keys[j - 1] = k;
+        cache_sort_order(buf, cnt, cache_len, keys, NULL, cache, out);
+        order_colour(P, ocam, opt, out, cnt, alt);
+        if (max_abs_diff3(base, alt) > 5e-5) tie = 1;
+        keys[j - 1] = keys[j];
+        keys[j] = k;
+    }
+    for (int64_t j = 0; j < cnt && !tie; j++)
+        for (int64_t l = j + 1; l < cnt && buf[l].t - buf[j].t <= 2e-6 * buf[l].t && !tie; l++) {
+            rank[j] = l;
+            rank[l] = j;
+            cache_sort_order(buf, cnt, cache_len, keys, rank, cache, out);
+            order_colour(P, ocam, opt, out, cnt, alt);
+            if (max_abs_diff3(base, alt) > 5e-5) tie = 1;
+            rank[j] = j;
+            rank[l] = l;
+        }
+    cache_sort_order(buf, cnt, cache_len, keys, NULL, cache, out);
     memcpy(buf, out, sizeof(contrib) * (size_t)cnt);
+done:
+    free(keys);
+    free(out);
+    free(rank);
+    free(cache);
     return tie;
 }
 
@@ -563,12 +631,9 @@ static int64_t gather_contributors(const ord_params *P, const ord_camera *cam, c
     }
     qsort(buf, (size_t)cnt, sizeof(contrib), contrib_cmp);
     if (opt->order_mode == 1 && cnt > 0) {
-        contrib *out = (contrib *)malloc(sizeof(contrib) * (size_t)cnt);
-        presort_key *keys = (presort_key *)malloc(sizeof(presort_key) * (size_t)cnt);
-        if (out && keys && cache_sort_order(P, cam, buf, cnt, opt->cache_len > 0 ? opt->cache_len : 8, out, keys))
-            *near_amin |= 2;
-        free(out);
-        free(keys);
+        int r = cache_sort_pixel(P, cam, opt, ocam, buf, cnt);
+        if (r < 0) return -1;
+        if (r) *near_amin |= 2;
     }
     return cnt;
 }
@@ -617,6 +682,11 @@ int ord_render(const ord_params *P, const ord_camera *cam, const ord_options *op
             int px = pix[2 * q], py = pix[2 * q + 1];
             int near_amin;
             int64_t cnt = gather_contributors(P, cam, opt, ocam, px, py, buf, &near_amin);
+            if (cnt < 0) {
+#pragma omp atomic write
+                fail = 1;
+                continue;
+            }
             int64_t nc = composite_count(buf, cnt, opt->T_min);
             double C[3] = {0, 0, 0}, T = 1.0;
             int flag = (near_amin & 1) ? ORD_FLAG_ALPHA_MIN : 0;
@@ -673,6 +743,10 @@ int64_t ord_contributors(const ord_params *P, const ord_camera *cam, const ord_o
     if (!buf) return -1;
     int near_amin;
     int64_t cnt = gather_contributors(P, cam, opt, ocam, px, py, buf, &near_amin);
+    if (cnt < 0) {
+        free(buf);
+        return -1;
+    }
     for (int64_t j = 0; j < cnt && j < cap; j++) {
         idx[j] = buf[j].idx;
         t[j] = buf[j].t;
@@ -847,6 +921,11 @@ int ord_render_backward(const ord_params *P, const ord_camera *cam, const ord_op
             const double *gC = dL_drgb + 3 * q;
             int near_amin;
             int64_t cnt = gather_contributors(P, cam, opt, ocam, px, py, buf, &near_amin);
+            if (cnt < 0) {
+#pragma omp atomic write
+                fail = 1;
+                continue;
+            }
             int64_t nc = composite_count(buf, cnt, opt->T_min);
             double T = 1.0;
             for (int64_t j = 0; j < nc; j++) {

@@ -14,7 +14,8 @@ def f32(x):
 def oracle_options(opt) -> O.Options:
     """The oracle's options with the float32 values the GPU uses."""
     return O.Options(alpha_min=f32(opt.alpha_min), T_min=f32(opt.T_min), alpha_max=f32(opt.alpha_max),
-                     lowpass_sl=f32(opt.lowpass_sl), near=f32(opt.near_plane), bg=tuple(f32(b) for b in opt.bg))
+                     lowpass_sl=f32(opt.lowpass_sl), near=f32(opt.near_plane), bg=tuple(f32(b) for b in opt.bg),
+                     order_mode=int(getattr(opt, "order_mode", 0)), cache_len=int(opt.kbuf_capacity))
 
 
 def excluded(flags: np.ndarray) -> np.ndarray:
