@@ -99,6 +99,18 @@ typedef struct {
     float world_to_cam[12];     /* host values, row-major 3 x 4 */
 } drk_camera_t;
 
+/* Compositing orders.  DRK_ORDER_EXACT composites each pixel's contributors
+ * in exact (r_t, primitive index) order.  DRK_ORDER_CACHE_SORT is the
+ * paper's cache-sorting (Sec. 4.4 "Cache Sorting", supplementary
+ * Algorithm 1), an approximation kept for comparison: pairs are pre-sorted
+ * by the view-space depth of the primitive centre, and each pixel keeps a
+ * cache of kbuf_capacity contributors sorted by r_t whose smallest entry is
+ * composited when it overflows.  Forward only (no backward state). */
+enum {
+    DRK_ORDER_EXACT = 0,
+    DRK_ORDER_CACHE_SORT = 1
+};
+
 /* Tile culling levels (Sec. 4.4, "Kernel Culling").  All three give the
  * same image bit for bit: culling only removes pairs that cannot reach
  * alpha_min. */
@@ -125,7 +137,8 @@ typedef struct {
                              (any value gives the same image): 0 = 2048
                              (default), 1..2048, or -1 = none (a full heap
                              then takes extra passes over the list) */
-    int32_t reserved[5];  /* must be zero */
+    int32_t order_mode;   /* DRK_ORDER_*; default DRK_ORDER_EXACT */
+    int32_t reserved[4];  /* must be zero */
 } drk_options_t;
 
 /* Fills *opt with the defaults listed above. */

@@ -190,7 +190,9 @@ drk_status_t validate(const drk_params_t* p, const drk_camera_t* cam, const drk_
         return fail(DRK_ERR_INVALID_ARG, "kbuf_capacity must be 8, 16 or 32");
     if (opt->ovf_capacity < -1 || opt->ovf_capacity > 2048)
         return fail(DRK_ERR_INVALID_ARG, "ovf_capacity not in -1..2048");
-    for (int i = 0; i < 5; i++)
+    if (opt->order_mode != DRK_ORDER_EXACT && opt->order_mode != DRK_ORDER_CACHE_SORT)
+        return fail(DRK_ERR_INVALID_ARG, "order_mode not in 0..1");
+    for (int i = 0; i < 4; i++)
         if (opt->reserved[i] != 0) return fail(DRK_ERR_INVALID_ARG, "reserved option fields must be zero");
     for (int i = 0; i < 3; i++)
         if (!std::isfinite(opt->bg[i])) return fail(DRK_ERR_INVALID_ARG, "non-finite bg");
@@ -213,6 +215,7 @@ Frame make_frame(const drk_params_t* p, const drk_camera_t* cam, const drk_optio
     fc.alpha_max = opt->alpha_max;
     fc.T_min = opt->T_min;
     for (int c = 0; c < 3; c++) fc.bg[c] = opt->bg[c];
+    fc.order_mode = opt->order_mode;
     F.cam.fx = cam->fx; F.cam.fy = cam->fy; F.cam.cx = cam->cx; F.cam.cy = cam->cy;
     for (int i = 0; i < 12; i++) F.cam.w2c[i] = cam->world_to_cam[i];
     const float* M = cam->world_to_cam;
@@ -267,6 +270,24 @@ drk_status_t frame_phase_a(FrameWork& w, const drk_params_t* params, const drk_c
     DRK_CUDA(cudaMemsetAsync(A.zmax_bits, 0, sizeof(int), st));
     cudaEvent_t ev = tm ? tm->begin(st) : nullptr;
     if (F.kmax == 8) launch_preprocess<8>(A, st); else launch_preprocess<16>(A, st);
+    if (opt->order_mode == DRK_ORDER_CACHE_SORT && n > 0) {
+        // pre-sort of the paper's cache-sorting: pair keys carry the rank of
+        // the primitive's centre depth instead of the depth bound
+        if ((uint64_t)n >= (uint64_t(1) << F.depth_bits) - 1)
+            return fail(DRK_ERR_INVALID_ARG, "cache-sorting order: %lld primitives exceed the %d-bit rank field",
+                        (long long)n, F.depth_bits);
+        uint32_t *rk = nullptr, *rv = nullptr, *ra = nullptr, *rb = nullptr, *rank = nullptr;
+        uint8_t* rscr = nullptr;
+        if ((s = al.get(&rk, (size_t)n)) != DRK_OK) return s;
+        if ((s = al.get(&rv, (size_t)n)) != DRK_OK) return s;
+        if ((s = al.get(&ra, (size_t)n)) != DRK_OK) return s;
+        if ((s = al.get(&rb, (size_t)n)) != DRK_OK) return s;
+        if ((s = al.get(&rank, (size_t)n)) != DRK_OK) return s;
+        if ((s = al.get(&rscr, radix_sort_scratch_bytes(n))) != DRK_OK) return s;
+        if (F.kmax == 8) launch_centre_rank<8>(A, rk, rv, ra, rb, rscr, rank, st);
+        else launch_centre_rank<16>(A, rk, rv, ra, rb, rscr, rank, st);
+        A.rank = rank;
+    }
     if (opt->cull_level >= 2) {
         if (F.kmax == 8) launch_count<8>(A, st); else launch_count<16>(A, st);
     }
@@ -383,6 +404,8 @@ drk_status_t drk_render(drk_ctx_t* ctx, const drk_params_t* params, const drk_ca
     drk_status_t s = validate(params, cam, opt);
     if (s != DRK_OK) return s;
     if (!out || !out->rgb) return fail(DRK_ERR_INVALID_ARG, "null output image");
+    if (state && opt->order_mode != DRK_ORDER_EXACT)
+        return fail(DRK_ERR_INVALID_ARG, "the cache-sorting order has no backward (render without a state)");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     DRK_CUDA(cudaSetDevice(ctx->device));
     ctx->last_stream = st;
@@ -512,6 +535,7 @@ drk_status_t drk_render_backward(drk_ctx_t* ctx, const drk_params_t* params, con
     if (params->n != state->n || params->K != state->K || cam->width != state->width || cam->height != state->height ||
         params->sh_degree != state->sh_degree || opt->kbuf_capacity != state->cap)
         return fail(DRK_ERR_INVALID_ARG, "backward arguments do not match the forward state");
+    if (opt->order_mode != DRK_ORDER_EXACT) return fail(DRK_ERR_INVALID_ARG, "the cache-sorting order has no backward");
     const int64_t n = params->n;
     if (n > 0 && (!grads->mu || !grads->quat || !grads->scale || !grads->theta || !grads->eta || !grads->tau ||
                   !grads->opacity || !grads->color))

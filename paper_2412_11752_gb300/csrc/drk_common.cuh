@@ -97,7 +97,8 @@ struct Rec {
 enum : int { B_X0 = 0, B_Y0, B_X1, B_Y1, B_ZLB, B_FCX, B_FCY, B_FR2, B_FLAGS, B_RHOMAX, B_RHO = 10 };
 template <int KMAX>
 struct Bnd {
-    static constexpr int STRIDE = ((B_RHO + KMAX) + 3) / 4 * 4;
+    static constexpr int ZC = B_RHO + KMAX;                    // view-space depth of mu
+    static constexpr int STRIDE = ((ZC + 1) + 3) / 4 * 4;
 };
 
 // Per-primitive record-space gradient accumulator used between the raster
@@ -283,6 +284,7 @@ struct FrameConst {
     float ifx, ify, ox, oy;          // ray: d = (x ifx + ox, y ify + oy, 1)
     float near_plane, alpha_min, alpha_max, T_min;
     float bg[3];
+    int order_mode;                  // DRK_ORDER_EXACT or DRK_ORDER_CACHE_SORT
 };
 
 __device__ __forceinline__ PixelRay make_ray(const FrameConst& fc, int x, int y) {

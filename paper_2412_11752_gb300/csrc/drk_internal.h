@@ -37,6 +37,7 @@ struct PreArgs {
     uint32_t* vals;         // pair values (primitive index)
     unsigned long long* counters;  // [3]: primitives with at least one pair
     int* status;                   // device status bits (1 << drk_status_t)
+    const uint32_t* rank;          // cache-sorting mode: rank of each primitive by centre depth (else null)
 };
 
 // One frame of a batched forward raster (serving): everything the raster
@@ -118,6 +119,10 @@ template <int KMAX> void launch_emit(const PreArgs& A, cudaStream_t st);
 template <int KMAX>
 void launch_preprocess_backward(const PreArgs& A, const float* gtmp, const drk_params_grad_t& g, cudaStream_t st);
 void launch_depth_quant(const PreArgs& A, cudaStream_t st);
+// rank of every primitive in (centre depth, index) order (cache-sorting mode)
+template <int KMAX>
+void launch_centre_rank(const PreArgs& A, uint32_t* keys, uint32_t* vals, uint32_t* kalt, uint32_t* valt,
+                        void* scratch, uint32_t* rank, cudaStream_t st);
 
 size_t scan_scratch_bytes(int64_t n);
 void exclusive_scan_u32_u64(const uint32_t* in, uint64_t* out, int64_t n, void* scratch, cudaStream_t st);

@@ -348,6 +348,7 @@ __global__ void __launch_bounds__(128) preprocess_kernel(PreArgs A) {
     bnd[B_RHOMAX] = rho_max;
     for (int k = 0; k < KMAX; k++) bnd[B_RHO + k] = rho[k];
     for (int j = B_RHO + KMAX; j < Bnd<KMAX>::STRIDE; j++) bnd[j] = 0.f;
+    bnd[Bnd<KMAX>::ZC] = G.muc[2];
     const bool nonempty = x1 >= x0 && y1 >= y0;
     A.count[i] = nonempty ? (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1)) : 0u;
     if (nonempty && kernel_on && !crosses_near) atomicMax(A.zmax_bits, __float_as_int(fmaxf(zub, A.fc.near_plane)));
@@ -500,8 +501,13 @@ __global__ void __launch_bounds__(256) emit_kernel(PreArgs A) {
             const int tx = x0 + j % wdt, ty = y0 + j / wdt;
             float lb;
             keep = tile_test<KMAX>(rec, bnd, A.p.K, A.fc, tx, ty, cull, lb);
-            const float qf = floorf((lb - dq.zmin) * dq.scale);
-            const uint32_t qd = qf <= 0.f ? 0u : (qf >= (float)qmax ? qmax : (uint32_t)qf);
+            uint32_t qd;
+            if (A.rank) {
+                qd = A.rank[i];   // pre-sort by centre depth (the paper's cache-sorting mode)
+            } else {
+                const float qf = floorf((lb - dq.zmin) * dq.scale);
+                qd = qf <= 0.f ? 0u : (qf >= (float)qmax ? qmax : (uint32_t)qf);
+            }
             key = ((uint32_t)(ty * A.fc.tiles_x + tx) << dq.depth_bits) | qd;
         }
         const uint32_t m = __ballot_sync(0xffffffffu, keep);
@@ -524,6 +530,38 @@ __global__ void __launch_bounds__(256) emit_kernel(PreArgs A) {
         A.vals[pos] = (uint32_t)i;
     }
 }
+
+// Pre-sort of the cache-sorting mode: the rank of every primitive in the
+// order (view-space depth of mu, index).  keys: order-preserving bits of the
+// depth; a stable sort by them leaves equal depths in index order.
+__global__ void centre_key_kernel(const float* __restrict__ bnd, int stride, int zc, int64_t n,
+                                  uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t b = __float_as_uint(bnd[(int64_t)stride * i + zc]);
+    keys[i] = (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+    vals[i] = (uint32_t)i;
+}
+__global__ void rank_scatter_kernel(const uint32_t* __restrict__ vals, int64_t n, uint32_t* __restrict__ rank) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    rank[vals[k]] = (uint32_t)k;
+}
+
+template <int KMAX>
+void launch_centre_rank(const PreArgs& A, uint32_t* keys, uint32_t* vals, uint32_t* kalt, uint32_t* valt,
+                        void* scratch, uint32_t* rank, cudaStream_t st) {
+    const int64_t n = A.p.n;
+    if (n <= 0) return;
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    centre_key_kernel<<<blocks, 256, 0, st>>>(A.bnd, Bnd<KMAX>::STRIDE, Bnd<KMAX>::ZC, n, keys, vals); note_launch();
+    radix_sort_pairs(keys, vals, kalt, valt, n, 32, scratch, st);
+    rank_scatter_kernel<<<blocks, 256, 0, st>>>(vals, n, rank); note_launch();
+}
+template void launch_centre_rank<8>(const PreArgs&, uint32_t*, uint32_t*, uint32_t*, uint32_t*, void*, uint32_t*,
+                                    cudaStream_t);
+template void launch_centre_rank<16>(const PreArgs&, uint32_t*, uint32_t*, uint32_t*, uint32_t*, void*, uint32_t*,
+                                     cudaStream_t);
 
 // depth quantisation from the device-side maximum depth
 __global__ void depth_quant_kernel(PreArgs A) {

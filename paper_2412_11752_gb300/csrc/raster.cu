@@ -409,8 +409,9 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
     }
     // contributor records for the backward
     const bool rec_on = !BWD && A.rec_key != nullptr;
+    const bool literal = fc.order_mode == DRK_ORDER_CACHE_SORT;
     kb.init(ring + threadIdx.x, reinterpret_cast<uint32_t*>(ring) + CAP * kRasterThreads + threadIdx.x,
-            ring + 2 * CAP * kRasterThreads + threadIdx.x, ovf, A.ovf_cap, list);
+            ring + 2 * CAP * kRasterThreads + threadIdx.x, literal ? nullptr : ovf, A.ovf_cap, list);
     // Exact order with a bounded heap.  When a contributor finds the heap
     // full, the largest key among the heap and the new entry is dropped;
     // `lost` is the smallest dropped key (every key in the heap stays below
@@ -421,28 +422,14 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
     uint64_t lost = ~0ull;     // smallest dropped key
     bool finished = ps.done;
 
-    // a contributor with key kk at list position j
-    auto offer = [&](float t, uint32_t j, float a, uint64_t kk) {
-        if (kk < lo || kk >= lost) return;
-        if (!kb.full()) {
-            if (kb.n >= CAP) wc.spills++;
-            kb.push(t, j, a);
-        } else {
-            const uint64_t d = kb.push_full(t, j, a);
-            if (d < lost) lost = d;
-        }
-    };
-
-    // composites the root of this lane's heap; `slot` is the record slot of
-    // the composited contributor (kNoSlot: not recorded)
-    auto emit_front = [&](uint32_t slot) {
-        const float a = kb.front_a();
+    // composites contributor (a, list position p); `slot` is its record slot
+    // (kNoSlot: not recorded)
+    auto composite = [&](float a, uint32_t p, uint32_t slot) {
         const float Tn = __fmul_rn(ps.T, __fsub_rn(1.f, a));
         if (Tn < fc.T_min) {
             ps.done = true;
             return;
         }
-        const uint32_t p = kb.front_p();
         const uint32_t idx = __ldg(list + p);
         const float col[3] = {__ldg(rgbp + 3 * (size_t)idx), __ldg(rgbp + 3 * (size_t)idx + 1),
                               __ldg(rgbp + 3 * (size_t)idx + 2)};
@@ -473,6 +460,39 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
         ps.T = Tn;
         ps.n_emit++;
     };
+    // composites the root of this lane's heap
+    auto emit_front = [&](uint32_t slot) { composite(kb.front_a(), kb.front_p(), slot); };
+
+    // a contributor with key kk at list position j
+    auto offer = [&](float t, uint32_t j, float a, uint64_t kk) {
+        if (literal) {
+            // the paper's cache-sorting: a full cache composites the smaller
+            // of its smallest entry and the new one (Sec. 4.4)
+            if (!kb.full()) {
+                kb.push(t, j, a);
+            } else if (kb.less(t, j, kb.front_t(), kb.front_p())) {
+                composite(a, j, kNoSlot);
+            } else {
+                const float ra = kb.front_a();
+                const uint32_t rp = kb.front_p();
+                composite(ra, rp, kNoSlot);
+                if (!ps.done) {
+                    kb.pop();
+                    kb.push(t, j, a);
+                }
+            }
+            return;
+        }
+        if (kk < lo || kk >= lost) return;
+        if (!kb.full()) {
+            if (kb.n >= CAP) wc.spills++;
+            kb.push(t, j, a);
+        } else {
+            const uint64_t d = kb.push_full(t, j, a);
+            if (d < lost) lost = d;
+        }
+    };
+
 
     // Called by all 32 lanes.  For each lane with `go`, composites every
     // pending entry that no item at or after a list position with depth
@@ -555,7 +575,7 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
             // larger of the item's key bound and 1 / max w over the block's
             // corners (w is affine in the pixel indices), deflated for FP32;
             // for the items after the chunk the next chunk's first key bound.
-            {
+            if (!literal) {
                 float bb = __int_as_float(0x7f800000);
                 if (lo_lane && c0 + (uint32_t)lane < L) {
                     const float* hs = reinterpret_cast<const float*>(stage + (buf * kChunk + lane) * HDR4);
@@ -604,6 +624,7 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
                                                      fc.alpha_max, a)) {
                             wc.contrib++;
                             offer(gm.t, j, a, key_of(gm.t, idx));
+                            if (ps.done) pass_done = true;
                         }
                     }
                 }

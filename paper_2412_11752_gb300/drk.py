@@ -49,7 +49,7 @@ class drk_options_t(C.Structure):
     _fields_ = [("alpha_min", C.c_float), ("T_min", C.c_float), ("alpha_max", C.c_float),
                 ("lowpass_sl", C.c_float), ("near_plane", C.c_float), ("bg", C.c_float * 3),
                 ("cull_level", C.c_int32), ("kbuf_capacity", C.c_int32), ("ovf_capacity", C.c_int32),
-                ("reserved", C.c_int32 * 5)]
+                ("order_mode", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
 class drk_image_t(C.Structure):
@@ -139,6 +139,7 @@ class Options:
     cull_level: int = CULL_TILE
     kbuf_capacity: int = 8
     ovf_capacity: int = 0
+    order_mode: int = 0          # 0 exact order; 1 the paper's cache-sorting (forward only)
 
     def to_c(self) -> drk_options_t:
         o = drk_options_t()
@@ -148,6 +149,7 @@ class Options:
             o.bg[i] = float(self.bg[i])
         o.cull_level, o.kbuf_capacity = int(self.cull_level), int(self.kbuf_capacity)
         o.ovf_capacity = int(self.ovf_capacity)
+        o.order_mode = int(self.order_mode)
         return o
 
 

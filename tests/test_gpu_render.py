@@ -202,3 +202,36 @@ def test_clustered_100k_1080p_sampled_pixels(drk):
     assert nex <= 0.05 * len(pix), f"{nex} of {len(pix)} excluded"
     stats = drk.default_context().stats()
     assert stats["n_pairs"] > 0 and stats["n_evals"] > 0
+
+
+# ---------------------------------------------------------------------------
+# the paper's cache-sorting (Sec. 4.4, supplementary Algorithm 1): an
+# approximate order, checked against the oracle's version of the same order
+
+@pytest.mark.parametrize("cap", [8, 16])
+def test_cache_sort_order_matches_oracle(drk, cap):
+    scene = synth.scene_clustered(3000, 8, seed=2300, n_clusters=8, sh_degree=-1)
+    cam = synth.camera_front(64, 48)
+    opt = drk.Options(order_mode=1, kbuf_capacity=cap)
+    rgb, ref = check_full(drk, scene, cam, opt, max_excluded_frac=0.1)
+    # the approximation is visible: it differs from the exact order somewhere
+    exact = O.render(scene, cam, oracle_options(drk.Options()))
+    assert np.abs(ref["rgb"] - exact["rgb"]).max() > 1e-3
+
+
+def test_cache_sort_without_overflow_is_exact(drk):
+    # with 30 primitives a 32-entry cache never overflows, so it composites
+    # in exact order
+    scene = synth.scene_plain(30, 8, seed=2301)
+    cam = synth.camera_front(48, 48)
+    lit, _, _, _ = render_gpu(drk, scene, cam, drk.Options(order_mode=1, kbuf_capacity=32))
+    ex, _, _, _ = render_gpu(drk, scene, cam, drk.Options())
+    np.testing.assert_array_equal(lit, ex)
+
+
+def test_cache_sort_has_no_backward(drk):
+    scene = synth.scene_plain(100, 8, seed=2302)
+    ds = drk.DeviceScene.from_scene(scene, "cuda")
+    with pytest.raises(drk.DrkError) as e:
+        drk.drk_render(ds, synth.camera_front(16, 16), drk.Options(order_mode=1), need_state=True)
+    assert e.value.code == 1
