@@ -5,6 +5,7 @@ forward + backward render (Sec. 4.4 pipeline and its reverse mode) of a
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl drk|reference]
     python bench.py --serve [--serve-requests R] [--serve-rate HZ] [--serve-batch B]
+    python bench.py --order-study     (forward only: exact vs cache-sorting order)
 
 One process per GPU (torchrun for N > 1).  The path does not shard: every
 rank renders its own replica of the workload ("replicas only"), value =
@@ -59,6 +60,8 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=160)
     ap.add_argument("--serve-rate", type=float, default=0.0, help="arrivals per second (0 = all at once)")
     ap.add_argument("--serve-batch", type=int, default=16)
+    ap.add_argument("--order-study", action="store_true",
+                    help="forward-only comparison of the exact order with the paper's cache-sorting order")
     return ap.parse_args()
 
 
@@ -360,6 +363,56 @@ def run_drk(args):
     return 0
 
 
+def order_study(args):
+    """Forward-only render time and image of the exact (r_t, index) order
+    against the cache-sorting order (Sec. 4.4, centre-depth pre-sort, a
+    cache of 8 or 16 entries), on the bench workload.  One JSON line."""
+    import torch
+    from paper_2412_11752_gb300 import drk
+    dev = torch.device("cuda", 0)
+    sc_f, cam_f = synth.WORKLOADS[args.workload]
+    scene, cam = sc_f(), cam_f()
+    H, W = cam.height, cam.width
+    ds = drk.DeviceScene.from_scene(scene, dev)
+    ctx = drk.Context(0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    modes = {"exact": drk.Options(), "cache8": drk.Options(order_mode=1, kbuf_capacity=8),
+             "cache16": drk.Options(order_mode=1, kbuf_capacity=16)}
+    res, imgs = {}, {}
+    for name, opt in modes.items():
+        out = dict(rgb=torch.empty((3, H, W), device=dev), T=None, n=None)
+        for _ in range(args.warmup):
+            drk.drk_render(ds, cam, opt, ctx=ctx, out=out)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        ctx.timing_enable(True)
+        for a, b in ev:
+            flush.zero_()
+            a.record()
+            drk.drk_render(ds, cam, opt, ctx=ctx, out=out)
+            b.record()
+        torch.cuda.synchronize()
+        stage = ctx.timing_read()
+        ctx.timing_enable(False)
+        ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+        imgs[name] = out["rgb"].clone()
+        res[name] = {"ms_per_frame": ms, "mpix_s": H * W / ms / 1e3,
+                     "stages_ms": {k: v[0] / max(1, v[1]) for k, v in stage.items() if v[1]}}
+    for name in ("cache8", "cache16"):
+        d = (imgs[name] - imgs["exact"]).abs()
+        mse = float(((imgs[name] - imgs["exact"]) ** 2).mean())
+        res[name]["vs_exact"] = {"max_abs": float(d.max()), "mean_abs": float(d.mean()),
+                                 "psnr_db": 10 * np.log10(1.0 / mse) if mse > 0 else None,
+                                 "pixels_over_1e-3": int((d.amax(0) > 1e-3).sum())}
+        res[name]["speedup_vs_exact"] = res["exact"]["ms_per_frame"] / res[name]["ms_per_frame"]
+    print(json.dumps({"metric": "Mpix/s forward, exact vs cache-sorting order", "unit": "Mpix/s",
+                      "steps": args.steps, "warmup": args.warmup, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": args.workload, "primitives": scene.n, "width": W, "height": H,
+                                 "l2": "flushed between timed frames (256 MiB write)"},
+                      "modes": res}), flush=True)
+    return 0
+
+
 def serve_run(D, torch, dscenes, reqs, max_batch: int, budget: int) -> dict:
     """Replays (arrival_s, scene, camera) requests through one server; latency
     = completion - arrival of each request, throughput over the whole run."""
@@ -415,6 +468,8 @@ def main():
     args = parse()
     if args.serve:
         return run_serve(args)
+    if args.order_study:
+        return order_study(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_drk(args)
