@@ -44,6 +44,11 @@ def sigmoid(x):
         return 1.0 / (1.0 + np.exp(-x))
 
 
+def dsigmoid(x):
+    """sigmoid'(x) = sigmoid(x) sigmoid(-x), accurate where s (1 - s) cancels."""
+    return sigmoid(x) * sigmoid(-np.asarray(x, np.float64))
+
+
 def theta_from_raw(x: np.ndarray) -> np.ndarray:
     """(n, K) raw angles -> (n, K) polar angles, reading T1."""
     x = np.asarray(x, np.float64)
@@ -90,10 +95,9 @@ def activate_backward(raw: dict, g: dict) -> dict:
     gt = np.asarray(g["theta"], np.float64)
     after = np.cumsum(gt[..., ::-1], axis=-1)[..., ::-1] - gt   # sum over k > j of g_k
     gw = 2.0 * math.pi * (after / S - np.sum(gt * Ck, axis=-1, keepdims=True) / S ** 2)
-    out["theta"] = gw * np.where(sg < SIG_CAP, sg * (1.0 - sg), 0.0)
+    out["theta"] = gw * np.where(sg < SIG_CAP, dsigmoid(xt), 0.0)
     for k, scale in (("eta", 1.0), ("tau", TAU_SPAN), ("opacity", 1.0)):
-        s = sigmoid(raw[k])
-        out[k] = np.asarray(g[k], np.float64) * scale * s * (1.0 - s)
+        out[k] = np.asarray(g[k], np.float64) * scale * dsigmoid(raw[k])
     return out
 
 

@@ -108,6 +108,13 @@ def test_adam_matches_torch():
             np.testing.assert_allclose(p, tp.detach().numpy(), rtol=1e-13, atol=1e-15)
 
 
+def test_sigmoid_derivative_where_the_sigmoid_saturates():
+    # sigmoid'(x) = e^-x / (1 + e^-x)^2 exactly; s (1 - s) loses it past |x| ~ 30
+    for x in (30.0, 40.0, -45.0, 80.0):
+        e = math.exp(-abs(x))
+        assert float(T.dsigmoid(x)) == pytest.approx(e / (1 + e) ** 2, rel=1e-12)
+
+
 def test_lr_exponential_end_points():
     assert T.lr_exponential(0, 5e-3, 5e-5, 35000) == pytest.approx(5e-3, rel=1e-14)
     assert T.lr_exponential(35000, 5e-3, 5e-5, 35000) == pytest.approx(5e-5, rel=1e-14)
