@@ -310,6 +310,70 @@ drk_status_t drk_serve_inject_alloc_failure(drk_serve_t *srv, int n);
 /* Drains the queue, joins the worker and frees everything. */
 drk_status_t drk_serve_destroy(drk_serve_t *srv);
 
+/* ------------------------------------------------------------------------
+ * Training: the activations of the learnable parameters (supplementary
+ * "Parametrization") and the optimiser step that fits them ("Model
+ * Training": Adam as in 3D-GS, learning rates decayed exponentially).
+ *
+ * Raw parameters are unconstrained float32 device arrays with the shapes
+ * of drk_params_t.  The activated parameters the renderer reads are
+ *   opacity = sigmoid(x),  eta = sigmoid(x),  scale_k = exp(x_k),
+ *   tau     = -0.1 + 1.09 sigmoid(x)          (the range (-0.1, 0.99)),
+ *   quat    = x / |x|                          ((1, 0, 0, 0) when x = 0),
+ *   theta_0 = 0, theta_k = 2 pi (w_0 + ... + w_{k-1}) / (w_0 + ... + w_{K-1})
+ *             with w_j = min(sigmoid(x_j), 1 - 1e-3) + 1 / (K - 2),
+ * so every cyclic gap between angles stays below pi (the cap keeps it
+ * below pi even where float32 sigmoids saturate).  mu and color are used
+ * as they are: the renderer reads the raw arrays. */
+typedef struct {
+    int64_t n;
+    int32_t K;            /* 3 .. 16 */
+    int32_t sh_degree;    /* -1 .. 3, as in drk_params_t */
+    float *mu, *quat, *scale, *theta, *eta, *tau, *opacity, *color;
+} drk_raw_params_t;
+
+/* Writes the activated quat, scale, theta, eta, tau and opacity of raw
+ * into out (device arrays of drk_params_t shapes; out->mu and out->color
+ * are not touched).  Returns DRK_ERR_INVALID_ARG for n < 0, K outside
+ * 3..16 or a NULL array when n > 0. */
+drk_status_t drk_activate(const drk_raw_params_t *raw, const drk_params_grad_t *out, void *stream);
+
+/* Chain rule through the activations: from gradients of the activated
+ * parameters (g_act, as drk_render_backward writes them) to gradients of
+ * the raw ones (g_raw, written; mu and color are copied). */
+drk_status_t drk_activate_backward(const drk_raw_params_t *raw, const drk_params_grad_t *g_act,
+                                   const drk_params_grad_t *g_raw, void *stream);
+
+/* Adam hyper-parameters of one step.  lr[] has one rate per array in the
+ * order mu, quat, scale, theta, eta, tau, opacity, color (index with the
+ * DRK_ARR_* constants); step is the 1-based step t of the bias corrections
+ * 1 - beta1^t and 1 - beta2^t. */
+enum { DRK_ARR_MU = 0, DRK_ARR_QUAT, DRK_ARR_SCALE, DRK_ARR_THETA, DRK_ARR_ETA, DRK_ARR_TAU,
+       DRK_ARR_OPACITY, DRK_ARR_COLOR, DRK_ARR_COUNT };
+typedef struct {
+    float lr[DRK_ARR_COUNT];
+    float beta1, beta2, eps;  /* 0.9, 0.999, 1e-15 in 3D-GS */
+    int64_t step;
+} drk_adam_t;
+
+/* One fused training update in a single launch: raw gradients from g_act
+ * (chain rule through the activations), the Adam update of every raw array
+ *   m = b1 m + (1 - b1) g,  v = b2 v + (1 - b2) g^2,
+ *   x -= lr / (1 - b1^t) * m / (sqrt(v) / sqrt(1 - b2^t) + eps),
+ * and the activation of the updated raw parameters into act (as
+ * drk_activate).  m and v are the moment arrays (shapes of raw, zero
+ * before step 1), updated in place; raw is updated in place.  Returns
+ * DRK_ERR_INVALID_ARG for bad shapes, NULL arrays, step < 1 or a beta
+ * outside [0, 1). */
+drk_status_t drk_adam_step(const drk_raw_params_t *raw, const drk_params_grad_t *g_act, const drk_params_grad_t *m,
+                           const drk_params_grad_t *v, const drk_adam_t *hp, const drk_params_grad_t *act,
+                           void *stream);
+
+/* Learning rate at `step` decayed log-linearly from lr_init to lr_final
+ * over max_steps (constant lr_final afterwards): the supplement decays the
+ * DRK-specific rate 5e-3 to 1e-2 of it at 35K steps.  Host function. */
+double drk_lr_exponential(int64_t step, double lr_init, double lr_final, int64_t max_steps);
+
 /* Message for the last failure on the calling thread ("" if none). */
 const char *drk_last_error(void);
 

@@ -40,6 +40,15 @@ class drk_params_grad_t(C.Structure):
     _fields_ = [(k, _fp) for k in PARAM_NAMES]
 
 
+class drk_raw_params_t(C.Structure):
+    _fields_ = [("n", C.c_int64), ("K", C.c_int32), ("sh_degree", C.c_int32)] + [(k, _fp) for k in PARAM_NAMES]
+
+
+class drk_adam_t(C.Structure):
+    _fields_ = [("lr", C.c_float * 8), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("step", C.c_int64)]
+
+
 class drk_camera_t(C.Structure):
     _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("fx", C.c_float), ("fy", C.c_float),
                 ("cx", C.c_float), ("cy", C.c_float), ("world_to_cam", C.c_float * 12)]
@@ -113,6 +122,16 @@ def lib():
         L.drk_serve_release.argtypes = [vp, C.c_uint64]
         L.drk_serve_inject_alloc_failure.argtypes = [vp, C.c_int]
         L.drk_serve_destroy.argtypes = [vp]
+        L.drk_activate.argtypes = [C.POINTER(drk_raw_params_t), C.POINTER(drk_params_grad_t), vp]
+        L.drk_activate_backward.argtypes = [C.POINTER(drk_raw_params_t), C.POINTER(drk_params_grad_t),
+                                            C.POINTER(drk_params_grad_t), vp]
+        L.drk_adam_step.argtypes = [C.POINTER(drk_raw_params_t), C.POINTER(drk_params_grad_t),
+                                    C.POINTER(drk_params_grad_t), C.POINTER(drk_params_grad_t),
+                                    C.POINTER(drk_adam_t), C.POINTER(drk_params_grad_t), vp]
+        L.drk_lr_exponential.restype = C.c_double
+        L.drk_lr_exponential.argtypes = [C.c_int64, C.c_double, C.c_double, C.c_int64]
+        for f in ("drk_activate", "drk_activate_backward", "drk_adam_step"):
+            getattr(L, f).restype = C.c_int
         for f in ("drk_ctx_create", "drk_render", "drk_render_backward", "drk_get_stats", "drk_sort_pairs",
                   "drk_timing_enable", "drk_timing_read", "drk_serve_create", "drk_serve_add_scene",
                   "drk_serve_submit", "drk_serve_poll", "drk_serve_wait", "drk_serve_release",
@@ -373,6 +392,117 @@ class DRKRender(torch.autograd.Function):
 
 def render_autograd(params: dict, cam, opt: Options | None = None, sh_degree: int = -1) -> torch.Tensor:
     return DRKRender.apply(cam, opt or Options(), sh_degree, *(params[k] for k in PARAM_NAMES))
+
+
+# ---------------------------------------------------------------------------
+# training: activations of the learnable parameters and the fused Adam step
+
+@dataclass
+class RawScene:
+    """Unconstrained learnable parameters (supplementary "Parametrization"),
+    contiguous float32 CUDA tensors with the shapes of DeviceScene.  mu and
+    color are used by the renderer as they are."""
+    mu: torch.Tensor
+    quat: torch.Tensor
+    scale: torch.Tensor
+    theta: torch.Tensor
+    eta: torch.Tensor
+    tau: torch.Tensor
+    opacity: torch.Tensor
+    color: torch.Tensor
+    sh_degree: int = -1
+
+    @property
+    def n(self) -> int:
+        return int(self.mu.shape[0])
+
+    @property
+    def K(self) -> int:
+        return int(self.scale.shape[1])
+
+    @staticmethod
+    def from_arrays(arrays: dict, sh_degree: int = -1, device="cuda") -> "RawScene":
+        t = {k: torch.as_tensor(np.ascontiguousarray(arrays[k], np.float32)).to(device).contiguous()
+             for k in PARAM_NAMES}
+        return RawScene(**t, sh_degree=int(sh_degree))
+
+    def tensors(self) -> dict:
+        return {k: getattr(self, k) for k in PARAM_NAMES}
+
+    def to_c(self) -> drk_raw_params_t:
+        p = drk_raw_params_t()
+        p.n, p.K, p.sh_degree = self.n, self.K, int(self.sh_degree)
+        for k in PARAM_NAMES:
+            setattr(p, k, _fptr(getattr(self, k)))
+        return p
+
+
+def _arrays_c(d: dict) -> drk_params_grad_t:
+    g = drk_params_grad_t()
+    for k in PARAM_NAMES:
+        setattr(g, k, _fptr(d.get(k)))
+    return g
+
+
+def activate(raw: RawScene, out: DeviceScene | None = None, stream=None) -> DeviceScene:
+    """Activated parameters of raw (drk_activate); the result shares raw's mu
+    and color tensors."""
+    if out is None:
+        out = DeviceScene(raw.mu, *(torch.empty_like(getattr(raw, k)) for k in PARAM_NAMES[1:-1]), raw.color,
+                          sh_degree=raw.sh_degree)
+    p, o = raw.to_c(), _arrays_c(out.tensors())
+    _check(lib().drk_activate(C.byref(p), C.byref(o), _stream_ptr(stream)))
+    return out
+
+
+def activate_backward(raw: RawScene, g_act: dict, stream=None) -> dict:
+    """Gradients of the raw parameters from those of the activated ones."""
+    g_raw = {k: torch.empty_like(getattr(raw, k)) for k in PARAM_NAMES}
+    p, gi, go = raw.to_c(), _arrays_c(g_act), _arrays_c(g_raw)
+    _check(lib().drk_activate_backward(C.byref(p), C.byref(gi), C.byref(go), _stream_ptr(stream)))
+    return g_raw
+
+
+# Learning rates (initial, final) decayed log-linearly over max_steps.  The
+# supplement fixes the DRK-specific ones (scale, theta, eta, tau: 5e-3 to
+# 1e-2 of it at 35K steps); the others follow 3D-GS's published defaults.
+LR_SCHEDULE = {"mu": (1.6e-4, 1.6e-6), "quat": (1e-3, 1e-3), "scale": (5e-3, 5e-5), "theta": (5e-3, 5e-5),
+               "eta": (5e-3, 5e-5), "tau": (5e-3, 5e-5), "opacity": (5e-2, 5e-2), "color": (2.5e-3, 2.5e-3)}
+
+
+def lr_exponential(step: int, lr_init: float, lr_final: float, max_steps: int) -> float:
+    return float(lib().drk_lr_exponential(int(step), float(lr_init), float(lr_final), int(max_steps)))
+
+
+def learning_rates(step: int, max_steps: int = 35000, schedule: dict | None = None) -> dict:
+    sch = schedule or LR_SCHEDULE
+    return {k: lr_exponential(step, *sch[k], max_steps) for k in PARAM_NAMES}
+
+
+class Adam:
+    """Adam on a RawScene from gradients of the activated parameters
+    (drk_adam_step: chain rule, update and re-activation in one launch).
+    `scene` is the activated DeviceScene the renderer reads; it is updated
+    in place by every step."""
+
+    def __init__(self, raw: RawScene, betas=(0.9, 0.999), eps: float = 1e-15, stream=None):
+        self.raw = raw
+        self.m = {k: torch.zeros_like(getattr(raw, k)) for k in PARAM_NAMES}
+        self.v = {k: torch.zeros_like(getattr(raw, k)) for k in PARAM_NAMES}
+        self.betas, self.eps, self.t = betas, float(eps), 0
+        self.scene = activate(raw, stream=stream)
+
+    def step(self, g_act: dict, lr: dict, stream=None) -> DeviceScene:
+        self.t += 1
+        hp = drk_adam_t()
+        for i, k in enumerate(PARAM_NAMES):
+            hp.lr[i] = float(lr[k])
+        hp.beta1, hp.beta2, hp.eps, hp.step = float(self.betas[0]), float(self.betas[1]), self.eps, self.t
+        p, g = self.raw.to_c(), _arrays_c(g_act)
+        m, v, a = _arrays_c(self.m), _arrays_c(self.v), _arrays_c(self.scene.tensors())
+        _check(lib().drk_adam_step(C.byref(p), C.byref(g), C.byref(m), C.byref(v), C.byref(hp), C.byref(a),
+                                   _stream_ptr(stream)))
+        return self.scene
 
 
 # ---------------------------------------------------------------------------

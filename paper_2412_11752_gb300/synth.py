@@ -317,6 +317,47 @@ def serve_requests(count: int, n_scenes: int, rate_hz: float, seed: int = 4500,
     return out
 
 
+def raw_scene(n: int, K: int = 8, seed: int = 6000, sh_degree: int = -1, lo=(-0.3, -0.3, 0.4),
+              hi=(1.3, 1.3, 0.6)) -> dict:
+    """Initial unconstrained (raw) parameters for fitting, drawn in raw
+    space: centres uniform in the box [lo, hi], raw quaternions near the
+    identity (primitives roughly facing camera_front), raw scales around
+    log 0.06, raw angles, blend and sharpness standard normal x 0.3, raw
+    opacity around -1, colours uniform (or small SH coefficients)."""
+    rng = np.random.default_rng(seed)
+    f = lambda a: np.ascontiguousarray(a, dtype=np.float32)
+    quat = np.zeros((n, 4))
+    quat[:, 0] = 1.0
+    quat += rng.normal(0.0, 0.2, size=(n, 4))
+    return dict(mu=f(rng.uniform(lo, hi, size=(n, 3))), quat=f(quat),
+                scale=f(np.log(0.06) + rng.normal(0.0, 0.3, size=(n, K))),
+                theta=f(rng.normal(0.0, 0.3, size=(n, K))), eta=f(rng.normal(0.0, 0.3, size=n)),
+                tau=f(rng.normal(0.0, 0.3, size=n)), opacity=f(rng.normal(-1.0, 0.3, size=n)),
+                color=f(_sh_colors(rng, n, sh_degree)))
+
+
+def shape_target(height: int, width: int, seed: int = 6100, n_shapes: int = 6) -> np.ndarray:
+    """(3, H, W) float32 image of a few filled convex polygons (3 to 7
+    vertices, random rotation and anisotropic size, random colour) painted
+    over a grey background, later shapes on top."""
+    rng = np.random.default_rng(seed)
+    img = np.full((3, height, width), 0.35, np.float64)
+    ys, xs = np.mgrid[0:height, 0:width]
+    px, py = (xs + 0.5) / width, (ys + 0.5) / height
+    for _ in range(n_shapes):
+        m = int(rng.integers(3, 8))
+        ang = rng.uniform(0, 2 * np.pi) + 2 * np.pi * np.arange(m) / m
+        sx, sy = rng.uniform(0.08, 0.3, size=2)
+        cx, cy = rng.uniform(0.2, 0.8, size=2)
+        vx, vy = cx + sx * np.cos(ang), cy + sy * np.sin(ang)
+        inside = np.ones((height, width), bool)
+        for k in range(m):
+            ex, ey = vx[(k + 1) % m] - vx[k], vy[(k + 1) % m] - vy[k]
+            inside &= ex * (py - vy[k]) - ey * (px - vx[k]) >= 0.0
+        img[:, inside] = rng.uniform(0.0, 1.0, size=(3, 1))
+    return img.astype(np.float32)
+
+
 def target_image(height: int, width: int, seed: int = 3001) -> np.ndarray:
     return np.random.default_rng(seed).uniform(0.0, 1.0, size=(3, height, width)).astype(np.float32)
 
