@@ -731,6 +731,64 @@ int ord_render(const ord_params *P, const ord_camera *cam, const ord_options *op
     return fail ? -1 : 0;
 }
 
+/* Depth and normal images of the listed pixels (supplementary "Converting
+ * Mesh to DRK": rendered depth and normal images), composited with the
+ * weights of the colour (Eq. 1): depth = sum_i T_i alpha_i r_t,i (r_t of
+ * Eq. 13, the view depth) and normal = sum_i T_i alpha_i n_i, n_i the unit
+ * normal R_z of primitive i's plane in camera coordinates, oriented towards
+ * the camera (the side of the plane the camera is on).  Reading: the paper
+ * shows these images without defining them; unnormalised sums (divide by
+ * 1 - T_final for the mean over the covered part).  depth: npix, normal:
+ * npix x 3.  Returns 0, or -1 on allocation failure.                        */
+int ord_render_aux(const ord_params *P, const ord_camera *cam, const ord_options *opt, int64_t npix,
+                   const int32_t *pix, double *depth, double *normal)
+{
+    double ocam[3];
+    cam_center(cam, ocam);
+    const double *M = cam->w2c;
+    int fail = 0;
+#pragma omp parallel
+    {
+        contrib *buf = (contrib *)malloc(sizeof(contrib) * (size_t)(P->n > 0 ? P->n : 1));
+        if (!buf) {
+#pragma omp atomic write
+            fail = 1;
+        }
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t q = 0; q < npix; q++) {
+            if (!buf) continue;
+            int near_amin;
+            int64_t cnt = gather_contributors(P, cam, opt, ocam, pix[2 * q], pix[2 * q + 1], buf, &near_amin);
+            if (cnt < 0) {
+#pragma omp atomic write
+                fail = 1;
+                continue;
+            }
+            int64_t nc = composite_count(buf, cnt, opt->T_min);
+            double D = 0.0, N[3] = {0.0, 0.0, 0.0}, T = 1.0;
+            for (int64_t j = 0; j < nc; j++) {
+                const int64_t i = buf[j].idx;
+                double R[9];
+                ord_rotation(P->quat + 4 * i, R);
+                double nw[3] = {R[2], R[5], R[8]}, nc3[3];
+                for (int r = 0; r < 3; r++) nc3[r] = M[4 * r] * nw[0] + M[4 * r + 1] * nw[1] + M[4 * r + 2] * nw[2];
+                /* the camera is on the side of the plane that n points to */
+                double side = 0.0;
+                for (int c = 0; c < 3; c++) side += nw[c] * (ocam[c] - P->mu[3 * i + c]);
+                const double sg = side >= 0.0 ? 1.0 : -1.0;
+                const double w = T * buf[j].alpha;
+                D += w * buf[j].t;
+                for (int c = 0; c < 3; c++) N[c] += w * sg * nc3[c];
+                T *= 1.0 - buf[j].alpha;
+            }
+            depth[q] = D;
+            for (int c = 0; c < 3; c++) normal[3 * q + c] = N[c];
+        }
+        free(buf);
+    }
+    return fail ? -1 : 0;
+}
+
 /* Sorted contributor list of one pixel (for inspection by tests).
  * Writes up to cap entries; returns the total count; *n_composited gets the
  * number composited before the stop.                                        */

@@ -109,6 +109,9 @@ def lib():
         L.ord_contributors.restype = C.c_int64
         L.ord_contributors.argtypes = [C.POINTER(_Params), C.POINTER(_Camera), C.POINTER(_Options), C.c_int,
                                        C.c_int, C.c_int64, C.POINTER(C.c_int64), dp, dp, C.POINTER(C.c_int64)]
+        L.ord_render_aux.restype = C.c_int
+        L.ord_render_aux.argtypes = [C.POINTER(_Params), C.POINTER(_Camera), C.POINTER(_Options), C.c_int64,
+                                     C.POINTER(C.c_int32), dp, dp]
         L.ord_max_threads.restype = C.c_int
         L.ord_set_threads.argtypes = [C.c_int]
         _lib = L
@@ -248,6 +251,28 @@ def render(scene, cam, opt: Options):
     r = render_pixels(scene, cam, opt, all_pixels(W, H))
     return dict(rgb=r["rgb"].T.reshape(3, H, W), T=r["T"].reshape(H, W),
                 n_contrib=r["n_contrib"].reshape(H, W), flags=r["flags"].reshape(H, W))
+
+
+def render_aux_pixels(scene, cam, opt: Options, pixels: np.ndarray):
+    """Depth (m,) and camera-space normal (m, 3) images of listed pixels:
+    sums of the compositing weights times r_t and times the plane normal
+    oriented towards the camera."""
+    keep = _Keep()
+    P, Cm, O = _params(scene, keep), _camera(cam), _options(opt)
+    pix = np.ascontiguousarray(np.asarray(pixels, np.int32))
+    m = pix.shape[0]
+    depth, normal = np.zeros(m), np.zeros((m, 3))
+    if lib().ord_render_aux(C.byref(P), C.byref(Cm), C.byref(O), m, pix.ctypes.data_as(C.POINTER(C.c_int32)),
+                            _dp(depth), _dp(normal)) != 0:
+        raise MemoryError("oracle aux render: allocation failed")
+    return depth, normal
+
+
+def render_aux(scene, cam, opt: Options):
+    """Full images: depth (H, W), normal (3, H, W)."""
+    H, W = cam.height, cam.width
+    d, n = render_aux_pixels(scene, cam, opt, all_pixels(W, H))
+    return d.reshape(H, W), n.T.reshape(3, H, W)
 
 
 def render_backward_pixels(scene, cam, opt: Options, pixels: np.ndarray, dL_drgb: np.ndarray) -> dict:

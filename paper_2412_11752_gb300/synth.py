@@ -358,6 +358,63 @@ def shape_target(height: int, width: int, seed: int = 6100, n_shapes: int = 6) -
     return img.astype(np.float32)
 
 
+def mesh_heightfield(nx: int, ny: int, seed: int = 7000, lo=(-0.3, -0.1), hi=(1.3, 1.1), z0: float = 0.6,
+                     amp: float = 0.08, triangles: bool = False):
+    """A height-field wall facing camera_front: an (nx+1) x (ny+1) vertex
+    grid over [lo, hi] in x, y at depth z0 plus a smooth random relief (a sum
+    of a few random sinusoids of amplitude amp).  Returns (verts (V, 3)
+    float32, faces (F, 4) or (F, 3) int32, counter-clockwise seen from the
+    camera side, -z)."""
+    rng = np.random.default_rng(seed)
+    xs = np.linspace(lo[0], hi[0], nx + 1)
+    ys = np.linspace(lo[1], hi[1], ny + 1)
+    X, Y = np.meshgrid(xs, ys)
+    Z = np.full_like(X, z0)
+    for _ in range(5):
+        kx, ky = rng.uniform(1.0, 8.0, size=2)
+        ph = rng.uniform(0, 2 * np.pi)
+        Z += amp / 5 * np.sin(kx * X + ky * Y + ph)
+    verts = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    i = np.arange(ny)[:, None] * (nx + 1) + np.arange(nx)[None, :]
+    a, b, c, d = i.ravel(), i.ravel() + 1, i.ravel() + nx + 2, i.ravel() + nx + 1
+    # seen from -z with y down the image, (a, d, c, b) runs counter-clockwise
+    # about -z, the normal that faces the camera
+    if triangles:
+        faces = np.concatenate([np.stack([a, d, c], 1), np.stack([a, c, b], 1)])
+    else:
+        faces = np.stack([a, d, c, b], 1)
+    return verts.astype(np.float32), faces.astype(np.int32)
+
+
+def mesh_polygons(n: int, max_vertices: int = 8, seed: int = 7100):
+    """n separate convex polygons (3 .. max_vertices vertices: regular
+    polygons with a random radius, in-plane stretch and rotation, randomly
+    oriented) with centres uniform in the unit cube.  Returns (verts,
+    faces (n, max_vertices) int32 with -1 padding)."""
+    rng = np.random.default_rng(seed)
+    verts, faces = [], []
+    q = _uniform_quats(rng, n)
+    for f in range(n):
+        m = int(rng.integers(3, max_vertices + 1))
+        ang = rng.uniform(0, 2 * np.pi) + 2 * np.pi * np.arange(m) / m
+        r = rng.uniform(0.02, 0.08)
+        sx, sy = rng.uniform(0.6, 1.4, size=2)
+        w, x, y, z = q[f]
+        R = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                      [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                      [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+        local = np.stack([r * sx * np.cos(ang), r * sy * np.sin(ang), np.zeros(m)], axis=1)
+        c = rng.uniform(0.0, 1.0, size=3)
+        base = len(verts)
+        verts.extend(list(c + local @ R.T))
+        faces.append(list(range(base, base + m)) + [-1] * (max_vertices - m))
+    return np.asarray(verts, np.float32), np.asarray(faces, np.int32)
+
+
+def mesh_colors(n_faces: int, seed: int = 7200) -> np.ndarray:
+    return np.random.default_rng(seed).uniform(0.1, 1.0, size=(n_faces, 3)).astype(np.float32)
+
+
 def target_image(height: int, width: int, seed: int = 3001) -> np.ndarray:
     return np.random.default_rng(seed).uniform(0.0, 1.0, size=(3, height, width)).astype(np.float32)
 
