@@ -149,6 +149,17 @@ typedef struct {
     float *rgb;           /* 3 x H x W, includes T_final * bg */
     float *T_final;       /* H x W final transmittance, may be NULL */
     int32_t *n_emitted;   /* H x W number of composited contributors, may be NULL */
+    /* Depth and normal images (supplementary "Converting Mesh to DRK"),
+     * composited with the colour's weights T_i alpha_i: depth = sum of
+     * T_i alpha_i r_t,i (view depth, Eq. 13), normal = sum of T_i alpha_i
+     * n_i with n_i the unit normal of primitive i's plane in camera
+     * coordinates, oriented towards the camera.  Unnormalised: divide by
+     * 1 - T_final for the mean over the covered part.  Either may be NULL
+     * (not computed); when one is given the forward raster runs a variant
+     * that also accumulates them.  Not differentiated by
+     * drk_render_backward. */
+    float *depth;         /* H x W, may be NULL */
+    float *normal;        /* 3 x H x W, may be NULL */
 } drk_image_t;
 
 /* Counters of the last render on a context (device-side counts). */
@@ -373,6 +384,55 @@ drk_status_t drk_adam_step(const drk_raw_params_t *raw, const drk_params_grad_t 
  * over max_steps (constant lr_final afterwards): the supplement decays the
  * DRK-specific rate 5e-3 to 1e-2 of it at 35K steps.  Host function. */
 double drk_lr_exponential(int64_t step, double lr_init, double lr_final, int64_t max_steps);
+
+/* ------------------------------------------------------------------------
+ * Mesh to DRK (Sec. 5.4 "Converting Mesh to DRK", supplementary section of
+ * the same name): every convex polygon face becomes one DRK, without any
+ * optimisation.
+ *
+ *   mu      mean of the face's vertices;
+ *   frame   R_z = unit normal by Newell's method (sum over the edges of
+ *           (v_j - mu) x (v_{j+1} - mu)), so the vertices run
+ *           counter-clockwise about R_z; R_x from mu towards the first vertex
+ *           projected into the plane; R_y = R_z x R_x; quat of [R_x R_y R_z]
+ *           with w >= 0;
+ *   bases   endpoints at the vertices projected into the plane, in face
+ *           order; a face of m < K vertices gets K - m extra endpoints on its
+ *           edges, edge j (vertex j to j+1) receiving (K-m)/m + (j < (K-m) %
+ *           m) of them, equally spaced; theta_0 = 0, theta_k the polar angle
+ *           of endpoint k in [0, 2 pi); s_k = |endpoint k| / sqrt(-2 ln g_e);
+ *   shape   eta = 1 (L1 norm alone, Eq. 7-8): the contours of the kernel
+ *           are scaled copies of the polygon and the polygon is the contour
+ *           g = g_e (edge_density); g_e = 1/2 puts the edges where Psi = 1/2
+ *           for any tau (Eq. 9), g_e = exp(-1/2) puts the endpoints exactly on
+ *           the vertices;
+ *   colour  face colour x (ambient + diffuse |R_z . light|), plain RGB.
+ * A face is rejected (status 1: index out of range, padding inside the row,
+ * fewer than 3 or more than K vertices, zero area; status 2: the endpoint
+ * angles do not increase strictly with every cyclic gap below pi - 1e-3)
+ * and its DRK gets opacity 0 (it renders nothing). */
+typedef struct {
+    int32_t K;            /* bases per DRK, 3 .. 16, at least the largest face */
+    float edge_density;   /* g_e in (0, 1); default 0.5 */
+    float tau;            /* sharpness in (-1, 1); default 0.95 */
+    float opacity;        /* in (0, 1]; default 1 */
+    float light[3];       /* direction of the light (world), any length > 0 */
+    float ambient, diffuse;
+} drk_mesh_options_t;
+
+/* Fills *opt with K = 4, edge_density 0.5, tau 0.95, opacity 1, light
+ * (0.3, -0.5, -0.8), ambient 0.35, diffuse 0.65. */
+void drk_mesh_options_default(drk_mesh_options_t *opt);
+
+/* verts: n_verts x 3; faces: n_faces x face_size vertex indices (int32),
+ * -1 padding at the end of a row; face_color: n_faces x 3 (may be NULL:
+ * white); out: the DRK arrays of n_faces primitives (mu n x 3, quat n x 4,
+ * scale n x K, theta n x K, eta, tau, opacity n, color n x 3 with
+ * sh_degree -1); face_status: n_faces int32 (may be NULL).  All device
+ * pointers.  Returns DRK_ERR_INVALID_ARG for bad sizes or options. */
+drk_status_t drk_mesh_to_drk(const float *verts, int64_t n_verts, const int32_t *faces, int64_t n_faces,
+                             int32_t face_size, const float *face_color, const drk_mesh_options_t *opt,
+                             const drk_params_grad_t *out, int32_t *face_status, void *stream);
 
 /* Message for the last failure on the calling thread ("" if none). */
 const char *drk_last_error(void);

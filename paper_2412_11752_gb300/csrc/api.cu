@@ -445,6 +445,8 @@ drk_status_t drk_render(drk_ctx_t* ctx, const drk_params_t* params, const drk_ca
     R.out_rgb = out->rgb;
     R.out_T = out->T_final;
     R.out_n = out->n_emitted;
+    R.out_depth = out->depth;
+    R.out_normal = out->normal;
     R.p = *params;
     if (state) {
         // one record per composited contributor for the backward; the pool

@@ -85,6 +85,8 @@ struct RasterArgs {
     float* out_rgb;
     float* out_T;
     int32_t* out_n;
+    float* out_depth;      // H x W sum of T alpha r_t (null: not computed)
+    float* out_normal;     // 3 x H x W sum of T alpha n (camera frame, towards the camera)
     // contributor records written by the forward for the backward (may be
     // null): one per composited contributor, in rec_cap slots handed out in
     // chunks of kRecChunk; rec_key = global pair index (ranges[tile].x + list

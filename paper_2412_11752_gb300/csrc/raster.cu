@@ -364,7 +364,7 @@ struct WarpCounters {
 
 // One task of the forward (or replay) traversal: the 8 x 4 block `blk` of
 // `tile` in the frame (fc, rec, rgb, vals, keys, ranges, dq, out).
-template <int KMAX, int CAP, bool BWD>
+template <int KMAX, int CAP, bool BWD, bool AUX>
 __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& fc, const float* __restrict__ recp,
                                          const float* __restrict__ rgbp, const uint32_t* __restrict__ valsp,
                                          const uint32_t* __restrict__ keysp, const uint2* __restrict__ rangesp,
@@ -422,9 +422,17 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
     uint64_t lost = ~0ull;     // smallest dropped key
     bool finished = ps.done;
 
-    // composites contributor (a, list position p); `slot` is its record slot
-    // (kNoSlot: not recorded)
-    auto composite = [&](float a, uint32_t p, uint32_t slot) {
+    // depth and normal images (AUX): the plane normal in camera coordinates
+    // follows from the homography row of 1/r_t: with the ray d = (x ifx + ox,
+    // y ify + oy, 1), 1/r_t = n . d / c, so n / c = (HW0 / ifx, HW1 / ify,
+    // HW2 - ox HW0 / ifx - oy HW1 / ify); n / c . d = 1/r_t > 0, so -n / c
+    // points towards the camera
+    float aux_d = 0.f, aux_n[3] = {0.f, 0.f, 0.f};
+    const float fxp = AUX ? 1.f / fc.ifx : 0.f, fyp = AUX ? 1.f / fc.ify : 0.f;
+
+    // composites contributor (r_t t, alpha a, list position p); `slot` is its
+    // record slot (kNoSlot: not recorded)
+    auto composite = [&](float t, float a, uint32_t p, uint32_t slot) {
         const float Tn = __fmul_rn(ps.T, __fsub_rn(1.f, a));
         if (Tn < fc.T_min) {
             ps.done = true;
@@ -434,6 +442,16 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
         const float col[3] = {__ldg(rgbp + 3 * (size_t)idx), __ldg(rgbp + 3 * (size_t)idx + 1),
                               __ldg(rgbp + 3 * (size_t)idx + 2)};
         const float wgt = __fmul_rn(a, ps.T);
+        if (AUX) {
+            const float* h = recp + (size_t)Rec<KMAX>::STRIDE * idx;
+            const float nx = __ldg(h + R_HW0) * fxp, ny = __ldg(h + R_HW1) * fyp;
+            const float nz = __ldg(h + R_HW2) - fc.ox * nx - fc.oy * ny;
+            const float s = -wgt * rsqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
+            aux_n[0] = fmaf(s, nx, aux_n[0]);
+            aux_n[1] = fmaf(s, ny, aux_n[1]);
+            aux_n[2] = fmaf(s, nz, aux_n[2]);
+            aux_d = fmaf(wgt, t, aux_d);
+        }
         if (!BWD) {
             const float T_i = ps.T;
             for (int c = 0; c < 3; c++) ps.C[c] = fmaf(wgt, col[c], ps.C[c]);
@@ -461,7 +479,7 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
         ps.n_emit++;
     };
     // composites the root of this lane's heap
-    auto emit_front = [&](uint32_t slot) { composite(kb.front_a(), kb.front_p(), slot); };
+    auto emit_front = [&](uint32_t slot) { composite(kb.front_t(), kb.front_a(), kb.front_p(), slot); };
 
     // a contributor with key kk at list position j
     auto offer = [&](float t, uint32_t j, float a, uint64_t kk) {
@@ -471,11 +489,11 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
             if (!kb.full()) {
                 kb.push(t, j, a);
             } else if (kb.less(t, j, kb.front_t(), kb.front_p())) {
-                composite(a, j, kNoSlot);
+                composite(t, a, j, kNoSlot);
             } else {
-                const float ra = kb.front_a();
+                const float ra = kb.front_a(), rt = kb.front_t();
                 const uint32_t rp = kb.front_p();
-                composite(ra, rp, kNoSlot);
+                composite(rt, ra, rp, kNoSlot);
                 if (!ps.done) {
                     kb.pop();
                     kb.push(t, j, a);
@@ -659,6 +677,11 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
         for (int c = 0; c < 3; c++) outp[c * npix + pix] = fmaf(ps.T, fc.bg[c], ps.C[c]);
         if (!batched && A.out_T) A.out_T[pix] = ps.T;
         if (!batched && A.out_n) A.out_n[pix] = ps.n_emit;
+        if (AUX && !batched) {
+            if (A.out_depth) A.out_depth[pix] = aux_d;
+            if (A.out_normal)
+                for (int c = 0; c < 3; c++) A.out_normal[c * npix + pix] = aux_n[c];
+        }
     }
     wc.emit += (unsigned long long)ps.n_emit;
 }
@@ -676,7 +699,7 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
 // stage with cp.async one chunk ahead of use; the kernel stage runs only
 // when some lane of the warp passes the geometry stage.  Tasks are taken
 // heaviest tile first (longest list), which keeps the tail short.
-template <int KMAX, int CAP, bool BWD, bool BATCH>
+template <int KMAX, int CAP, bool BWD, bool BATCH, bool AUX = false>
 __global__ void __launch_bounds__(kRasterThreads, 5) raster_kernel(RasterArgs A) {
     constexpr int kWarps = kRasterThreads / 32;
     constexpr int HDR4 = Rec<KMAX>::HDR / 4;
@@ -708,7 +731,7 @@ __global__ void __launch_bounds__(kRasterThreads, 5) raster_kernel(RasterArgs A)
         const int tile = A.tile_order ? (int)A.tile_order[task >> 3] : (int)(task >> 3);
         if (BATCH) {
             const FrameSlot& sl = A.slots[(uint32_t)tile >> 20];
-            run_task<KMAX, CAP, BWD>(A, sl.fc, sl.rec, sl.rgb, sl.vals, sl.keys, sl.ranges, sl.dq, sl.out_rgb, true,
+            run_task<KMAX, CAP, BWD, false>(A, sl.fc, sl.rec, sl.rgb, sl.vals, sl.keys, sl.ranges, sl.dq, sl.out_rgb, true,
                                      sl.K, tile & ((1 << 20) - 1), task, stage, ring, ovf, kb, wc, rc);
             // the warp that finishes a frame's last task publishes it: its
             // image is complete in device memory once the flag is visible
@@ -721,7 +744,7 @@ __global__ void __launch_bounds__(kRasterThreads, 5) raster_kernel(RasterArgs A)
                 }
             }
         } else {
-            run_task<KMAX, CAP, BWD>(A, A.fc, A.rec, A.rgb, A.vals, A.keys, A.ranges, A.dq, A.out_rgb, false, A.K, tile,
+            run_task<KMAX, CAP, BWD, AUX>(A, A.fc, A.rec, A.rgb, A.vals, A.keys, A.ranges, A.dq, A.out_rgb, false, A.K, tile,
                                      task, stage, ring, ovf, kb, wc, rc);
         }
     }
@@ -868,36 +891,40 @@ constexpr size_t raster_smem() {
 }
 
 // resident CTAs x SMs of one instantiation (computed once)
-template <int KMAX, int CAP, bool BWD, bool BATCH>
+template <int KMAX, int CAP, bool BWD, bool BATCH, bool AUX = false>
 static int raster_grid() {
     static int grid = 0;
     if (grid == 0) {
         constexpr size_t smem = raster_smem<KMAX, CAP>();
-        cudaFuncSetAttribute(raster_kernel<KMAX, CAP, BWD, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(raster_kernel<KMAX, CAP, BWD, BATCH, AUX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raster_kernel<KMAX, CAP, BWD, BATCH>, kRasterThreads,
-                                                      smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raster_kernel<KMAX, CAP, BWD, BATCH, AUX>,
+                                                      kRasterThreads, smem);
         grid = sms * (per_sm > 0 ? per_sm : 1);
     }
     return grid;
 }
 
-template <int KMAX, int CAP, bool BWD, bool BATCH>
+template <int KMAX, int CAP, bool BWD, bool BATCH, bool AUX = false>
 static int raster_blocks(int n_tiles) {
     constexpr int kWarps = kRasterThreads / 32;
     const int n_tasks = n_tiles * 8;
-    return std::min(raster_grid<KMAX, CAP, BWD, BATCH>(), (n_tasks + kWarps - 1) / kWarps);
+    return std::min(raster_grid<KMAX, CAP, BWD, BATCH, AUX>(), (n_tasks + kWarps - 1) / kWarps);
 }
 
-template <int KMAX, int CAP, bool BWD, bool BATCH>
+template <int KMAX, int CAP, bool BWD, bool BATCH, bool AUX = false>
 static void launch_raster_t(const RasterArgs& A, int n_tiles, cudaStream_t st) {
-    const int blocks = raster_blocks<KMAX, CAP, BWD, BATCH>(n_tiles);
+    // the depth/normal instantiation never has more resident warps than the
+    // plain one (same bounds, at least as many registers), so the overflow
+    // columns sized by raster_slots cover it; warps past them run without
+    const int blocks = raster_blocks<KMAX, CAP, BWD, BATCH, AUX>(n_tiles);
     if (blocks <= 0) return;
     cudaMemsetAsync(A.task_counter, 0, sizeof(unsigned int), st);
-    raster_kernel<KMAX, CAP, BWD, BATCH><<<blocks, kRasterThreads, raster_smem<KMAX, CAP>(), st>>>(A); note_launch();
+    raster_kernel<KMAX, CAP, BWD, BATCH, AUX><<<blocks, kRasterThreads, raster_smem<KMAX, CAP>(), st>>>(A);
+    note_launch();
 }
 
 int raster_slots(int kmax, int cap, bool bwd, bool batch, int n_tiles) {
@@ -924,9 +951,11 @@ size_t raster_ovf_bytes(int slots) { return (size_t)slots * kOvfCap * 32 * sizeo
 void launch_raster(const RasterArgs& A, int kmax, int cap, bool bwd, cudaStream_t st) {
     const int n_tiles = A.fc.tiles_x * A.fc.tiles_y;
     if (n_tiles == 0) return;
+    const bool aux = !bwd && (A.out_depth || A.out_normal);
 #define DRK_RASTER_CASE(KM, CP)                                                   \
     if (kmax == KM && cap == CP) {                                                \
         if (bwd) launch_raster_t<KM, CP, true, false>(A, n_tiles, st);            \
+        else if (aux) launch_raster_t<KM, CP, false, false, true>(A, n_tiles, st);\
         else launch_raster_t<KM, CP, false, false>(A, n_tiles, st);               \
         return;                                                                   \
     }

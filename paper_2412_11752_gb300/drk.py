@@ -30,6 +30,7 @@ class DrkError(RuntimeError):
 
 
 _fp = C.POINTER(C.c_float)
+_ip = C.POINTER(C.c_int32)
 
 
 class drk_params_t(C.Structure):
@@ -62,7 +63,8 @@ class drk_options_t(C.Structure):
 
 
 class drk_image_t(C.Structure):
-    _fields_ = [("rgb", _fp), ("T_final", _fp), ("n_emitted", C.POINTER(C.c_int32))]
+    _fields_ = [("rgb", _fp), ("T_final", _fp), ("n_emitted", C.POINTER(C.c_int32)), ("depth", _fp),
+                ("normal", _fp)]
 
 
 class drk_stats_t(C.Structure):
@@ -130,7 +132,9 @@ def lib():
                                     C.POINTER(drk_adam_t), C.POINTER(drk_params_grad_t), vp]
         L.drk_lr_exponential.restype = C.c_double
         L.drk_lr_exponential.argtypes = [C.c_int64, C.c_double, C.c_double, C.c_int64]
-        for f in ("drk_activate", "drk_activate_backward", "drk_adam_step"):
+        L.drk_mesh_to_drk.argtypes = [_fp, C.c_int64, _ip, C.c_int64, C.c_int32, _fp, C.POINTER(drk_mesh_options_t),
+                                      C.POINTER(drk_params_grad_t), _ip, vp]
+        for f in ("drk_activate", "drk_activate_backward", "drk_adam_step", "drk_mesh_to_drk"):
             getattr(L, f).restype = C.c_int
         for f in ("drk_ctx_create", "drk_render", "drk_render_backward", "drk_get_stats", "drk_sort_pairs",
                   "drk_timing_enable", "drk_timing_read", "drk_serve_create", "drk_serve_add_scene",
@@ -322,12 +326,27 @@ def drk_render(scene: DeviceScene, cam, opt: Options | None = None, ctx: Context
     img.rgb = _fptr(out["rgb"])
     img.T_final = _fptr(out.get("T"))
     img.n_emitted = C.cast(C.c_void_p(out["n"].data_ptr()), C.POINTER(C.c_int32)) if out.get("n") is not None else None
+    img.depth = _fptr(out.get("depth"))
+    img.normal = _fptr(out.get("normal"))
     p, cc, oc = scene.to_c(), camera_c(cam), opt.to_c()
     h = C.c_void_p()
     _check(lib().drk_render(ctx.handle, C.byref(p), C.byref(cc), C.byref(oc), C.byref(img),
                             C.byref(h) if need_state else None, _stream_ptr(stream)))
     st = State(h, ctx) if need_state else None
     return out["rgb"], out.get("T"), out.get("n"), st
+
+
+def drk_render_aux(scene: DeviceScene, cam, opt: Options | None = None, ctx: Context | None = None, stream=None):
+    """Forward render with the depth and normal images.  Returns (rgb
+    (3, H, W), T_final (H, W), depth (H, W), normal (3, H, W)); depth and
+    normal are sums weighted by T_i alpha_i (divide by 1 - T_final for the
+    mean over the covered part)."""
+    H, W = int(cam.height), int(cam.width)
+    dev = scene.mu.device
+    out = dict(rgb=torch.empty((3, H, W), device=dev), T=torch.empty((H, W), device=dev), n=None,
+               depth=torch.empty((H, W), device=dev), normal=torch.empty((3, H, W), device=dev))
+    drk_render(scene, cam, opt, ctx=ctx, stream=stream, out=out)
+    return out["rgb"], out["T"], out["depth"], out["normal"]
 
 
 def drk_render_backward(scene: DeviceScene, cam, opt: Options | None, state: State, dL_drgb: torch.Tensor,
@@ -503,6 +522,55 @@ class Adam:
         _check(lib().drk_adam_step(C.byref(p), C.byref(g), C.byref(m), C.byref(v), C.byref(hp), C.byref(a),
                                    _stream_ptr(stream)))
         return self.scene
+
+
+# ---------------------------------------------------------------------------
+# mesh to DRK
+
+class drk_mesh_options_t(C.Structure):
+    _fields_ = [("K", C.c_int32), ("edge_density", C.c_float), ("tau", C.c_float), ("opacity", C.c_float),
+                ("light", C.c_float * 3), ("ambient", C.c_float), ("diffuse", C.c_float)]
+
+
+@dataclass
+class MeshOptions:
+    """drk_mesh_options_t (include/drk.h documents every field)."""
+    K: int = 4
+    edge_density: float = 0.5
+    tau: float = 0.95
+    opacity: float = 1.0
+    light: tuple = (0.3, -0.5, -0.8)
+    ambient: float = 0.35
+    diffuse: float = 0.65
+
+    def to_c(self) -> drk_mesh_options_t:
+        o = drk_mesh_options_t()
+        o.K, o.edge_density, o.tau, o.opacity = int(self.K), float(self.edge_density), float(self.tau), \
+            float(self.opacity)
+        for i in range(3):
+            o.light[i] = float(self.light[i])
+        o.ambient, o.diffuse = float(self.ambient), float(self.diffuse)
+        return o
+
+
+def mesh_to_drk(verts: torch.Tensor, faces: torch.Tensor, face_color: torch.Tensor | None = None,
+                opt: MeshOptions | None = None, stream=None):
+    """One DRK per face (drk_mesh_to_drk).  verts (V, 3) float32, faces
+    (F, face_size) int32 with -1 padding, face_color (F, 3) or None, all on
+    the GPU.  Returns (DeviceScene with sh_degree -1, status (F,) int32)."""
+    opt = opt or MeshOptions()
+    assert verts.is_cuda and verts.dtype == torch.float32 and verts.is_contiguous()
+    assert faces.is_cuda and faces.dtype == torch.int32 and faces.is_contiguous() and faces.dim() == 2
+    F, K, dev = int(faces.shape[0]), int(opt.K), verts.device
+    sc = DeviceScene(torch.empty((F, 3), device=dev), torch.empty((F, 4), device=dev), torch.empty((F, K), device=dev),
+                     torch.empty((F, K), device=dev), torch.empty(F, device=dev), torch.empty(F, device=dev),
+                     torch.empty(F, device=dev), torch.empty((F, 3), device=dev), sh_degree=-1)
+    status = torch.empty(F, dtype=torch.int32, device=dev)
+    o, arr = opt.to_c(), _arrays_c(sc.tensors())
+    _check(lib().drk_mesh_to_drk(_fptr(verts), int(verts.shape[0]), C.cast(C.c_void_p(faces.data_ptr()), _ip),
+                                 F, int(faces.shape[1]), _fptr(face_color), C.byref(o), C.byref(arr),
+                                 C.cast(C.c_void_p(status.data_ptr()), _ip), _stream_ptr(stream)))
+    return sc, status
 
 
 # ---------------------------------------------------------------------------
