@@ -6,6 +6,8 @@ forward + backward render (Sec. 4.4 pipeline and its reverse mode) of a
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl drk|reference]
     python bench.py --serve [--serve-requests R] [--serve-rate HZ] [--serve-batch B]
     python bench.py --order-study     (forward only: exact vs cache-sorting order)
+    python bench.py --train           (training step with the fused Adam update)
+    python bench.py --mesh            (mesh to DRK conversion and render)
 
 One process per GPU (torchrun for N > 1).  The path does not shard: every
 rank renders its own replica of the workload ("replicas only"), value =
@@ -60,6 +62,10 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=160)
     ap.add_argument("--serve-rate", type=float, default=0.0, help="arrivals per second (0 = all at once)")
     ap.add_argument("--serve-batch", type=int, default=16)
+    ap.add_argument("--train", action="store_true",
+                    help="training step: render + L1 gradient + backward + fused Adam (activations included)")
+    ap.add_argument("--mesh", action="store_true",
+                    help="mesh to DRK: conversion of a 518k-triangle wall and its 1080p render with depth and normal")
     ap.add_argument("--order-study", action="store_true",
                     help="forward-only comparison of the exact order with the paper's cache-sorting order")
     return ap.parse_args()
@@ -413,6 +419,160 @@ def order_study(args):
     return 0
 
 
+def train_bench(args):
+    """Training steps of 100k DRKs (K = 8, SH degree 3) fitted to a synthetic
+    1920 x 1080 shape image: render with a backward state, L1 gradient,
+    render backward, fused activation backward + Adam + activation
+    (supplementary "Parametrization" and "Model Training").  One JSON line
+    with the step rate and the Adam kernel against the HBM roofline."""
+    import torch
+    from paper_2412_11752_gb300 import drk
+    dev = torch.device("cuda", 0)
+    n, K, sh, W, H = 100_000, 8, 3, 1920, 1080
+    cam = synth.camera_front(W, H)
+    raw = drk.RawScene.from_arrays(synth.raw_scene(n, K, seed=6002, sh_degree=sh), sh_degree=sh, device=dev)
+    target = torch.from_numpy(synth.shape_target(H, W)).to(dev)
+    opt = drk.Adam(raw)
+    ropt = drk.Options(bg=(0.35, 0.35, 0.35))
+    ctx = drk.Context(0)
+    out = dict(rgb=torch.empty((3, H, W), device=dev), T=None, n=None)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    inv_n = 1.0 / float(3 * H * W)
+    losses = []
+
+    def step(k, ev=None):
+        rgb, _, _, st = drk.drk_render(opt.scene, cam, ropt, ctx=ctx, need_state=True, out=out)
+        diff = rgb - target
+        losses.append(diff.abs().mean())
+        g = drk.drk_render_backward(opt.scene, cam, ropt, st, torch.sign(diff).mul_(inv_n), ctx=ctx)
+        st.free()
+        if ev is not None:
+            ev[0].record()
+        opt.step(g, drk.learning_rates(k, 35000))
+        if ev is not None:
+            ev[1].record()
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    mk = lambda: torch.cuda.Event(enable_timing=True)
+    st_ev = [(mk(), mk()) for _ in range(args.steps)]
+    ad_ev = [(mk(), mk()) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        st_ev[k][0].record()
+        step(args.warmup + k, ad_ev[k])
+        st_ev[k][1].record()
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in st_ev]))
+    adam_ms = float(np.mean([a.elapsed_time(b) for a, b in ad_ev]))
+    ncol = 3 * (sh + 1) ** 2
+    # algorithmic bytes of one update: every raw float read with its gradient
+    # and two moments, written back with the moments (28 B); activated
+    # arrays written once more (quat, K scales, K angles, eta, tau, opacity)
+    floats = 3 + 4 + 2 * K + 3 + ncol
+    adam_bytes = n * (28 * floats + 4 * (7 + 2 * K))
+    peak = float(measured_peaks().get("hbm_gbs") or 6800.0)
+    achieved = adam_bytes / (adam_ms / 1e3) / 1e9
+    print(json.dumps({"metric": "training steps/s (render + backward + fused Adam) at 1080p/100k DRK",
+                      "value": 1e3 / ms, "unit": "steps/s", "ms_per_step": ms, "mpix_s": H * W / ms / 1e3,
+                      "steps": args.steps, "warmup": args.warmup, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": "train-100k-1080p (raw init, shape target)", "primitives": n, "K": K,
+                                 "sh_degree": sh, "width": W, "height": H,
+                                 "l2": "flushed between timed steps (256 MiB write)"},
+                      "adam": {"ms": adam_ms, "bytes_per_launch": adam_bytes,
+                               "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                                            "frac": achieved / peak, "peak_basis": "hbm_gbs of MEASURED_PEAKS.json"}},
+                      "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
+                      "gpu_launches_adam_per_step": 1}), flush=True)
+    return 0
+
+
+def mesh_bench(args):
+    """Mesh to DRK (Sec. 5.4): conversion of a 720 x 360-cell triangulated
+    height-field wall (518,400 faces, K = 3) and its 1920 x 1080 render:
+    exact order, exact with depth and normal images, and the cache-sorting
+    order (the supplement notes that converted meshes depend on the order;
+    that mode packs a centre-depth rank into the 19 depth bits of a 1080p
+    pair key, so it takes at most 2^19 primitives).  One JSON line."""
+    import torch
+    from paper_2412_11752_gb300 import drk
+    dev = torch.device("cuda", 0)
+    W, H = 1920, 1080
+    verts, faces = synth.mesh_heightfield(720, 360, seed=7003, triangles=True)
+    colors = synth.mesh_colors(len(faces), seed=7203)
+    v, f, c = (torch.from_numpy(x).to(dev) for x in (verts, faces, colors))
+    mopt = drk.MeshOptions(K=3, tau=0.95)
+    cam = synth.camera_front(W, H)
+    ctx = drk.Context(0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    mk = lambda: torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ev = [(mk(), mk()) for _ in range(args.steps)]
+        for a, b in ev:
+            flush.zero_()
+            a.record()
+            fn()
+            b.record()
+        torch.cuda.synchronize()
+        return float(np.mean([a.elapsed_time(b) for a, b in ev]))
+
+    holder = {}
+
+    def convert():
+        holder["sc"], holder["st"] = drk.mesh_to_drk(v, f, c, mopt)
+
+    conv_ms = timed(convert)
+    sc, st = holder["sc"], holder["st"]
+    n_rejected = int((st != 0).sum())
+    nf = len(faces)
+    # algorithmic bytes per face: the index row and three gathered vertices
+    # and the colour read; mu, quat, scale, theta, eta, tau, opacity, colour
+    # and status written
+    bytes_face = 4 * 3 + 3 * 12 + 12 + 4 * (3 + 4 + 3 + 3 + 1 + 1 + 1 + 3) + 4
+    peak = float(measured_peaks().get("hbm_gbs") or 6800.0)
+    res = {}
+    imgs = {}
+    for name, opt, aux in (("exact", drk.Options(), False), ("exact_depth_normal", drk.Options(), True),
+                           ("cache8", drk.Options(order_mode=1, kbuf_capacity=8), False)):
+        out = dict(rgb=torch.empty((3, H, W), device=dev), T=torch.empty((H, W), device=dev), n=None)
+        if aux:
+            out["depth"] = torch.empty((H, W), device=dev)
+            out["normal"] = torch.empty((3, H, W), device=dev)
+        ctx.timing_enable(True)
+        ms = timed(lambda: drk.drk_render(sc, cam, opt, ctx=ctx, out=out))
+        stage = ctx.timing_read()
+        ctx.timing_enable(False)
+        imgs[name] = out["rgb"].clone()
+        res[name] = {"ms_per_frame": ms, "mpix_s": H * W / ms / 1e3,
+                     "stages_ms": {k: v_[0] / max(1, v_[1]) for k, v_ in stage.items() if v_[1]}}
+        if aux:
+            cov = (1.0 - out["T"]).clamp_min(1e-6)
+            inner = cov > 0.9
+            res[name]["mean_depth_covered"] = float((out["depth"] / cov)[inner].mean())
+    d = (imgs["cache8"] - imgs["exact"]).abs()
+    mse = float(((imgs["cache8"] - imgs["exact"]) ** 2).mean())
+    res["cache8"]["vs_exact"] = {"max_abs": float(d.max()), "mean_abs": float(d.mean()),
+                                 "psnr_db": 10 * np.log10(1.0 / mse) if mse > 0 else None,
+                                 "pixels_over_1e-3": int((d.amax(0) > 1e-3).sum())}
+    print(json.dumps({"metric": "mesh to DRK: faces/s converted and 1080p frames/s rendered", "unit": "faces/s",
+                      "value": nf / (conv_ms / 1e3), "steps": args.steps, "warmup": args.warmup, "dtype": "f32",
+                      "data": "synthetic", "config": {"workload": "heightfield-518k-tri-1080p", "faces": nf, "K": 3,
+                                                      "tau": 0.95, "width": W, "height": H,
+                                                      "l2": "flushed between timed calls (256 MiB write)"},
+                      "convert": {"ms": conv_ms, "rejected": n_rejected,
+                                  "roofline": {"bound": "hbm", "achieved": nf * bytes_face / (conv_ms / 1e3) / 1e9,
+                                               "peak": peak, "unit": "GB/s",
+                                               "frac": nf * bytes_face / (conv_ms / 1e3) / 1e9 / peak,
+                                               "bytes_per_face": bytes_face}},
+                      "render": res}), flush=True)
+    return 0
+
+
 def serve_run(D, torch, dscenes, reqs, max_batch: int, budget: int) -> dict:
     """Replays (arrival_s, scene, camera) requests through one server; latency
     = completion - arrival of each request, throughput over the whole run."""
@@ -470,6 +630,10 @@ def main():
         return run_serve(args)
     if args.order_study:
         return order_study(args)
+    if args.train:
+        return train_bench(args)
+    if args.mesh:
+        return mesh_bench(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_drk(args)
