@@ -53,8 +53,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-pixels", type=int, default=1024, help="oracle sample size (pixels, fwd+bwd)")
-    ap.add_argument("--cull-level", type=int, default=2, choices=(0, 1, 2),
-                    help="tile culling: 0 none, 1 screen rectangle, 2 per-tile test (same image)")
+    ap.add_argument("--cull-level", type=int, default=2, choices=(0, 1, 2, 3),
+                    help="tile culling: 0 none, 1 screen rectangle, 2 per-tile test (same image), "
+                         "3 the paper's endpoint polygon (lossy)")
     ap.add_argument("--kbuf-capacity", type=int, default=8, choices=(8, 16, 32),
                     help="per-pixel depth-order buffer entries (any value gives the same image)")
     ap.add_argument("--serve", action="store_true",
@@ -383,7 +384,11 @@ def order_study(args):
     ctx = drk.Context(0)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     modes = {"exact": drk.Options(), "cache8": drk.Options(order_mode=1, kbuf_capacity=8),
-             "cache16": drk.Options(order_mode=1, kbuf_capacity=16)}
+             "cache16": drk.Options(order_mode=1, kbuf_capacity=16),
+             # the paper's tile culling as printed (Eq. 11 - Eq. 12), alone and
+             # with the cache: the whole pipeline as the paper states it
+             "exact_papercull": drk.Options(cull_level=drk.CULL_PAPER),
+             "cache8_papercull": drk.Options(order_mode=1, kbuf_capacity=8, cull_level=drk.CULL_PAPER)}
     res, imgs = {}, {}
     for name, opt in modes.items():
         out = dict(rgb=torch.empty((3, H, W), device=dev), T=None, n=None)
@@ -402,9 +407,9 @@ def order_study(args):
         ctx.timing_enable(False)
         ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
         imgs[name] = out["rgb"].clone()
-        res[name] = {"ms_per_frame": ms, "mpix_s": H * W / ms / 1e3,
+        res[name] = {"ms_per_frame": ms, "mpix_s": H * W / ms / 1e3, "pairs": ctx.stats()["n_pairs"],
                      "stages_ms": {k: v[0] / max(1, v[1]) for k, v in stage.items() if v[1]}}
-    for name in ("cache8", "cache16"):
+    for name in [m for m in modes if m != "exact"]:
         d = (imgs[name] - imgs["exact"]).abs()
         mse = float(((imgs[name] - imgs["exact"]) ** 2).mean())
         res[name]["vs_exact"] = {"max_abs": float(d.max()), "mean_abs": float(d.mean()),

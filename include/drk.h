@@ -111,13 +111,22 @@ enum {
     DRK_ORDER_CACHE_SORT = 1
 };
 
-/* Tile culling levels (Sec. 4.4, "Kernel Culling").  All three give the
- * same image bit for bit: culling only removes pairs that cannot reach
- * alpha_min. */
+/* Tile culling levels (Sec. 4.4, "Kernel Culling").  The first three give
+ * the same image bit for bit: culling only removes pairs that cannot reach
+ * alpha_min.  DRK_CULL_PAPER is the paper's culling as printed, kept for
+ * comparison: a tile is kept iff it meets the polygon of the basis
+ * endpoints v_k = mu + s_k sqrt(-log Psi^-1(alpha_min / o)) (cos theta_k
+ * R_x + sin theta_k R_y) (Eq. 11 - Eq. 12), tested in the primitive's plane
+ * with the tile's corner pixels.  It is lossy: Eq. 11 omits the factor 2
+ * of the exponent (the printed radius is 1/sqrt 2 of the alpha_min contour
+ * at o = 1, tau = 0), the chords between endpoints cut off the L2 contour,
+ * and the low-pass filter's disc is not considered.  Tiles whose corner
+ * rays do not all meet the plane in front of the camera are kept. */
 enum {
     DRK_CULL_NONE = 0,   /* every primitive is paired with every tile */
     DRK_CULL_RECT = 1,   /* tiles of the screen rectangle of the K-basis bound */
-    DRK_CULL_TILE = 2    /* plus a per-tile test against the per-sector radii */
+    DRK_CULL_TILE = 2,   /* plus a per-tile test against the per-sector radii */
+    DRK_CULL_PAPER = 3   /* the paper's endpoint polygon (lossy) */
 };
 
 typedef struct {

@@ -41,6 +41,12 @@
  *   R7  colour: plain RGB, or real spherical harmonics of degree <= 3 in the
  *       view direction camera centre -> mu, plus 0.5, clamped below at 0.
  *   R8  background colour bg is added with the final transmittance.
+ *   R10 cull_paper 1 applies the paper's tile culling as printed (Sec. 4.4,
+ *       Eq. 11 - Eq. 12): a primitive reaches the pixels of a 16 x 16 tile only
+ *       if the polygon of its basis endpoints at s_k sqrt(-log
+ *       Psi^-1(alpha_min / o)) meets the tile, tested in the primitive's
+ *       plane against the quad of the tile's corner pixel centres; tiles whose
+ *       corner rays do not all meet the plane in front of the camera are kept.
  *   R9  order_mode 1 composites in the order of the paper's cache-sorting
  *       (Sec. 4.4 "Cache Sorting", supplementary Algorithm 1) instead of the
  *       exact order: pre-sort by centre depth, a cache of cache_len entries
@@ -87,6 +93,7 @@ typedef struct {
     double bg[3];
     int order_mode;         /* 0: exact (r_t, index) order; 1: the paper's cache-sorting */
     int cache_len;          /* cache length of order_mode 1 (the paper uses 8) */
+    int cull_paper;         /* 1: the paper's endpoint-polygon tile culling (lossy), reading R10 */
 } ord_options;
 
 /* parity flags written per pixel by ord_render */
@@ -95,6 +102,8 @@ typedef struct {
 #define ORD_FLAG_DEPTH_TIE 4   /* two contributors with near-equal depth and visible order effect */
 #define ORD_FLAG_STEEP     8   /* float32 error of the alphas could exceed half the tolerance
                                   (near-hard edges: Psi's middle slope (1+tau)/(1-tau)) */
+#define ORD_FLAG_CULL      16  /* a contributor whose paper-culling decision for the pixel's
+                                  tile is within float32 margin */
 
 /* ------------------------------------------------------------------------ */
 /* Sharpening, Eq. 9, and its inverse (used by tests and by the culling
@@ -611,6 +620,115 @@ done:
     return tie;
 }
 
+/* Does the convex quad (qu, qv) meet the polygon (px, py) of K vertices,
+ * star-shaped about the origin?  Either holds a vertex of the other (the
+ * origin stands for the polygon), or two edges cross.                       */
+static int quad_meets_polygon(const double *qu, const double *qv, const double *px, const double *py, int K)
+{
+    double pts[17][2];
+    pts[0][0] = 0.0;
+    pts[0][1] = 0.0;
+    for (int k = 0; k < K; k++) {
+        pts[k + 1][0] = px[k];
+        pts[k + 1][1] = py[k];
+    }
+    for (int j = 0; j <= K; j++) {
+        int pos = 0, neg = 0;
+        for (int c = 0; c < 4; c++) {
+            int n = (c + 1) & 3;
+            double cr = (qu[n] - qu[c]) * (pts[j][1] - qv[c]) - (qv[n] - qv[c]) * (pts[j][0] - qu[c]);
+            pos += cr > 0.0;
+            neg += cr < 0.0;
+        }
+        if (pos == 0 || neg == 0) return 1;
+    }
+    for (int c = 0; c < 4; c++) {           /* even-odd rule, ray towards +u */
+        int in = 0;
+        for (int k = 0; k < K; k++) {
+            int k1 = (k + 1) % K;
+            if ((py[k] > qv[c]) != (py[k1] > qv[c])) {
+                double xc = px[k] + (qv[c] - py[k]) * (px[k1] - px[k]) / (py[k1] - py[k]);
+                if (qu[c] < xc) in = !in;
+            }
+        }
+        if (in) return 1;
+    }
+    for (int k = 0; k < K; k++) {
+        int k1 = (k + 1) % K;
+        for (int c = 0; c < 4; c++) {
+            int n = (c + 1) & 3;
+            double d1 = (px[k1] - px[k]) * (qv[c] - py[k]) - (py[k1] - py[k]) * (qu[c] - px[k]);
+            double d2 = (px[k1] - px[k]) * (qv[n] - py[k]) - (py[k1] - py[k]) * (qu[n] - px[k]);
+            double d3 = (qu[n] - qu[c]) * (py[k] - qv[c]) - (qv[n] - qv[c]) * (px[k] - qu[c]);
+            double d4 = (qu[n] - qu[c]) * (py[k1] - qv[c]) - (qv[n] - qv[c]) * (px[k1] - qu[c]);
+            if (((d1 > 0.0) != (d2 > 0.0)) && ((d3 > 0.0) != (d4 > 0.0))) return 1;
+        }
+    }
+    return 0;
+}
+
+/* The paper's tile culling (reading R10) for primitive i and the tile of
+ * pixel (px, py).  Returns 1 to keep; *undecided is set when the decision
+ * changes with the polygon scaled by 1 -+ delta (delta covers the float32
+ * error of the corner mapping) or a corner ray is nearly parallel to the
+ * plane.                                                                    */
+static int paper_tile_keep(const ord_params *P, int64_t i, const ord_camera *cam, const ord_options *opt,
+                           const double *ocam, int px, int py, int *undecided)
+{
+    *undecided = 0;
+    const int K = P->K;
+    const double o = P->opacity[i];
+    if (o < opt->alpha_min) return 0;
+    double R[9];
+    ord_rotation(P->quat + 4 * i, R);
+    const double Rx[3] = {R[0], R[3], R[6]}, Ry[3] = {R[1], R[4], R[7]}, Rz[3] = {R[2], R[5], R[8]};
+    const double *mu = P->mu + 3 * i;
+    double m[3];
+    for (int c = 0; c < 3; c++) m[c] = mu[c] - ocam[c];
+    const double mz = dot3(m, Rz);
+    const int tx = px / 16, ty = py / 16;
+    const int xs[2] = {tx * 16, (tx * 16 + 15 < cam->width - 1) ? tx * 16 + 15 : cam->width - 1};
+    const int ys[2] = {ty * 16, (ty * 16 + 15 < cam->height - 1) ? ty * 16 + 15 : cam->height - 1};
+    const int cx[4] = {xs[0], xs[1], xs[1], xs[0]}, cy[4] = {ys[0], ys[0], ys[1], ys[1]};
+    double w[4], wmin = 1e300, wmax = -1e300, qu[4], qv[4], wabs = 0.0;
+    for (int c = 0; c < 4; c++) {
+        double d[3];
+        cam_ray(cam, cx[c], cy[c], d);
+        w[c] = dot3(d, Rz) / mz;                  /* 1 / r_t at the corner */
+        wmin = fmin(wmin, w[c]);
+        wmax = fmax(wmax, w[c]);
+        wabs = fmax(wabs, fabs(w[c]));
+        if (w[c] > 0.0) {
+            double p[3];
+            for (int r = 0; r < 3; r++) p[r] = d[r] / w[c] - m[r];
+            qu[c] = dot3(p, Rx);
+            qv[c] = dot3(p, Ry);
+        }
+    }
+    if (wmax <= 0.0) return 0;
+    if (fabs(wmin) <= 1e-5 * wabs) *undecided = 1;
+    if (wmin <= 0.0) return 1;
+    const double cl = sqrt(fmax(-log(ord_psi_inv(opt->alpha_min / o, P->tau[i])), 0.0));
+    double pxs[16], pys[16], ext_p = 0.0, ext_q = 0.0;
+    for (int k = 0; k < K; k++) {
+        pxs[k] = cl * P->scale[K * i + k] * cos(P->theta[K * i + k]);
+        pys[k] = cl * P->scale[K * i + k] * sin(P->theta[K * i + k]);
+        ext_p = fmax(ext_p, hypot(pxs[k], pys[k]));
+    }
+    for (int c = 0; c < 4; c++) ext_q = fmax(ext_q, hypot(qu[c], qv[c]));
+    const int keep = quad_meets_polygon(qu, qv, pxs, pys, K);
+    const double delta = 1e-4 * fmax(1.0, ext_q / fmax(ext_p, 1e-300));
+    double sx[16], sy[16];
+    for (int sgn = -1; sgn <= 1; sgn += 2) {
+        for (int k = 0; k < K; k++) {
+            sx[k] = pxs[k] * (1.0 + sgn * delta);
+            sy[k] = pys[k] * (1.0 + sgn * delta);
+        }
+        if (quad_meets_polygon(qu, qv, sx, sy, K) != keep) *undecided = 1;
+    }
+    return keep;
+}
+
 static int64_t gather_contributors(const ord_params *P, const ord_camera *cam, const ord_options *opt,
                                    const double *ocam, int px, int py, contrib *buf, int *near_amin)
 {
@@ -620,7 +738,13 @@ static int64_t gather_contributors(const ord_params *P, const ord_camera *cam, c
         pair_eval pe;
         eval_pair(P, i, cam, opt, ocam, px, py, &pe);
         if (!pe.valid) continue;
-        if (fabs(pe.alpha_tilde / opt->alpha_min - 1.0) < 1e-4) *near_amin = 1;
+        if (opt->cull_paper) {
+            int und;
+            const int keep = paper_tile_keep(P, i, cam, opt, ocam, px, py, &und);
+            if (und && pe.alpha_tilde >= opt->alpha_min) *near_amin |= 4;
+            if (!keep) continue;
+        }
+        if (fabs(pe.alpha_tilde / opt->alpha_min - 1.0) < 1e-4) *near_amin |= 1;
         if (pe.alpha_tilde >= opt->alpha_min) {
             buf[cnt].t = pe.t;
             buf[cnt].idx = i;
@@ -691,6 +815,7 @@ int ord_render(const ord_params *P, const ord_camera *cam, const ord_options *op
             double C[3] = {0, 0, 0}, T = 1.0;
             int flag = (near_amin & 1) ? ORD_FLAG_ALPHA_MIN : 0;
             if (near_amin & 2) flag |= ORD_FLAG_DEPTH_TIE;
+            if (near_amin & 4) flag |= ORD_FLAG_CULL;
             double cmax = 1.0;
             for (int c = 0; c < 3; c++) cmax = fmax(cmax, fabs(opt->bg[c]));
             double dT_rel = 0.0;     /* float32 error estimate of T (relative) */

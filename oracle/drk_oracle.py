@@ -31,6 +31,7 @@ FLAG_ALPHA_MIN = 1
 FLAG_T_MIN = 2
 FLAG_DEPTH_TIE = 4
 FLAG_STEEP = 8
+FLAG_CULL = 16
 
 
 @dataclass
@@ -44,6 +45,7 @@ class Options:
     bg: tuple = (0.0, 0.0, 0.0)
     order_mode: int = 0          # 0 exact (r_t, index) order; 1 the paper's cache-sorting
     cache_len: int = 8
+    cull_paper: int = 0          # 1: the paper's endpoint-polygon tile culling (lossy)
 
 
 class _Params(C.Structure):
@@ -64,7 +66,7 @@ class _Camera(C.Structure):
 class _Options(C.Structure):
     _fields_ = [("alpha_min", C.c_double), ("T_min", C.c_double), ("alpha_max", C.c_double),
                 ("lowpass_sl", C.c_double), ("near_plane", C.c_double), ("bg", C.c_double * 3),
-                ("order_mode", C.c_int), ("cache_len", C.c_int)]
+                ("order_mode", C.c_int), ("cache_len", C.c_int), ("cull_paper", C.c_int)]
 
 
 def build(force: bool = False) -> str:
@@ -161,6 +163,7 @@ def _options(opt: Options) -> _Options:
     for i in range(3):
         o.bg[i] = float(opt.bg[i])
     o.order_mode, o.cache_len = int(opt.order_mode), int(opt.cache_len)
+    o.cull_paper = int(opt.cull_paper)
     return o
 
 

@@ -185,7 +185,7 @@ drk_status_t validate(const drk_params_t* p, const drk_camera_t* cam, const drk_
     if (!(opt->T_min >= 0.f && opt->T_min < 1.f)) return fail(DRK_ERR_INVALID_ARG, "T_min not in [0, 1)");
     if (!(opt->lowpass_sl >= 0.f) || !std::isfinite(opt->lowpass_sl)) return fail(DRK_ERR_INVALID_ARG, "bad lowpass_sl");
     if (!finite_pos(opt->near_plane)) return fail(DRK_ERR_INVALID_ARG, "near_plane must be > 0");
-    if (opt->cull_level < 0 || opt->cull_level > 2) return fail(DRK_ERR_INVALID_ARG, "cull_level not in 0..2");
+    if (opt->cull_level < 0 || opt->cull_level > 3) return fail(DRK_ERR_INVALID_ARG, "cull_level not in 0..3");
     if (opt->kbuf_capacity != 8 && opt->kbuf_capacity != 16 && opt->kbuf_capacity != 32)
         return fail(DRK_ERR_INVALID_ARG, "kbuf_capacity must be 8, 16 or 32");
     if (opt->ovf_capacity < -1 || opt->ovf_capacity > 2048)

@@ -98,7 +98,8 @@ enum : int { B_X0 = 0, B_Y0, B_X1, B_Y1, B_ZLB, B_FCX, B_FCY, B_FR2, B_FLAGS, B_
 template <int KMAX>
 struct Bnd {
     static constexpr int ZC = B_RHO + KMAX;                    // view-space depth of mu
-    static constexpr int STRIDE = ((ZC + 1) + 3) / 4 * 4;
+    static constexpr int CPAPER = ZC + 1;                      // sqrt(-log g*) of Eq. 11 as printed
+    static constexpr int STRIDE = ((CPAPER + 1) + 3) / 4 * 4;
 };
 
 // Per-primitive record-space gradient accumulator used between the raster

@@ -258,10 +258,12 @@ __global__ void __launch_bounds__(128) preprocess_kernel(PreArgs A) {
     // ---- conservative screen bound
     int flags = 0;
     float rho[KMAX];
-    float rho_max = 0.f;
+    float rho_max = 0.f, c_paper = 0.f;
     const bool kernel_on = plane_ok && A.fc.alpha_min <= o;
     if (kernel_on) {
         const float gstar = psi_inv(A.fc.alpha_min / o, tau);
+        // Eq. 11 as printed (no factor 2): endpoints at s_k sqrt(-log g*)
+        c_paper = sqrtf(fmaxf(-logf(fmaxf(gstar, 1e-38f)), 0.f));
         const float Estar = -2.f * logf(fmaxf(gstar, 1e-38f)) * 1.004f + 1e-4f;
         const float sq = sqrtf(Estar) * 1.002f;
         for (int k = 0; k < KMAX; k++) {
@@ -348,6 +350,7 @@ __global__ void __launch_bounds__(128) preprocess_kernel(PreArgs A) {
     bnd[B_RHOMAX] = rho_max;
     for (int k = 0; k < KMAX; k++) bnd[B_RHO + k] = rho[k];
     for (int j = B_RHO + KMAX; j < Bnd<KMAX>::STRIDE; j++) bnd[j] = 0.f;
+    bnd[Bnd<KMAX>::CPAPER] = c_paper;
     bnd[Bnd<KMAX>::ZC] = G.muc[2];
     const bool nonempty = x1 >= x0 && y1 >= y0;
     A.count[i] = nonempty ? (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1)) : 0u;
@@ -357,9 +360,65 @@ __global__ void __launch_bounds__(128) preprocess_kernel(PreArgs A) {
 // ---------------------------------------------------------------------------
 // Per-(primitive, tile) test.  Returns whether the pair may contribute and
 // a lower bound of r_t over the tile's contributing pixels.
+// Does the quad q (the corner pixels of a tile mapped into the plane frame,
+// convex) meet the polygon of the K endpoints cl (EX_k, EY_k) (star-shaped
+// about the origin, counter-clockwise)?  Either contains a vertex of the
+// other, or two edges cross.
+template <int KMAX>
+__device__ bool quad_meets_polygon(const float (&qu)[4], const float (&qv)[4], const float* __restrict__ ex,
+                                   const float* __restrict__ ey, int K, float cl) {
+    float px[KMAX], py[KMAX];
+    for (int k = 0; k < KMAX; k++) {
+        px[k] = k < K ? cl * ex[k] : 0.f;
+        py[k] = k < K ? cl * ey[k] : 0.f;
+    }
+    // a polygon vertex (or the origin, inside the polygon) inside the quad
+    auto in_quad = [&](float x, float y) {
+        int pos = 0, neg = 0;
+        for (int c = 0; c < 4; c++) {
+            const int n = (c + 1) & 3;
+            const float cr = (qu[n] - qu[c]) * (y - qv[c]) - (qv[n] - qv[c]) * (x - qu[c]);
+            pos += cr > 0.f;
+            neg += cr < 0.f;
+        }
+        return pos == 0 || neg == 0;
+    };
+    if (in_quad(0.f, 0.f)) return true;
+    for (int k = 0; k < K; k++)
+        if (in_quad(px[k], py[k])) return true;
+    // a quad corner inside the polygon (crossings of a ray towards +u)
+    for (int c = 0; c < 4; c++) {
+        bool in = false;
+        for (int k = 0; k < K; k++) {
+            const int k1 = (k + 1 == K) ? 0 : k + 1;
+            const float ya = py[k], yb = py[k1];
+            if ((ya > qv[c]) != (yb > qv[c])) {
+                const float xc = px[k] + (qv[c] - ya) * (px[k1] - px[k]) / (yb - ya);
+                if (qu[c] < xc) in = !in;
+            }
+        }
+        if (in) return true;
+    }
+    // proper edge crossings
+    for (int k = 0; k < K; k++) {
+        const int k1 = (k + 1 == K) ? 0 : k + 1;
+        const float ax = px[k], ay = py[k], bx = px[k1], by = py[k1];
+        for (int c = 0; c < 4; c++) {
+            const int n = (c + 1) & 3;
+            const float d1 = (bx - ax) * (qv[c] - ay) - (by - ay) * (qu[c] - ax);
+            const float d2 = (bx - ax) * (qv[n] - ay) - (by - ay) * (qu[n] - ax);
+            const float d3 = (qu[n] - qu[c]) * (ay - qv[c]) - (qv[n] - qv[c]) * (ax - qu[c]);
+            const float d4 = (qu[n] - qu[c]) * (by - qv[c]) - (qv[n] - qv[c]) * (bx - qu[c]);
+            if (((d1 > 0.f) != (d2 > 0.f)) && ((d3 > 0.f) != (d4 > 0.f))) return true;
+        }
+    }
+    return false;
+}
+
 template <int KMAX>
 __device__ __forceinline__ bool tile_test(const float* __restrict__ rec, const float* __restrict__ bnd, int K,
-                                          const FrameConst& fc, int tx, int ty, bool do_cull, float& lb) {
+                                          const FrameConst& fc, int tx, int ty, int cull, float& lb) {
+    const bool do_cull = cull >= DRK_CULL_TILE, paper = cull == DRK_CULL_PAPER;
     const float x0 = (float)(tx * kTile), y0 = (float)(ty * kTile);
     const float x1 = (float)min(tx * kTile + kTile - 1, fc.width - 1);
     const float y1 = (float)min(ty * kTile + kTile - 1, fc.height - 1);
@@ -385,15 +444,24 @@ __device__ __forceinline__ bool tile_test(const float* __restrict__ rec, const f
     if (!do_cull) return true;
     if (wmax <= 0.f) return false;                                 // plane behind every pixel
     if (wmin * fc.near_plane >= 1.f + 1e-5f) return false;         // every r_t below the near plane
-    if (keep_f) return true;
+    if (keep_f && !paper) return true;
     if (!kernel_on) return false;
-    if (crosses || wmin <= 0.f) return true;                       // no quad: keep
+    // no quad: keep (the paper's polygon test needs only w > 0 at the corners:
+    // then the tile maps to a convex quad of the plane, whatever the bound)
+    if ((crosses && !paper) || wmin <= 0.f) return true;
     // tile corners in the rotated plane frame
     float qu[4], qv[4];
     for (int c = 0; c < 4; c++) {
         const float it = 1.f / w[c];
         qu[c] = fmaf(rec[R_HU0], cx[c], fmaf(rec[R_HU1], cy[c], rec[R_HU2])) * it;
         qv[c] = fmaf(rec[R_HV0], cx[c], fmaf(rec[R_HV1], cy[c], rec[R_HV2])) * it;
+    }
+    if (paper) {
+        // the paper's culling (Sec. 4.4, Eq. 11 - Eq. 12): the polygon of the
+        // basis endpoints at the calibrated lengths; lossy (see DRK_CULL_PAPER)
+        using RK = Rec<KMAX>;
+        const float cl = bnd[Bnd<KMAX>::CPAPER];
+        return cl > 0.f && quad_meets_polygon<KMAX>(qu, qv, rec + RK::EX, rec + RK::EY, K, cl);
     }
     // distance from the centre to the quad, and whether it contains it
     float dmin2 = 1e30f;
@@ -465,7 +533,7 @@ __global__ void __launch_bounds__(256) count_kernel(PreArgs A) {
         bool keep = false;
         if (j < area) {
             float lb;
-            keep = tile_test<KMAX>(rec, bnd, A.p.K, A.fc, x0 + j % wdt, y0 + j / wdt, true, lb);
+            keep = tile_test<KMAX>(rec, bnd, A.p.K, A.fc, x0 + j % wdt, y0 + j / wdt, A.cull_level, lb);
         }
         cnt += __popc(__ballot_sync(0xffffffffu, keep));
     }
@@ -492,7 +560,7 @@ __global__ void __launch_bounds__(256) emit_kernel(PreArgs A) {
     const int area = wdt * (y1 - y0 + 1);
     uint64_t out = A.offsets[i];
     const uint64_t end = A.offsets[i + 1];
-    const bool cull = A.cull_level >= 2;
+    const int cull = A.cull_level >= DRK_CULL_TILE ? A.cull_level : DRK_CULL_NONE;
     for (int base = 0; base < area; base += 32) {
         const int j = base + lane;
         bool keep = false;

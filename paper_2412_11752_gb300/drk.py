@@ -19,7 +19,7 @@ from . import build as _build
 DRK_OK = 0
 STATUS = {0: "DRK_OK", 1: "DRK_ERR_INVALID_ARG", 2: "DRK_ERR_OOM", 3: "DRK_ERR_CUDA", 4: "DRK_ERR_CAPACITY",
           5: "DRK_ERR_TIMEOUT", 6: "DRK_ERR_BUSY", 7: "DRK_ERR_NOT_FOUND"}
-CULL_NONE, CULL_RECT, CULL_TILE = 0, 1, 2
+CULL_NONE, CULL_RECT, CULL_TILE, CULL_PAPER = 0, 1, 2, 3
 PARAM_NAMES = ("mu", "quat", "scale", "theta", "eta", "tau", "opacity", "color")
 
 

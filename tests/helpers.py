@@ -15,12 +15,13 @@ def oracle_options(opt) -> O.Options:
     """The oracle's options with the float32 values the GPU uses."""
     return O.Options(alpha_min=f32(opt.alpha_min), T_min=f32(opt.T_min), alpha_max=f32(opt.alpha_max),
                      lowpass_sl=f32(opt.lowpass_sl), near=f32(opt.near_plane), bg=tuple(f32(b) for b in opt.bg),
-                     order_mode=int(getattr(opt, "order_mode", 0)), cache_len=int(opt.kbuf_capacity))
+                     order_mode=int(getattr(opt, "order_mode", 0)), cache_len=int(opt.kbuf_capacity),
+                     cull_paper=int(getattr(opt, "cull_level", 2) == 3))
 
 
 def excluded(flags: np.ndarray) -> np.ndarray:
     """Pixels whose result is decided by an FP32-vs-FP64 threshold or depth tie."""
-    return (flags & (O.FLAG_T_MIN | O.FLAG_DEPTH_TIE | O.FLAG_STEEP)) != 0
+    return (flags & (O.FLAG_T_MIN | O.FLAG_DEPTH_TIE | O.FLAG_STEEP | O.FLAG_CULL)) != 0
 
 
 def image_error(gpu_rgb: np.ndarray, ref_rgb: np.ndarray, flags: np.ndarray):

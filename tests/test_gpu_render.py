@@ -235,3 +235,22 @@ def test_cache_sort_has_no_backward(drk):
     with pytest.raises(drk.DrkError) as e:
         drk.drk_render(ds, synth.camera_front(16, 16), drk.Options(order_mode=1), need_state=True)
     assert e.value.code == 1
+
+
+# ---------------------------------------------------------------------------
+# the paper's tile culling as printed (Eq. 11 - Eq. 12): lossy, checked
+# against the oracle applying the same rule
+
+@pytest.mark.parametrize("K,seed,sh", [(8, 2310, -1), (5, 2311, -1), (12, 2312, 1)])
+def test_paper_culling_matches_oracle(drk, K, seed, sh):
+    scene = synth.scene_plain(1500, K, seed=seed, sh_degree=sh)
+    cam = synth.camera_front(96, 80)
+    opt = drk.Options(cull_level=drk.CULL_PAPER)
+    rgb, ref = check_full(drk, scene, cam, opt)
+    pairs_paper = drk.default_context().stats()["n_pairs"]
+    render_gpu(drk, scene, cam, drk.Options())
+    pairs_tile = drk.default_context().stats()["n_pairs"]
+    assert pairs_paper < pairs_tile
+    # lossy: the image differs from the exact one
+    exact = O.render(scene, cam, oracle_options(drk.Options()))
+    assert np.abs(ref["rgb"] - exact["rgb"]).max() > 1e-3
