@@ -99,7 +99,8 @@ template <int KMAX>
 struct Bnd {
     static constexpr int ZC = B_RHO + KMAX;                    // view-space depth of mu
     static constexpr int CPAPER = ZC + 1;                      // sqrt(-log g*) of Eq. 11 as printed
-    static constexpr int STRIDE = ((CPAPER + 1) + 3) / 4 * 4;
+    static constexpr int CL1 = CPAPER + 1;                     // L1 bound sqrt(E* / eta) (0: none)
+    static constexpr int STRIDE = ((CL1 + 1) + 3) / 4 * 4;
 };
 
 // Per-primitive record-space gradient accumulator used between the raster

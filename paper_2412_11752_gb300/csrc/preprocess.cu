@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(128) preprocess_kernel(PreArgs A) {
     // ---- conservative screen bound
     int flags = 0;
     float rho[KMAX];
-    float rho_max = 0.f, c_paper = 0.f;
+    float rho_max = 0.f, c_paper = 0.f, l1_bound = 0.f;
     const bool kernel_on = plane_ok && A.fc.alpha_min <= o;
     if (kernel_on) {
         const float gstar = psi_inv(A.fc.alpha_min / o, tau);
@@ -266,6 +266,10 @@ __global__ void __launch_bounds__(128) preprocess_kernel(PreArgs A) {
         c_paper = sqrtf(fmaxf(-logf(fmaxf(gstar, 1e-38f)), 0.f));
         const float Estar = -2.f * logf(fmaxf(gstar, 1e-38f)) * 1.004f + 1e-4f;
         const float sq = sqrtf(Estar) * 1.002f;
+        // Eq. 8's exponent is at least eta r1^2, so alpha >= alpha_min needs
+        // r1 <= sqrt(E* / eta): inside the polygon of the endpoints e_k scaled
+        // by that factor (Eq. 7's r1 is 1 on the chord between e_k and e_k1)
+        if (eta > 1e-3f) l1_bound = sqrtf(Estar / eta) * 1.002f;
         for (int k = 0; k < KMAX; k++) {
             if (k < K) {
                 const int k1 = (k + 1 == K) ? 0 : k + 1;
@@ -351,6 +355,7 @@ __global__ void __launch_bounds__(128) preprocess_kernel(PreArgs A) {
     for (int k = 0; k < KMAX; k++) bnd[B_RHO + k] = rho[k];
     for (int j = B_RHO + KMAX; j < Bnd<KMAX>::STRIDE; j++) bnd[j] = 0.f;
     bnd[Bnd<KMAX>::CPAPER] = c_paper;
+    bnd[Bnd<KMAX>::CL1] = l1_bound;
     bnd[Bnd<KMAX>::ZC] = G.muc[2];
     const bool nonempty = x1 >= x0 && y1 >= y0;
     A.count[i] = nonempty ? (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1)) : 0u;
@@ -500,15 +505,32 @@ __device__ __forceinline__ bool tile_test(const float* __restrict__ rec, const f
     }
     const float eps = 2e-3f;
     const float lo = A0 - eps, hi = A0 + (kTwoPi - best) + eps;
+    // In each sector the quad overlaps: the wedge radius, and the chord of
+    // the L1 bound (a sector's part of the polygon {r1 <= L} is the triangle
+    // (0, L e_k, L e_k1); a convex quad meets the origin's side of the chord
+    // only if one of its corners does)
+    using RK = Rec<KMAX>;
+    const float L = bnd[Bnd<KMAX>::CL1];
     float rho_arc = 0.f;
+    bool chord_ok = !(L > 0.f);
     for (int k = 0; k < K; k++) {
         const float tk = (k == 0) ? 0.f : rec[R_TH + k - 1];
         const float tk1 = (k + 1 == K) ? kTwoPi : rec[R_TH + k];
         const bool ov = (tk <= hi && lo <= tk1) || (tk + kTwoPi <= hi && lo <= tk1 + kTwoPi) ||
                         (tk - kTwoPi <= hi && lo <= tk1 - kTwoPi);
-        if (ov) rho_arc = fmaxf(rho_arc, bnd[B_RHO + k]);
+        if (ov) {
+            rho_arc = fmaxf(rho_arc, bnd[B_RHO + k]);
+            if (!chord_ok) {
+                const int k1 = (k + 1 == K) ? 0 : k + 1;
+                const float ex = rec[RK::EX + k], ey = rec[RK::EY + k];
+                const float nx = rec[RK::EY + k1] - ey, ny = ex - rec[RK::EX + k1];   // outward normal
+                const float lim = L * (nx * ex + ny * ey);
+                for (int c = 0; c < 4; c++)
+                    if (nx * qu[c] + ny * qv[c] <= lim) chord_ok = true;
+            }
+        }
     }
-    return dmin2 <= rho_arc * rho_arc * 1.002f;
+    return chord_ok && dmin2 <= rho_arc * rho_arc * 1.002f;
 }
 
 // K2a: count the pairs of each primitive (one warp per primitive).
