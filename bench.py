@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--cull-level", type=int, default=2, choices=(0, 1, 2, 3),
                     help="tile culling: 0 none, 1 screen rectangle, 2 per-tile test (same image), "
                          "3 the paper's endpoint polygon (lossy)")
-    ap.add_argument("--kbuf-capacity", type=int, default=8, choices=(8, 16, 32),
+    ap.add_argument("--kbuf-capacity", type=int, default=16, choices=(8, 16, 32),
                     help="per-pixel depth-order buffer entries (any value gives the same image)")
     ap.add_argument("--serve", action="store_true",
                     help="serving mode: Poisson request mix through drk_serve (batched vs one at a time)")

@@ -138,9 +138,10 @@ typedef struct {
     float bg[3];          /* background colour */
     int32_t cull_level;   /* DRK_CULL_*; default DRK_CULL_TILE */
     int32_t kbuf_capacity;/* per-pixel depth-order heap slots in shared
-                             memory: 8 (default), 16 or 32 (any value gives
+                             memory: 8, 16 (default) or 32 (any value gives
                              the same image; deeper heaps continue in the
-                             overflow column) */
+                             overflow column); in DRK_ORDER_CACHE_SORT the
+                             cache length (the paper uses 8) */
     int32_t ovf_capacity; /* depth-order heap slots per pixel in global memory
                              beyond the kbuf_capacity slots in shared memory
                              (any value gives the same image): 0 = 2048

@@ -340,7 +340,7 @@ void drk_options_default(drk_options_t* opt) {
     opt->lowpass_sl = 0.70710678f;
     opt->near_plane = 0.2f;
     opt->cull_level = DRK_CULL_TILE;
-    opt->kbuf_capacity = 8;
+    opt->kbuf_capacity = 16;
 }
 
 const char* drk_last_error(void) { return last_error_message(); }

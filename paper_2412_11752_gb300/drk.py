@@ -160,7 +160,7 @@ class Options:
     near_plane: float = 0.2
     bg: tuple = (0.0, 0.0, 0.0)
     cull_level: int = CULL_TILE
-    kbuf_capacity: int = 8
+    kbuf_capacity: int = 16
     ovf_capacity: int = 0
     order_mode: int = 0          # 0 exact order; 1 the paper's cache-sorting (forward only)
 
