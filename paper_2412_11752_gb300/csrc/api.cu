@@ -605,6 +605,11 @@ drk_status_t drk_render_backward(drk_ctx_t* ctx, const drk_params_t* params, con
     counting_sort_keys(state->rec_key, (uint32_t)nrec, n_keys, skey, sslot, sort_scr, st);
     tm.end(ST_REC_SORT, ev, st);
     ev = tm.begin(st);
+    float4* pixg = nullptr;
+    const size_t npix = (size_t)cam->width * cam->height;
+    if ((s = al.get(&pixg, 2 * npix)) != DRK_OK) return s;
+    launch_pack_pixel_grad(R.dL, R.Cfin, npix, pixg, st);
+    R.pixg = pixg;
     launch_raster_backward_records(R, skey, sslot, (uint32_t)nrec, F.kmax, st);
     tm.end(ST_RASTER_BWD, ev, st);
     ev = tm.begin(st);

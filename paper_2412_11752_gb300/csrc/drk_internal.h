@@ -104,6 +104,7 @@ struct RasterArgs {
     drk_params_t p;
     const float* dL;
     const float* Cfin;
+    const float4* pixg;    // per pixel {dL0, dL1, dL2, Cf0}, {Cf1, Cf2, -, -} (backward records)
     float* gtmp;                     // n x G_STRIDE
     drk_params_grad_t grads;
 };
@@ -147,6 +148,7 @@ void launch_raster(const RasterArgs& A, int kmax, int cap, bool bwd, cudaStream_
 int raster_slots(int kmax, int cap, bool bwd, bool batch, int n_tiles);
 size_t raster_ovf_bytes(int slots);
 // backward over n records sorted by key (skey, with their slots sslot)
+void launch_pack_pixel_grad(const float* dL, const float* Cfin, size_t npix, float4* out, cudaStream_t st);
 void launch_raster_backward_records(const RasterArgs& A, const uint32_t* skey, const uint32_t* sslot, uint32_t n,
                                     int kmax, cudaStream_t st);
 // v[i] = i for i < n

@@ -835,11 +835,11 @@ __global__ void __launch_bounds__(256) raster_backward_records_kernel(RasterArgs
             const float P[3] = {tp.y, tp.z, tp.w};
             const float wgt = __fmul_rn(a, T);
             const float inv1ma = 1.f / (1.f - a);
-            float G = 0.f, dL[3];
-            for (int c = 0; c < 3; c++) {
-                dL[c] = A.dL[c * npix + pix];
-                G += dL[c] * (T * col[c] - (A.Cfin[c * npix + pix] - P[c]) * inv1ma);
-            }
+            // the pixel's dL and final colour: one 32-byte sector
+            const float4 q0 = A.pixg[2 * (size_t)pix], q1 = A.pixg[2 * (size_t)pix + 1];
+            const float dL[3] = {q0.x, q0.y, q0.z}, Cf[3] = {q0.w, q1.x, q1.y};
+            float G = 0.f;
+            for (int c = 0; c < 3; c++) G += dL[c] * (T * col[c] - (Cf[c] - P[c]) * inv1ma);
             grad_from_info<KMAX>(A, r, idx, pr, e, G, pg);
             for (int c = 0; c < 3; c++) pg.v[A_RGB + c] = dL[c] * wgt;
         }
@@ -982,6 +982,20 @@ void launch_raster_batch(const RasterArgs& A, int kmax, int cap, cudaStream_t st
     DRK_RASTER_CASE(16, 16)
     DRK_RASTER_CASE(16, 32)
 #undef DRK_RASTER_CASE
+}
+
+__global__ void pack_pixel_grad_kernel(const float* __restrict__ dL, const float* __restrict__ Cfin, size_t npix,
+                                       float4* __restrict__ out) {
+    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npix) return;
+    out[2 * p] = make_float4(dL[p], dL[npix + p], dL[2 * npix + p], Cfin[p]);
+    out[2 * p + 1] = make_float4(Cfin[npix + p], Cfin[2 * npix + p], 0.f, 0.f);
+}
+
+void launch_pack_pixel_grad(const float* dL, const float* Cfin, size_t npix, float4* out, cudaStream_t st) {
+    if (npix == 0) return;
+    pack_pixel_grad_kernel<<<(unsigned)((npix + 255) / 256), 256, 0, st>>>(dL, Cfin, npix, out);
+    note_launch();
 }
 
 void launch_raster_backward_records(const RasterArgs& A, const uint32_t* skey, const uint32_t* sslot, uint32_t n,

@@ -299,22 +299,30 @@ void launch_batch_order_keys(const uint2* ranges, int n_tiles, int slot, uint32_
 // Counting sort of n dense keys (< n_keys; other keys are dropped): count,
 // exclusive scan, scatter.  Entries of one key end up contiguous in an
 // unspecified order; out_keys/out_idx beyond the kept entries hold kNoSlot.
+// Both passes aggregate over the warp: lanes holding equal keys (neighbouring
+// records usually share one) take a single atomic for the group.
 __global__ void key_count_kernel(const uint32_t* __restrict__ keys, uint32_t n, uint32_t n_keys,
                                  uint32_t* __restrict__ count) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const uint32_t k = keys[i];
-    if (k < n_keys) atomicAdd(count + k, 1u);
+    const uint32_t k = i < n ? keys[i] : 0xffffffffu;
+    const unsigned peers = __match_any_sync(0xffffffffu, k);
+    const int lane = threadIdx.x & 31;
+    if (k < n_keys && lane == __ffs(peers) - 1) atomicAdd(count + k, (uint32_t)__popc(peers));
 }
 
 __global__ void key_scatter_kernel(const uint32_t* __restrict__ keys, uint32_t n, uint32_t n_keys,
                                    unsigned long long* __restrict__ cursor, uint32_t* __restrict__ out_keys,
                                    uint32_t* __restrict__ out_idx) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const uint32_t k = keys[i];
-    if (k >= n_keys) return;
-    const unsigned long long pos = atomicAdd(cursor + k, 1ull);
+    const uint32_t k = i < n ? keys[i] : 0xffffffffu;
+    const bool valid = k < n_keys;
+    const unsigned peers = __match_any_sync(0xffffffffu, k);
+    const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+    unsigned long long base = 0ull;
+    if (valid && lane == leader) base = atomicAdd(cursor + k, (unsigned long long)__popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (!valid) return;
+    const unsigned long long pos = base + (unsigned long long)__popc(peers & ((1u << lane) - 1u));
     out_keys[pos] = k;
     out_idx[pos] = i;
 }
