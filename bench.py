@@ -8,6 +8,7 @@ forward + backward render (Sec. 4.4 pipeline and its reverse mode) of a
     python bench.py --order-study     (forward only: exact vs cache-sorting order)
     python bench.py --train           (training step with the fused Adam update)
     python bench.py --mesh            (mesh to DRK conversion and render)
+    python bench.py --serve-sweep     (serving: max arrival rate within the latency target)
 
 One process per GPU (torchrun for N > 1).  The path does not shard: every
 rank renders its own replica of the workload ("replicas only"), value =
@@ -63,6 +64,8 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=160)
     ap.add_argument("--serve-rate", type=float, default=0.0, help="arrivals per second (0 = all at once)")
     ap.add_argument("--serve-batch", type=int, default=16)
+    ap.add_argument("--serve-sweep", action="store_true",
+                    help="serving headline: max arrival rate with p99 <= L* for batched and one-at-a-time serving")
     ap.add_argument("--train", action="store_true",
                     help="training step: render + L1 gradient + backward + fused Adam (activations included)")
     ap.add_argument("--mesh", action="store_true",
@@ -629,8 +632,48 @@ def run_serve(args):
     return 0
 
 
+def serve_sweep(args):
+    """Serving headline: L* = p99 latency of one-at-a-time serving at half of
+    its saturation rate; for each mode, the largest Poisson arrival rate of
+    a grid whose p99 stays within L*.  One JSON line."""
+    import torch
+    from paper_2412_11752_gb300 import drk as D
+    D.lib()
+    scenes = synth.serve_scenes()
+    dscenes = [D.DeviceScene.from_scene(s, "cuda") for s in scenes]
+    budget = 64 << 30
+    nreq = args.serve_requests
+    modes = {"batched": args.serve_batch, "one_at_a_time": 1}
+    sat = {m: serve_run(D, torch, dscenes, synth.serve_requests(nreq, len(scenes), 0.0), b, budget)
+           for m, b in modes.items()}
+    x1 = sat["one_at_a_time"]["frames_per_s"]
+    ref = serve_run(D, torch, dscenes, synth.serve_requests(nreq, len(scenes), 0.5 * x1), 1, budget)
+    L = ref["p99_ms"]
+    grid = [round(f * x1, 2) for f in (0.4, 0.45, 0.5, 0.55, 0.6, 0.7, 0.8, 0.9, 1.0)]
+    runs, best = {m: [] for m in modes}, {}
+    for m, b in modes.items():
+        best[m] = None
+        for lam in grid:
+            r = serve_run(D, torch, dscenes, synth.serve_requests(nreq, len(scenes), lam), b, budget)
+            runs[m].append({"rate_hz": lam, "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"],
+                            "frames_per_s": r["frames_per_s"], "mean_batch": r["mean_batch"]})
+            if r["p99_ms"] <= L:
+                best[m] = lam
+    print(json.dumps({"metric": "max Poisson arrival rate with p99 latency <= L*", "unit": "requests/s",
+                      "impl": "drk-serve", "data": "synthetic", "requests_per_run": nreq,
+                      "saturation_frames_per_s": {m: v["frames_per_s"] for m, v in sat.items()},
+                      "L_star_ms": L, "L_star_rule": "p99 of one-at-a-time at half its saturation rate",
+                      "max_rate": best, "runs": runs,
+                      "config": {"scenes": [s.n for s in scenes], "resolutions": list(synth.SERVE_RESOLUTIONS),
+                                 "weights": list(synth.SERVE_RES_WEIGHTS), "mem_budget": budget,
+                                 "max_batch": args.serve_batch}}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.serve_sweep:
+        return serve_sweep(args)
     if args.serve:
         return run_serve(args)
     if args.order_study:
