@@ -100,3 +100,12 @@ def test_autograd_function_l1_loss(drk):
         assert params[k].grad is not None
         scale = float(g[k].abs().max())
         assert torch.allclose(params[k].grad, g[k], rtol=1e-3, atol=1e-5 * scale), k
+
+
+def test_backward_paper_culling(drk):
+    # the paper's lossy tile culling (Eq. 11 - Eq. 12 as printed): the
+    # gradient of the image it renders, against the oracle applying the
+    # same culling
+    scene = synth.scene_plain(400, 8, seed=44)
+    cam = synth.camera_front(48, 40)
+    compare_grads(drk, scene, cam, drk.Options(cull_level=drk.CULL_PAPER), seed=45)
