@@ -632,6 +632,34 @@ def run_serve(args):
     return 0
 
 
+def serve_sequential(D, torch, dscenes, reqs) -> dict:
+    """One request at a time without a server: each request, in arrival
+    order, is rendered with drk_render once it has arrived and the host waits
+    for it before taking the next; latency = completion - arrival."""
+    ctx = D.Context(0)
+    outs = [dict(rgb=torch.empty((3, c.height, c.width), device="cuda"), T=None, n=None) for _, _, c in reqs]
+    for _, sid, cam in reqs[:4]:                       # warm-up, as for the server
+        D.drk_render(dscenes[sid], cam, ctx=ctx, out=dict(rgb=torch.empty((3, cam.height, cam.width), device="cuda"),
+                                                          T=None, n=None))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lat, ends = [], []
+    for (arr, sid, cam), o in zip(reqs, outs):
+        dt = arr - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        D.drk_render(dscenes[sid], cam, ctx=ctx, out=o)
+        torch.cuda.synchronize()
+        now = time.perf_counter() - t0
+        lat.append((now - arr) * 1e3)
+        ends.append(now)
+    span = max(ends) - min(a for a, _, _ in reqs)
+    px = sum(c.width * c.height for _, _, c in reqs)
+    return {"max_batch": 1, "frames_per_s": len(reqs) / span, "Mpix_per_s": px / span / 1e6,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)), "mean_batch": 1.0,
+            "failed": 0}
+
+
 def serve_sweep(args):
     """Serving headline: L* = p99 latency of one-at-a-time serving at half of
     its saturation rate; for each mode, the largest Poisson arrival rate of
@@ -643,18 +671,26 @@ def serve_sweep(args):
     dscenes = [D.DeviceScene.from_scene(s, "cuda") for s in scenes]
     budget = 64 << 30
     nreq = args.serve_requests
-    modes = {"batched": args.serve_batch, "one_at_a_time": 1}
-    sat = {m: serve_run(D, torch, dscenes, synth.serve_requests(nreq, len(scenes), 0.0), b, budget)
-           for m, b in modes.items()}
-    x1 = sat["one_at_a_time"]["frames_per_s"]
-    ref = serve_run(D, torch, dscenes, synth.serve_requests(nreq, len(scenes), 0.5 * x1), 1, budget)
-    L = ref["p99_ms"]
-    grid = [round(f * x1, 2) for f in (0.4, 0.45, 0.5, 0.55, 0.6, 0.7, 0.8, 0.9, 1.0)]
+    # "sequential": drk_render one request at a time (no server);
+    # "server_batch1": the server with batches of one (consecutive requests
+    # still overlap on its two streams); "batched": batches of up to max_batch
+    modes = {"batched": args.serve_batch, "server_batch1": 1, "sequential": 0}
+
+    def run(m, lam):
+        reqs = synth.serve_requests(nreq, len(scenes), lam)
+        if modes[m] == 0:
+            return serve_sequential(D, torch, dscenes, reqs)
+        return serve_run(D, torch, dscenes, reqs, modes[m], budget)
+
+    sat = {m: run(m, 0.0) for m in modes}
+    x1 = sat["sequential"]["frames_per_s"]
+    L = run("sequential", 0.5 * x1)["p99_ms"]
+    grid = [round(f * x1, 2) for f in (0.4, 0.5, 0.6, 0.8, 1.0, 1.2)]
     runs, best = {m: [] for m in modes}, {}
-    for m, b in modes.items():
+    for m in modes:
         best[m] = None
         for lam in grid:
-            r = serve_run(D, torch, dscenes, synth.serve_requests(nreq, len(scenes), lam), b, budget)
+            r = run(m, lam)
             runs[m].append({"rate_hz": lam, "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"],
                             "frames_per_s": r["frames_per_s"], "mean_batch": r["mean_batch"]})
             if r["p99_ms"] <= L:
@@ -662,7 +698,7 @@ def serve_sweep(args):
     print(json.dumps({"metric": "max Poisson arrival rate with p99 latency <= L*", "unit": "requests/s",
                       "impl": "drk-serve", "data": "synthetic", "requests_per_run": nreq,
                       "saturation_frames_per_s": {m: v["frames_per_s"] for m, v in sat.items()},
-                      "L_star_ms": L, "L_star_rule": "p99 of one-at-a-time at half its saturation rate",
+                      "L_star_ms": L, "L_star_rule": "p99 of sequential rendering at half its saturation rate",
                       "max_rate": best, "runs": runs,
                       "config": {"scenes": [s.n for s in scenes], "resolutions": list(synth.SERVE_RESOLUTIONS),
                                  "weights": list(synth.SERVE_RES_WEIGHTS), "mem_budget": budget,

@@ -699,8 +699,11 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
 // stage with cp.async one chunk ahead of use; the kernel stage runs only
 // when some lane of the warp passes the geometry stage.  Tasks are taken
 // heaviest tile first (longest list), which keeps the tail short.
+// The batch variant keeps a frame slot per task and needs a few registers
+// more; with a register budget for four CTAs per SM (the shared memory of 16
+// heap slots allows no more) it does not spill.
 template <int KMAX, int CAP, bool BWD, bool BATCH, bool AUX = false>
-__global__ void __launch_bounds__(kRasterThreads, 5) raster_kernel(RasterArgs A) {
+__global__ void __launch_bounds__(kRasterThreads, BATCH ? 4 : 5) raster_kernel(RasterArgs A) {
     constexpr int kWarps = kRasterThreads / 32;
     constexpr int HDR4 = Rec<KMAX>::HDR / 4;
     extern __shared__ float4 smem4[];
