@@ -291,9 +291,12 @@ drk_status_t launch(PrimArgs& A, cudaStream_t st) {
     A.prim_blocks = (r.n + kTrainThreads - 1) / kTrainThreads;
     int64_t elem_blocks = 0;
     if (MODE != ACTIVATE) {
-        // grid-stride over the flat arrays; a few waves of the SMs at most
+        // grid-stride over the flat arrays; eight blocks per SM at most
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         elem_blocks = std::min<int64_t>((A.n_elem_mu + A.n_elem_col + kTrainThreads - 1) / kTrainThreads,
-                                        (int64_t)152 * 8);
+                                        (int64_t)std::max(sms, 1) * 8);
     }
     const int64_t blocks = A.prim_blocks + elem_blocks;
     if (blocks == 0) return DRK_OK;
