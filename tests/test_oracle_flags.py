@@ -1,0 +1,37 @@
+"""Pins of the oracle's float32-undecidability flags: two coplanar
+contributors have exactly equal r_t, so float32 may composite them in
+either order; the pixel is flagged when exchanging them changes the
+colour visibly, in the exact order and in the cache-sorting order, and not
+when their colours are equal."""
+import numpy as np
+
+from oracle import drk_oracle as O
+from paper_2412_11752_gb300 import synth
+
+
+def _two_coplanar(c0, c1):
+    f = lambda a: np.asarray(a, np.float64)
+    K = 4
+    return synth.Scene(mu=f([[0.5, 0.5, 0.5], [0.52, 0.49, 0.5]]), quat=f([[1.0, 0, 0, 0]] * 2),
+                       scale=f([[0.2] * K] * 2), theta=f([2 * np.pi * np.arange(K) / K] * 2), eta=f([0.0, 0.0]),
+                       tau=f([0.0, 0.0]), opacity=f([0.6, 0.6]), color=f([c0, c1]), sh_degree=-1)
+
+
+def test_equal_depths_with_different_colours_are_flagged():
+    cam = synth.camera_front(16, 16)
+    pix = np.array([[8, 8]], np.int32)
+    for mode in (0, 1):
+        opt = O.Options(lowpass_sl=0.0, order_mode=mode, cache_len=8)
+        idx, t, a, nc = O.contributors(_two_coplanar([1.0, 0.0, 0.0], [0.0, 0.0, 1.0]), cam, opt, 8, 8)
+        assert len(idx) == 2 and t[0] == t[1]                  # the same plane: r_t exactly equal
+        r = O.render_pixels(_two_coplanar([1.0, 0.0, 0.0], [0.0, 0.0, 1.0]), cam, opt, pix)
+        assert r["flags"][0] & O.FLAG_DEPTH_TIE, mode
+        same = O.render_pixels(_two_coplanar([0.3, 0.3, 0.3], [0.3, 0.3, 0.3]), cam, opt, pix)
+        assert not same["flags"][0] & O.FLAG_DEPTH_TIE, mode
+
+
+def test_excluded_covers_every_undecidable_flag():
+    from helpers import excluded
+    for f in (O.FLAG_T_MIN, O.FLAG_DEPTH_TIE, O.FLAG_STEEP, O.FLAG_CULL):
+        assert excluded(np.array([f]))[0]
+    assert not excluded(np.array([O.FLAG_ALPHA_MIN]))[0]      # informational only
