@@ -136,7 +136,8 @@ def test_training_argument_errors(drk):
 
 def test_fit_shape_target(drk):
     # a few hundred DRKs fitted to a synthetic image of convex shapes: the L1
-    # loss falls steadily through render -> backward -> fused Adam
+    # loss falls to a quarter of its start through render -> backward ->
+    # fused Adam
     H = W = 64
     cam = synth.camera_front(W, H)
     target = torch.from_numpy(synth.shape_target(H, W)).cuda()
@@ -156,7 +157,8 @@ def test_fit_shape_target(drk):
     torch.cuda.synchronize()
     assert all(np.isfinite(losses))
     first, last = np.mean(losses[:5]), np.mean(losses[-5:])
-    assert last < 0.6 * first, (first, last)
+    print(f"L1 loss {first:.4f} -> {last:.4f} (ratio {last / first:.3f})")
+    assert last < 0.25 * first, (first, last)          # measured: 0.142 -> 0.012
     th = opt.scene.theta.cpu().numpy()
     gaps = np.diff(np.concatenate([th, th[:, :1] + 2 * np.pi], axis=1), axis=1)
     assert gaps.max() < np.pi and gaps.min() > 0
