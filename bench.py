@@ -47,8 +47,8 @@ OPS_PER_EMIT_BWD = 190
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=("drk", "reference"), default="drk")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
@@ -296,7 +296,10 @@ def run_drk(args):
     ctx.timing_enable(False)
     stats = ctx.stats()
     ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    value, ms_step = replica_rate(H * W / 1e6, float(np.mean(ms)), world, dev)
+    # median step (robust to the odd slow step); spread reported beside it
+    value, ms_step = replica_rate(H * W / 1e6, float(np.median(ms)), world, dev)
+    spread = {"min": float(np.min(ms)), "p10": float(np.percentile(ms, 10)), "median": float(np.median(ms)),
+              "p90": float(np.percentile(ms, 90)), "max": float(np.max(ms)), "mean": float(np.mean(ms))}
 
     # ---- roofline of the dominant kernel (FP32 ALU bound)
     peaks = measured_peaks()
@@ -361,7 +364,7 @@ def run_drk(args):
                            "l2": "flushed between timed steps (256 MiB write)",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clocks,
+                "clocks": clocks, "step_ms_spread": spread, "statistic": "median step time",
                 "stages_ms": {k: v[0] / max(1, v[1]) for k, v in stage.items() if v[1]},
                 "counters": {k: stats[k] for k in ("n_pairs", "n_evals", "n_geo_evals", "n_contrib_evals", "n_emitted",
                                                    "n_spills", "n_replay_evals",

@@ -148,7 +148,13 @@ typedef struct {
                              (default), 1..2048, or -1 = none (a full heap
                              then takes extra passes over the list) */
     int32_t order_mode;   /* DRK_ORDER_*; default DRK_ORDER_EXACT */
-    int32_t reserved[4];  /* must be zero */
+    int32_t record_chunks;/* upper bound on the contributor records a forward
+                             with a backward state keeps, in chunks of 1024
+                             records (24 B each); 0 = automatic (sized from
+                             the previous recording forward).  Tiles whose
+                             records do not fit are replayed exactly by the
+                             backward instead (same gradients, slower) */
+    int32_t reserved[3];  /* must be zero */
 } drk_options_t;
 
 /* Fills *opt with the defaults listed above. */
@@ -233,23 +239,27 @@ void drk_state_free(drk_state_t *state);
 drk_status_t drk_sort_pairs(drk_ctx_t *ctx, uint32_t *keys, uint32_t *vals, int64_t n, int key_bits, void *stream);
 
 /* drk_sort_pairs without any device allocation, for callers that cannot
- * allocate when they sort: a stream being captured into a graph that must
- * hold no allocation nodes, a host callback, or an embedder whose device
- * memory is fixed at start-up.  The paper has no counterpart; this is a
- * service of the library.
- *   keys, vals  device arrays of n uint32 (sorted in place, stable, by the
- *               low key_bits bits of the keys, 1..32)
+ * allocate when they sort: an embedder whose device memory is handed out
+ * once at start-up and never grows, a real-time loop that must not meet the
+ * implicit synchronisation or latency of an allocation, or code inside a
+ * custom allocator's own bookkeeping, which must not re-enter it.  The
+ * paper has no counterpart; this is a service of the library.
+ *   keys, vals  device arrays of n uint32 on the CURRENT device (sorted in
+ *               place, stable, by the low key_bits bits of the keys, 1..32);
+ *               host pointers or arrays of another device are refused with
+ *               DRK_ERR_INVALID_ARG before anything is launched
  *   n           0 .. 1048576 (2^20); larger n returns DRK_ERR_CAPACITY
- *               before anything is launched
+ *               before anything is launched; n <= 1 returns at once
  * Working memory is one fixed device array inside the library (9 MiB per
  * GPU that loads it, held until the process exits); the call allocates and
  * frees nothing.  The first call on a device looks the array's address up
- * with that device current, so make that first call before any stream
- * capture.  All calls share the array and it keeps the contents of the last
- * call: calls whose work could overlap on the GPU (different streams, or
- * different host threads) race on it and must be ordered by the caller.
- * Asynchronous on `stream`; returns DRK_ERR_INVALID_ARG for bad arguments,
- * DRK_ERR_CUDA if a launch fails. */
+ * with that device current and keeps it; a device reset (which unloads the
+ * library's device image) invalidates it, so do not call this entry point
+ * after resetting a device it was used on.  All calls share the array and
+ * it keeps the contents of the last call: calls whose work could overlap on
+ * the GPU (different streams, or different host threads) race on it and
+ * must be ordered by the caller.  Asynchronous on `stream`; DRK_ERR_CUDA if
+ * a launch fails (message in drk_last_error). */
 drk_status_t drk_sort_pairs_static(uint32_t *keys, uint32_t *vals, int64_t n, int key_bits, void *stream);
 
 /* Synchronises the stream of the last render and copies its counters. */

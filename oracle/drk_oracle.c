@@ -455,34 +455,127 @@ void ord_color(const ord_params *P, int64_t i, const ord_camera *cam, double *rg
 /* ------------------------------------------------------------------------ */
 /* Per-pixel contributor list, sorted by (r_t, index) -- Eq. 13, reading R6 */
 
-typedef struct { double t; int64_t idx; double alpha, dalpha; } contrib;
+typedef struct {
+    double t;
+    int64_t idx;
+    double alpha, dalpha;   /* alpha_tilde and its float32 error model */
+    int cull_und;           /* the paper's culling decision is within float32 margin */
+} contrib;
 
 /* Rounding-error model of a float32 evaluation of alpha_tilde.  It decides
- * nothing in the rendered image; it only marks pixels whose result float32
- * arithmetic cannot pin down to the parity tolerance.  The exponent E of
- * Eq. 8 (or the filter exponent of Eq. 10) carries an absolute error of at
- * most about 4e-6 (1 + E) in float32 (relative 2e-6 from the projected
- * coordinates, plus the rounding of the exponent itself); it moves alpha by
- * o Psi'(g) g dE / 2.  Near grazing incidence the ray-plane intersection
- * of Eq. 4 is ill-conditioned: one float32 rounding (about 1.2e-7) of the
- * ray direction moves the intersection by t |d| 1.2e-7 / cos, with cos the
- * cosine between the ray and the plane normal, which adds about
- * 2 E (t |d| / r2) 1.2e-7 / cos to E.  A clamped alpha has no error.       */
-static double alpha_fp32_error(const pair_eval *pe, double tau, double o)
+ * nothing in the rendered image; it only bounds how far a float32
+ * evaluation of the pair may land from this one, to set the parity budget
+ * of a pixel.  First-order error propagation, where the sensitivities are
+ * taken from the kernel itself by re-evaluating it (FP64) at perturbed
+ * inputs:
+ *   - the plane coordinates (u, v) of Eq. 5 carry a relative error d_r of
+ *     about 2e-6 (a float32 product and sum of quantities of the size of
+ *     the camera distance that cancel down to r_2), plus, near grazing
+ *     incidence, t |d| 1.2e-7 / (cos r_2): one float32 rounding of the ray
+ *     direction moves the ray-plane intersection of Eq. 4 by t |d| 1.2e-7 /
+ *     cos, cos being the cosine between the ray and the plane normal;
+ *     (u, v) is moved by d_r radially and turned by d_r + 5e-7 rad (the
+ *     polar angle adds the rounding of atan2 and of theta_k - theta_0, a
+ *     few half-ulps of 2 pi);
+ *   - the sector endpoints theta_k, theta_k+1 carry 5e-7 rad and the
+ *     scales s_k, s_k+1 a relative 3e-7 (their float32 trigonometry and
+ *     products); narrow sectors amplify both through pi / gap (Eq. 6) and
+ *     the inverse endpoint matrix (Eq. 7), which is why they are measured
+ *     on the kernel and not estimated;
+ *   - the exponent E of Eq. 8 itself carries 4e-6 (1 + E) from its own
+ *     rounding, the cosine and the exponential: o Psi'(g) g dE / 2;
+ *   - the affine pieces of Eq. 9 and the product with o round a few times
+ *     more: 3e-7 alpha (this dominates on the flat pieces of Psi).
+ * The perturbed kernels are re-evaluated in the sector each point falls
+ * in; Eq. 6 - Eq. 7 are continuous across sectors.  For the filter of
+ * Eq. 10 the exponent carries 4e-6 (1 + 2 X_f) / 2 plus the grazing term.
+ * A clamped alpha has no error.                                            */
+static double alpha_fp32_error(const ord_params *P, int64_t i, const pair_eval *pe)
 {
     if (pe->clamped) return 0.0;
+    const double tau = P->tau[i], o = P->opacity[i];
     double dnorm = sqrt(dot3(pe->d, pe->d));
     double cosv = fabs(pe->dn) / dnorm;
     if (pe->use_filter) {
         double Xf = -log(pe->filt / o);
         return pe->filt * (0.5 * 4e-6 * (1.0 + 2.0 * Xf) + Xf * 2.4e-7 / cosv);
     }
+    const int K = P->K;
+    const double *s0 = P->scale + (int64_t)K * i, *th0 = P->theta + (int64_t)K * i;
+    const double eta = P->eta[i];
+    const double a0 = pe->ke.alpha;
     double dpsi, dtau;
     psi_grad(pe->ke.g, tau, &dpsi, &dtau);
+    double err = o * dpsi * pe->ke.g * 0.5 * 4e-6 * (1.0 + pe->ke.E) + 3e-7 * a0;
     double r2 = sqrt(pe->ke.r2sq);
-    double dE = 4e-6 * (1.0 + pe->ke.E);
-    if (r2 > 0.0) dE += 2.0 * pe->ke.E * (pe->t * dnorm / r2) * 1.2e-7 / cosv;
-    return o * dpsi * pe->ke.g * 0.5 * dE;
+    if (r2 <= 0.0) return err;
+    const double d_r = 2e-6 + (pe->t * dnorm / r2) * 1.2e-7 / cosv;
+    const double d_phi = d_r + 5e-7;
+    double s[ORD_MAXK], th[ORD_MAXK];
+    memcpy(s, s0, sizeof(double) * (size_t)K);
+    memcpy(th, th0, sizeof(double) * (size_t)K);
+    kernel_eval ke;
+    double worst;
+    /* radial */
+    worst = 0.0;
+    for (int sg = -1; sg <= 1; sg += 2) {
+        const double f = 1.0 + sg * d_r;
+        kernel_uv(K, s, th, eta, tau, o, pe->u * f, pe->v * f, &ke);
+        worst = fmax(worst, fabs(ke.alpha - a0));
+    }
+    err += worst;
+    /* angular */
+    worst = 0.0;
+    for (int sg = -1; sg <= 1; sg += 2) {
+        const double c = cos(sg * d_phi), sn = sin(sg * d_phi);
+        kernel_uv(K, s, th, eta, tau, o, c * pe->u - sn * pe->v, sn * pe->u + c * pe->v, &ke);
+        worst = fmax(worst, fabs(ke.alpha - a0));
+    }
+    err += worst;
+    /* sector endpoints and scales of the pair's sector (each one alone;
+     * angles stay ascending because every gap is far above 5e-7) */
+    const int ks[2] = {pe->ke.k, pe->ke.k1};
+    for (int e = 0; e < 2; e++) {
+        const int k = ks[e];
+        worst = 0.0;
+        for (int sg = -1; sg <= 1; sg += 2) {
+            th[k] = th0[k] + sg * 5e-7;
+            kernel_uv(K, s, th, eta, tau, o, pe->u, pe->v, &ke);
+            worst = fmax(worst, fabs(ke.alpha - a0));
+        }
+        th[k] = th0[k];
+        err += worst;
+        worst = 0.0;
+        for (int sg = -1; sg <= 1; sg += 2) {
+            s[k] = s0[k] * (1.0 + sg * 3e-7);
+            kernel_uv(K, s, th, eta, tau, o, pe->u, pe->v, &ke);
+            worst = fmax(worst, fabs(ke.alpha - a0));
+        }
+        s[k] = s0[k];
+        err += worst;
+    }
+    return err;
+}
+
+/* A batch of (pixel, primitive) pairs: alpha_tilde (0 where the ray misses
+ * the plane in front of the near plane), r_t, and the float32 error model
+ * of alpha_tilde (alpha_fp32_error) -- so that tests can hold the model
+ * against float32 evaluations.  pix: m x 2 (x, y).                          */
+void ord_pairs(const ord_params *P, const ord_camera *cam, const ord_options *opt, int64_t m, const int64_t *idx,
+               const int32_t *pix, double *alpha_tilde, double *t, double *dalpha, int32_t *valid)
+{
+    double ocam[3];
+    cam_center(cam, ocam);
+#pragma omp parallel for schedule(static)
+    for (int64_t q = 0; q < m; q++) {
+        pair_eval pe;
+        const int64_t i = idx[q];
+        eval_pair(P, i, cam, opt, ocam, pix[2 * q], pix[2 * q + 1], &pe);
+        valid[q] = pe.valid;
+        alpha_tilde[q] = pe.valid ? pe.alpha_tilde : 0.0;
+        t[q] = pe.t;
+        dalpha[q] = pe.valid ? alpha_fp32_error(P, i, &pe) : 0.0;
+    }
 }
 
 static int contrib_cmp(const void *pa, const void *pb)
@@ -567,7 +660,7 @@ static double max_abs_diff3(const double *a, const double *b);
  * pops later, so its effect is not bounded by the two contributors alone.
  * Returns -1 on allocation failure.                                        */
 static int cache_sort_pixel(const ord_params *P, const ord_camera *cam, const ord_options *opt,
-                            const double *ocam, contrib *buf, int64_t cnt)
+                            const double *ocam, contrib *buf, int64_t cnt, double *tie_move)
 {
     const int cache_len = opt->cache_len > 0 ? opt->cache_len : 8;
     presort_key *keys = (presort_key *)malloc(sizeof(presort_key) * (size_t)cnt);
@@ -589,7 +682,7 @@ static int cache_sort_pixel(const ord_params *P, const ord_camera *cam, const or
     double base[3], alt[3];
     cache_sort_order(buf, cnt, cache_len, keys, NULL, cache, out);
     order_colour(P, ocam, opt, out, cnt, base);
-    for (int64_t j = 1; j < cnt && !tie; j++) {
+    for (int64_t j = 1; j < cnt; j++) {
         if (keys[j].zc - keys[j - 1].zc > 1e-6 * fabs(keys[j].zc)) continue;
         presort_key k = keys[j];
         keys[j] = keys[j - 1];
@@ -597,16 +690,18 @@ static int cache_sort_pixel(const ord_params *P, const ord_camera *cam, const or
         cache_sort_order(buf, cnt, cache_len, keys, NULL, cache, out);
         order_colour(P, ocam, opt, out, cnt, alt);
         if (max_abs_diff3(base, alt) > 5e-5) tie = 1;
+        *tie_move = fmax(*tie_move, max_abs_diff3(base, alt));
         keys[j - 1] = keys[j];
         keys[j] = k;
     }
-    for (int64_t j = 0; j < cnt && !tie; j++)
-        for (int64_t l = j + 1; l < cnt && buf[l].t - buf[j].t <= 2e-6 * buf[l].t && !tie; l++) {
+    for (int64_t j = 0; j < cnt; j++)
+        for (int64_t l = j + 1; l < cnt && buf[l].t - buf[j].t <= 2e-6 * buf[l].t; l++) {
             rank[j] = l;
             rank[l] = j;
             cache_sort_order(buf, cnt, cache_len, keys, rank, cache, out);
             order_colour(P, ocam, opt, out, cnt, alt);
             if (max_abs_diff3(base, alt) > 5e-5) tie = 1;
+            *tie_move = fmax(*tie_move, max_abs_diff3(base, alt));
             rank[j] = j;
             rank[l] = l;
         }
@@ -729,35 +824,58 @@ static int paper_tile_keep(const ord_params *P, int64_t i, const ord_camera *cam
     return keep;
 }
 
+/* Contributors of pixel (px, py), sorted by (r_t, index) (or in the
+ * cache-sorting order).  With the paper's culling, a contributor whose
+ * culling decision is within float32 margin is marked (cull_und) when it
+ * is kept, and copied to und (if not NULL) when it is culled.  In the
+ * cache-sorting order *tie_move (if not NULL) gets the largest colour move
+ * of a float32-undecidable exchange.                                      */
 static int64_t gather_contributors(const ord_params *P, const ord_camera *cam, const ord_options *opt,
-                                   const double *ocam, int px, int py, contrib *buf, int *near_amin)
+                                   const double *ocam, int px, int py, contrib *buf, int *near_amin,
+                                   contrib *und, int64_t *n_und, double *tie_move)
 {
     int64_t cnt = 0;
     *near_amin = 0;
+    if (n_und) *n_und = 0;
+    if (tie_move) *tie_move = 0.0;
     for (int64_t i = 0; i < P->n; i++) {
         pair_eval pe;
         eval_pair(P, i, cam, opt, ocam, px, py, &pe);
         if (!pe.valid) continue;
+        int undecided = 0;
         if (opt->cull_paper) {
-            int und;
-            const int keep = paper_tile_keep(P, i, cam, opt, ocam, px, py, &und);
-            if (und && pe.alpha_tilde >= opt->alpha_min) *near_amin |= 4;
-            if (!keep) continue;
+            const int keep = paper_tile_keep(P, i, cam, opt, ocam, px, py, &undecided);
+            undecided = undecided && pe.alpha_tilde >= opt->alpha_min;
+            if (undecided) *near_amin |= 4;
+            if (!keep) {
+                if (undecided && und) {
+                    und[*n_und].t = pe.t;
+                    und[*n_und].idx = i;
+                    und[*n_und].alpha = pe.alpha_tilde;
+                    und[*n_und].dalpha = 0.0;
+                    und[*n_und].cull_und = 1;
+                    (*n_und)++;
+                }
+                continue;
+            }
         }
         if (fabs(pe.alpha_tilde / opt->alpha_min - 1.0) < 1e-4) *near_amin |= 1;
         if (pe.alpha_tilde >= opt->alpha_min) {
             buf[cnt].t = pe.t;
             buf[cnt].idx = i;
             buf[cnt].alpha = pe.alpha_tilde;
-            buf[cnt].dalpha = alpha_fp32_error(&pe, P->tau[i], P->opacity[i]);
+            buf[cnt].dalpha = alpha_fp32_error(P, i, &pe);
+            buf[cnt].cull_und = undecided;
             cnt++;
         }
     }
     qsort(buf, (size_t)cnt, sizeof(contrib), contrib_cmp);
     if (opt->order_mode == 1 && cnt > 0) {
-        int r = cache_sort_pixel(P, cam, opt, ocam, buf, cnt);
+        double move = 0.0;
+        int r = cache_sort_pixel(P, cam, opt, ocam, buf, cnt, &move);
         if (r < 0) return -1;
         if (r) *near_amin |= 2;
+        if (tie_move) *tie_move = move;
     }
     return cnt;
 }
@@ -786,26 +904,46 @@ static double max_abs_diff3(const double *a, const double *b)
 
 /* Render the listed pixels.  pix: npix x 2 (x, y).  Outputs per pixel:
  * rgb (npix x 3, includes T_final * bg), T_final, number of composited
- * contributors, parity flags.  Returns 0, or -1 on allocation failure.    */
+ * contributors, parity flags, and tol (may be NULL): how far a float32
+ * evaluation of the same pixel may legitimately land from this result
+ * (colour units, any channel), the sum of
+ *   - the alpha error model of every composited contributor and of the
+ *     first one not composited, carried through Eq. 1: T_j dalpha_j 2 c_max;
+ *   - for every stop decision within its float32 margin, the exact colour
+ *     change if that decision went the other way (stop before j: the
+ *     contributions of j .. last are replaced by the background; go on past
+ *     the stop: one more contributor is composited);
+ *   - for every pair of contributors with depths within 2e-6 (relative),
+ *     the exact change of exchanging them when adjacent, T a_j a_l |c_j - c_l|;
+ *   - in the cache-sorting order, the largest colour move of an exchange of
+ *     a float32-undecidable pair (re-running the cache);
+ *   - with the paper's culling, for a contributor whose culling decision
+ *     is within float32 margin, T a 2 c_max (T at its depth).
+ * Returns 0, or -1 on allocation failure.                                  */
 int ord_render(const ord_params *P, const ord_camera *cam, const ord_options *opt, int64_t npix,
-               const int32_t *pix, double *rgb, double *T_final, int32_t *n_contrib, int32_t *flags)
+               const int32_t *pix, double *rgb, double *T_final, int32_t *n_contrib, int32_t *flags, double *tol)
 {
     double ocam[3];
     cam_center(cam, ocam);
     int fail = 0;
+    const size_t nb = (size_t)(P->n > 0 ? P->n : 1);
 #pragma omp parallel
     {
-        contrib *buf = (contrib *)malloc(sizeof(contrib) * (size_t)(P->n > 0 ? P->n : 1));
-        if (!buf) {
+        contrib *buf = (contrib *)malloc(sizeof(contrib) * nb);
+        contrib *und = opt->cull_paper ? (contrib *)malloc(sizeof(contrib) * nb) : NULL;
+        double *w = (double *)malloc(sizeof(double) * 4 * (nb + 1));   /* T_j a_j (c_j - bg), then T_j */
+        if (!buf || !w || (opt->cull_paper && !und)) {
 #pragma omp atomic write
             fail = 1;
         }
 #pragma omp for schedule(dynamic, 4)
         for (int64_t q = 0; q < npix; q++) {
-            if (!buf) continue;
+            if (!buf || !w || (opt->cull_paper && !und)) continue;
             int px = pix[2 * q], py = pix[2 * q + 1];
             int near_amin;
-            int64_t cnt = gather_contributors(P, cam, opt, ocam, px, py, buf, &near_amin);
+            int64_t n_und = 0;
+            double tie_move = 0.0;
+            int64_t cnt = gather_contributors(P, cam, opt, ocam, px, py, buf, &near_amin, und, &n_und, &tie_move);
             if (cnt < 0) {
 #pragma omp atomic write
                 fail = 1;
@@ -820,38 +958,71 @@ int ord_render(const ord_params *P, const ord_camera *cam, const ord_options *op
             for (int c = 0; c < 3; c++) cmax = fmax(cmax, fabs(opt->bg[c]));
             double dT_rel = 0.0;     /* float32 error estimate of T (relative) */
             double budget = 0.0;     /* float32 error estimate of the colour */
+            double extra = tie_move; /* undecided stops, ties and culling decisions */
             for (int64_t j = 0; j <= nc && j < cnt; j++) {
                 double cj[3];
                 int cl[3];
                 prim_color(P, buf[j].idx, ocam, cj, cl);
                 double a = buf[j].alpha, da = buf[j].dalpha;
                 double cm = fmax(cmax, fmax(fabs(cj[0]), fmax(fabs(cj[1]), fabs(cj[2]))));
+                for (int c = 0; c < 3; c++) w[4 * j + c] = T * a * (cj[c] - opt->bg[c]);
+                w[4 * j + 3] = 0.0;      /* marks an undecided stop before j */
                 /* a stop decision within the float32 error of T (1 - alpha)
                  * whose flip would move the colour by more than 5e-5 */
                 double rel = fabs(T * (1.0 - a) / opt->T_min - 1.0);
                 double margin = 3.0 * (dT_rel + da / (1.0 - a)) + 1e-6;
-                if (opt->T_min > 0.0 && rel < margin && T * a * max_abs_diff3(cj, opt->bg) > 5e-5)
-                    flag |= ORD_FLAG_T_MIN;
+                if (opt->T_min > 0.0 && rel < margin) {
+                    if (T * a * max_abs_diff3(cj, opt->bg) > 5e-5) flag |= ORD_FLAG_T_MIN;
+                    w[4 * j + 3] = 1.0;
+                }
+                budget += T * da * 2.0 * cm;
                 if (j == nc) break;
+                if (buf[j].cull_und) extra += T * a * 2.0 * cm;
                 /* near-equal depths whose swap is visible */
                 for (int64_t l = j + 1; opt->order_mode == 0 && l < cnt && buf[l].t - buf[j].t <= 2e-6 * buf[l].t; l++) {
                     double cl_rgb[3];
                     int cl2[3];
                     prim_color(P, buf[l].idx, ocam, cl_rgb, cl2);
-                    if (T * a * buf[l].alpha * max_abs_diff3(cj, cl_rgb) > 5e-5) flag |= ORD_FLAG_DEPTH_TIE;
+                    const double sw = T * a * buf[l].alpha * max_abs_diff3(cj, cl_rgb);
+                    if (sw > 5e-5) flag |= ORD_FLAG_DEPTH_TIE;
+                    extra += sw;
                 }
-                budget += T * da * 2.0 * cm;
                 dT_rel += da / (1.0 - a) + 1e-7;
                 for (int c = 0; c < 3; c++) C[c] += T * a * cj[c];
                 T *= 1.0 - a;
+            }
+            /* undecided stops: stopping before j < nc drops j .. nc-1 (their
+             * colour replaced by the background); going on past nc adds nc */
+            double suffix[3] = {0.0, 0.0, 0.0};
+            for (int64_t j = (nc < cnt ? nc : cnt - 1); j >= 0; j--) {
+                if (j < nc)
+                    for (int c = 0; c < 3; c++) suffix[c] += w[4 * j + c];
+                if (w[4 * j + 3] != 0.0) {
+                    const double zero[3] = {0.0, 0.0, 0.0};
+                    extra += j < nc ? max_abs_diff3(suffix, zero)
+                                    : fmax(fabs(w[4 * j]), fmax(fabs(w[4 * j + 1]), fabs(w[4 * j + 2])));
+                }
+            }
+            /* culled contributors whose culling decision is undecided */
+            for (int64_t u = 0; u < n_und; u++) {
+                double Tu = 1.0;
+                for (int64_t j = 0; j < nc && contrib_cmp(&buf[j], &und[u]) < 0; j++) Tu *= 1.0 - buf[j].alpha;
+                double cu[3];
+                int cl[3];
+                prim_color(P, und[u].idx, ocam, cu, cl);
+                const double cm = fmax(cmax, fmax(fabs(cu[0]), fmax(fabs(cu[1]), fabs(cu[2]))));
+                extra += Tu * und[u].alpha * 2.0 * cm;
             }
             if (budget > 1e-4) flag |= ORD_FLAG_STEEP;
             for (int c = 0; c < 3; c++) rgb[3 * q + c] = C[c] + T * opt->bg[c];
             if (T_final) T_final[q] = T;
             if (n_contrib) n_contrib[q] = (int32_t)nc;
             if (flags) flags[q] = flag;
+            if (tol) tol[q] = budget + extra;
         }
         free(buf);
+        free(und);
+        free(w);
     }
     return fail ? -1 : 0;
 }
@@ -883,7 +1054,7 @@ int ord_render_aux(const ord_params *P, const ord_camera *cam, const ord_options
         for (int64_t q = 0; q < npix; q++) {
             if (!buf) continue;
             int near_amin;
-            int64_t cnt = gather_contributors(P, cam, opt, ocam, pix[2 * q], pix[2 * q + 1], buf, &near_amin);
+            int64_t cnt = gather_contributors(P, cam, opt, ocam, pix[2 * q], pix[2 * q + 1], buf, &near_amin, NULL, NULL, NULL);
             if (cnt < 0) {
 #pragma omp atomic write
                 fail = 1;
@@ -925,7 +1096,7 @@ int64_t ord_contributors(const ord_params *P, const ord_camera *cam, const ord_o
     contrib *buf = (contrib *)malloc(sizeof(contrib) * (size_t)(P->n > 0 ? P->n : 1));
     if (!buf) return -1;
     int near_amin;
-    int64_t cnt = gather_contributors(P, cam, opt, ocam, px, py, buf, &near_amin);
+    int64_t cnt = gather_contributors(P, cam, opt, ocam, px, py, buf, &near_amin, NULL, NULL, NULL);
     if (cnt < 0) {
         free(buf);
         return -1;
@@ -1103,7 +1274,7 @@ int ord_render_backward(const ord_params *P, const ord_camera *cam, const ord_op
             int px = pix[2 * q], py = pix[2 * q + 1];
             const double *gC = dL_drgb + 3 * q;
             int near_amin;
-            int64_t cnt = gather_contributors(P, cam, opt, ocam, px, py, buf, &near_amin);
+            int64_t cnt = gather_contributors(P, cam, opt, ocam, px, py, buf, &near_amin, NULL, NULL, NULL);
             if (cnt < 0) {
 #pragma omp atomic write
                 fail = 1;

@@ -101,10 +101,12 @@ def lib():
         L.ord_pair.restype = C.c_int
         L.ord_pair.argtypes = [C.POINTER(_Params), C.c_int64, C.POINTER(_Camera), C.POINTER(_Options),
                                C.c_int, C.c_int, dp, dp]
+        L.ord_pairs.argtypes = [C.POINTER(_Params), C.POINTER(_Camera), C.POINTER(_Options), C.c_int64,
+                                C.POINTER(C.c_int64), C.POINTER(C.c_int32), dp, dp, dp, C.POINTER(C.c_int32)]
         L.ord_color.argtypes = [C.POINTER(_Params), C.c_int64, C.POINTER(_Camera), dp]
         L.ord_render.restype = C.c_int
         L.ord_render.argtypes = [C.POINTER(_Params), C.POINTER(_Camera), C.POINTER(_Options), C.c_int64,
-                                 C.POINTER(C.c_int32), dp, dp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+                                 C.POINTER(C.c_int32), dp, dp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), dp]
         L.ord_render_backward.restype = C.c_int
         L.ord_render_backward.argtypes = [C.POINTER(_Params), C.POINTER(_Camera), C.POINTER(_Options), C.c_int64,
                                           C.POINTER(C.c_int32), dp, C.POINTER(_Grads)]
@@ -218,6 +220,22 @@ def pair(scene, i: int, cam, opt: Options, px: int, py: int):
     return bool(ok), a.value, t.value
 
 
+def pairs(scene, cam, opt: Options, idx: np.ndarray, pixels: np.ndarray) -> dict:
+    """Many (pixel, primitive) pairs at once: valid, alpha_tilde, r_t and the
+    float32 error model dalpha of alpha_tilde, each (m,)."""
+    keep = _Keep()
+    P, Cm, O = _params(scene, keep), _camera(cam), _options(opt)
+    ix = np.ascontiguousarray(np.asarray(idx, np.int64))
+    pix = np.ascontiguousarray(np.asarray(pixels, np.int32))
+    m = ix.shape[0]
+    a, t, da = np.zeros(m), np.zeros(m), np.zeros(m)
+    ok = np.zeros(m, np.int32)
+    lib().ord_pairs(C.byref(P), C.byref(Cm), C.byref(O), m, ix.ctypes.data_as(C.POINTER(C.c_int64)),
+                    pix.ctypes.data_as(C.POINTER(C.c_int32)), _dp(a), _dp(t), _dp(da),
+                    ok.ctypes.data_as(C.POINTER(C.c_int32)))
+    return dict(valid=ok.astype(bool), alpha=a, t=t, dalpha=da)
+
+
 def color(scene, i: int, cam) -> np.ndarray:
     keep = _Keep()
     P, Cm = _params(scene, keep), _camera(cam)
@@ -231,7 +249,8 @@ def color(scene, i: int, cam) -> np.ndarray:
 
 def render_pixels(scene, cam, opt: Options, pixels: np.ndarray):
     """Render listed pixels (int32 (m, 2) of x, y).  Returns dict with
-    rgb (m, 3), T (m,), n_contrib (m,), flags (m,)."""
+    rgb (m, 3), T (m,), n_contrib (m,), flags (m,), and tol (m,): the
+    float32 error budget of each pixel (colour units; ord_render)."""
     keep = _Keep()
     P, Cm, O = _params(scene, keep), _camera(cam), _options(opt)
     pix = np.ascontiguousarray(np.asarray(pixels, np.int32))
@@ -240,20 +259,23 @@ def render_pixels(scene, cam, opt: Options, pixels: np.ndarray):
     T = np.zeros(m)
     nc = np.zeros(m, np.int32)
     fl = np.zeros(m, np.int32)
+    tol = np.zeros(m)
     rc = lib().ord_render(C.byref(P), C.byref(Cm), C.byref(O), m, pix.ctypes.data_as(C.POINTER(C.c_int32)),
                           _dp(rgb), _dp(T), nc.ctypes.data_as(C.POINTER(C.c_int32)),
-                          fl.ctypes.data_as(C.POINTER(C.c_int32)))
+                          fl.ctypes.data_as(C.POINTER(C.c_int32)), _dp(tol))
     if rc != 0:
         raise MemoryError("oracle render: allocation failed")
-    return dict(rgb=rgb, T=T, n_contrib=nc, flags=fl)
+    return dict(rgb=rgb, T=T, n_contrib=nc, flags=fl, tol=tol)
 
 
 def render(scene, cam, opt: Options):
-    """Full image: rgb (3, H, W), T (H, W), n_contrib (H, W), flags (H, W)."""
+    """Full image: rgb (3, H, W), T (H, W), n_contrib (H, W), flags (H, W),
+    tol (H, W)."""
     H, W = cam.height, cam.width
     r = render_pixels(scene, cam, opt, all_pixels(W, H))
     return dict(rgb=r["rgb"].T.reshape(3, H, W), T=r["T"].reshape(H, W),
-                n_contrib=r["n_contrib"].reshape(H, W), flags=r["flags"].reshape(H, W))
+                n_contrib=r["n_contrib"].reshape(H, W), flags=r["flags"].reshape(H, W),
+                tol=r["tol"].reshape(H, W))
 
 
 def render_aux_pixels(scene, cam, opt: Options, pixels: np.ndarray):

@@ -192,7 +192,8 @@ drk_status_t validate(const drk_params_t* p, const drk_camera_t* cam, const drk_
         return fail(DRK_ERR_INVALID_ARG, "ovf_capacity not in -1..2048");
     if (opt->order_mode != DRK_ORDER_EXACT && opt->order_mode != DRK_ORDER_CACHE_SORT)
         return fail(DRK_ERR_INVALID_ARG, "order_mode not in 0..1");
-    for (int i = 0; i < 4; i++)
+    if (opt->record_chunks < 0) return fail(DRK_ERR_INVALID_ARG, "record_chunks must be >= 0");
+    for (int i = 0; i < 3; i++)
         if (opt->reserved[i] != 0) return fail(DRK_ERR_INVALID_ARG, "reserved option fields must be zero");
     for (int i = 0; i < 3; i++)
         if (!std::isfinite(opt->bg[i])) return fail(DRK_ERR_INVALID_ARG, "non-finite bg");
@@ -459,6 +460,7 @@ drk_status_t drk_render(drk_ctx_t* ctx, const drk_params_t* params, const drk_ca
         const uint64_t npix = (uint64_t)cam->width * cam->height;
         uint64_t chunks = prev > 0 ? prev + prev / 4 + warps : (npix * 128 + kRecChunk - 1) / kRecChunk + warps;
         chunks = std::min<uint64_t>(chunks, (0xffffffffull / kRecChunk) - 1);
+        if (opt->record_chunks > 0) chunks = std::min<uint64_t>(chunks, (uint64_t)opt->record_chunks);
         R.rec_cap = (uint32_t)(chunks * kRecChunk);
         R.rec_ctr = ctx->rec_ctr;
         if ((s = al.get(&R.rec_key, (size_t)R.rec_cap)) != DRK_OK) return s;

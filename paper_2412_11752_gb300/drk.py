@@ -59,7 +59,7 @@ class drk_options_t(C.Structure):
     _fields_ = [("alpha_min", C.c_float), ("T_min", C.c_float), ("alpha_max", C.c_float),
                 ("lowpass_sl", C.c_float), ("near_plane", C.c_float), ("bg", C.c_float * 3),
                 ("cull_level", C.c_int32), ("kbuf_capacity", C.c_int32), ("ovf_capacity", C.c_int32),
-                ("order_mode", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("order_mode", C.c_int32), ("record_chunks", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
 class drk_image_t(C.Structure):
@@ -163,6 +163,7 @@ class Options:
     kbuf_capacity: int = 16
     ovf_capacity: int = 0
     order_mode: int = 0          # 0 exact order; 1 the paper's cache-sorting (forward only)
+    record_chunks: int = 0       # cap on the backward's contributor records (1024 each); 0 = automatic
 
     def to_c(self) -> drk_options_t:
         o = drk_options_t()
@@ -173,6 +174,7 @@ class Options:
         o.cull_level, o.kbuf_capacity = int(self.cull_level), int(self.kbuf_capacity)
         o.ovf_capacity = int(self.ovf_capacity)
         o.order_mode = int(self.order_mode)
+        o.record_chunks = int(self.record_chunks)
         return o
 
 
@@ -377,16 +379,18 @@ def drk_sort_pairs(keys: torch.Tensor, vals: torch.Tensor, key_bits: int = 32, c
 
 def drk_sort_pairs_static(keys: torch.Tensor, vals: torch.Tensor, key_bits: int = 32, stream=None) -> None:
     """drk_sort_pairs for callers that cannot allocate device memory while they
-    sort (graph capture without allocation nodes, host callbacks, fixed
-    start-up memory): the working memory is a fixed array inside the library,
-    shared by all calls (order overlapping calls yourself).  At most 2^20
-    pairs; make the first call on a device before any stream capture."""
+    sort (device memory fixed at start-up, allocation latency not allowed, or
+    code inside an allocator's own bookkeeping): the working memory is a
+    fixed array inside the library, shared by all calls (order overlapping
+    calls yourself).  At most 2^20 pairs.  Runs on the device of `keys`, on
+    that device's current stream unless `stream` is given."""
     assert keys.is_cuda and keys.dtype == torch.int32 and vals.dtype == torch.int32
     assert keys.is_contiguous() and vals.is_contiguous() and keys.numel() == vals.numel()
-    code = lib().drk_sort_pairs_static(C.c_void_p(keys.data_ptr()), C.c_void_p(vals.data_ptr()), keys.numel(),
-                                      int(key_bits), _stream_ptr(stream))
-    if code != DRK_OK:
-        raise DrkError(code, "drk_sort_pairs_static failed (n above 2^20, bad arguments or a launch error)")
+    with torch.cuda.device(keys.device):
+        if stream is None:
+            stream = torch.cuda.current_stream(keys.device)
+        _check(lib().drk_sort_pairs_static(C.c_void_p(keys.data_ptr()), C.c_void_p(vals.data_ptr()), keys.numel(),
+                                           int(key_bits), _stream_ptr(stream)))
 
 
 class DRKRender(torch.autograd.Function):

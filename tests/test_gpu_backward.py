@@ -29,11 +29,16 @@ def compare_grads(drk, scene, cam, opt, seed=0, names=NAMES, tol=TOL_GRAD_REL):
     oopt = oracle_options(opt)
     ref_f = O.render(scene, cam, oopt)
     w = np.random.default_rng(seed).standard_normal((3, cam.height, cam.width))
-    w[:, excluded(ref_f["flags"])] = 0.0           # drop threshold-decided pixels
+    w[:, excluded(ref_f["flags"])] = 0.0           # no dL on float32-undecidable pixels
     g = drk.drk_render_backward(ds, cam, opt, st, torch.from_numpy(w.astype(np.float32)).cuda())
     torch.cuda.synchronize()
     st.free()
     ref = O.render_backward(scene, cam, oopt, w)
+    report = _compare_tensors(g, ref, names, tol, f"{cam.width}x{cam.height}")
+    return report
+
+
+def _compare_tensors(g, ref, names, tol, what):
     report = {}
     for k in names:
         a = g[k].cpu().numpy().astype(np.float64)
@@ -41,11 +46,62 @@ def compare_grads(drk, scene, cam, opt, seed=0, names=NAMES, tol=TOL_GRAD_REL):
         r = rel_err(a, b)
         report[k] = r
         assert np.all(np.isfinite(a)), k
-        assert r <= tol, f"{k}: relative error {r:.2e} (all: {report})"
+        assert r <= tol, f"{what} {k}: relative error {r:.2e} (all: {report})"
         bound = 1e-3 * np.abs(b).max() + 1e-3 * np.abs(b) + 1e-7
         worst = np.max(np.abs(a - b) - bound)
-        assert worst <= 0, f"{k}: elementwise excess {worst:.2e}"
+        assert worst <= 0, f"{what} {k}: elementwise excess {worst:.2e}"
+    print(f"{what}: gradient relative errors " + ", ".join(f"{k} {v:.1e}" for k, v in report.items()))
     return report
+
+
+def compare_grads_sampled(drk, workload, count, seed, tiles, opt=None):
+    """Backward of a full-size workload with dL nonzero only on seeded pixels
+    plus whole tiles, against the oracle's back-to-front derivative of those
+    pixels.  Pixels the oracle flags get dL = 0: a float32-undecidable stop,
+    depth tie or culling decision, or alphas whose float32 error the
+    budget lets exceed half the image tolerance (hard edges, where Psi's
+    pieces and their tau derivatives switch within float32 error)."""
+    from test_gpu_render import full_size_tiles
+    sc_f, cam_f = synth.WORKLOADS[workload]
+    scene, cam = sc_f(), cam_f()
+    opt = opt or drk.Options()
+    ds = drk.DeviceScene.from_scene(scene, "cuda")
+    rgb, T, n, st = drk.drk_render(ds, cam, opt, need_state=True)
+    oopt = oracle_options(opt)
+    pix = synth.pixel_sample(cam.width, cam.height, count, seed=seed, tiles=full_size_tiles(scene, cam, tiles))
+    keep = ~excluded(O.render_pixels(scene, cam, oopt, pix)["flags"])
+    pk = pix[keep]
+    wpix = np.random.default_rng(seed + 1).standard_normal((pk.shape[0], 3))
+    w = np.zeros((3, cam.height, cam.width), np.float32)
+    w[:, pk[:, 1], pk[:, 0]] = wpix.T
+    g = drk.drk_render_backward(ds, cam, opt, st, torch.from_numpy(w).cuda())
+    torch.cuda.synchronize()
+    st.free()
+    stats = drk.default_context().stats()
+    ref = O.render_backward_pixels(scene, cam, oopt, pk, w[:, pk[:, 1], pk[:, 0]].T.astype(np.float64))
+    print(f"{workload}: {pk.shape[0]} of {pix.shape[0]} sampled pixels carry dL, "
+          f"{stats['n_replay_evals']} replay evaluations")
+    _compare_tensors(g, ref, NAMES, TOL_GRAD_REL, workload)
+    return stats
+
+
+def test_backward_clustered_100k_1080p_sampled(drk):
+    compare_grads_sampled(drk, "clustered-100k-1080p", 2048, 2101, tiles=4)
+
+
+def test_backward_train_300k_1600x1064_sampled(drk):
+    compare_grads_sampled(drk, "train-300k-1600x1064", 1024, 3102, tiles=2)
+
+
+@pytest.mark.parametrize("chunks", [1, 6])
+def test_backward_with_record_pool_overflow(drk, chunks):
+    # a capped record pool sends tiles to the exact replay of the forward
+    # traversal; the gradients stay the oracle's
+    scene = synth.scene_clustered(2000, 8, seed=3200, n_clusters=5)
+    cam = synth.camera_lookat(64, 64, eye=(1.5, -0.4, -1.0), target=(0.5, 0.5, 0.5))
+    compare_grads(drk, scene, cam, drk.Options(record_chunks=chunks), seed=2)
+    st = drk.default_context().stats()
+    assert st["n_replay_evals"] > 0
 
 
 def test_backward_layers_no_thresholds(drk):

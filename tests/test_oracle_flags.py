@@ -28,10 +28,41 @@ def test_equal_depths_with_different_colours_are_flagged():
         assert r["flags"][0] & O.FLAG_DEPTH_TIE, mode
         same = O.render_pixels(_two_coplanar([0.3, 0.3, 0.3], [0.3, 0.3, 0.3]), cam, opt, pix)
         assert not same["flags"][0] & O.FLAG_DEPTH_TIE, mode
+        # the pixel's float32 budget covers the exchange: composited in the
+        # other order the colour moves by exactly a0 a1 |c0 - c1| (T = 1)
+        swap = a[0] * a[1] * 1.0
+        assert r["tol"][0] >= swap * (1 - 1e-9), (r["tol"][0], swap)
+        assert same["tol"][0] < 1e-5
+
+
+def test_budget_covers_an_undecidable_stop():
+    # identical fronto-parallel layers: compositing stops before the first
+    # layer whose T (1 - a) falls below T_min; with T_min set to that value
+    # exactly the stop is undecidable and the budget must cover the colour
+    # change of deciding it either way (one layer more or less)
+    f = lambda v: np.asarray(v, np.float64)
+    n, K = 6, 4
+    sc = synth.Scene(mu=f([[0.5, 0.5, 0.3 + 0.05 * i] for i in range(n)]), quat=f([[1.0, 0, 0, 0]] * n),
+                     scale=f([[0.3] * K] * n), theta=f([2 * np.pi * np.arange(K) / K] * n), eta=f([0.0] * n),
+                     tau=f([0.0] * n), opacity=f([0.5] * n), color=f([[0.9, 0.1, 0.5]] * n), sh_degree=-1)
+    cam = synth.camera_front(16, 16)
+    pix = np.array([[8, 8]], np.int32)
+    base = O.Options(lowpass_sl=0.0, T_min=0.0)
+    idx, t, a, nc = O.contributors(sc, cam, base, 8, 8)
+    T = np.cumprod(np.concatenate([[1.0], 1 - a]))
+    stop = 3                                   # T_min exactly at T_3 (1 - a_3)
+    opt = O.Options(lowpass_sl=0.0, T_min=float(T[stop] * (1 - a[stop])))
+    r = O.render_pixels(sc, cam, opt, pix)
+    assert r["flags"][0] & O.FLAG_T_MIN
+    one_more = T[stop] * a[stop] * 0.9          # composite layer 3 too (bg = 0)
+    assert r["tol"][0] >= one_more * (1 - 1e-9), (r["tol"][0], one_more)
 
 
 def test_excluded_covers_every_undecidable_flag():
-    from helpers import excluded
+    from helpers import excluded, undecidable
     for f in (O.FLAG_T_MIN, O.FLAG_DEPTH_TIE, O.FLAG_STEEP, O.FLAG_CULL):
         assert excluded(np.array([f]))[0]
+    for f in (O.FLAG_T_MIN, O.FLAG_DEPTH_TIE, O.FLAG_CULL):
+        assert undecidable(np.array([f]))[0]
+    assert not undecidable(np.array([O.FLAG_STEEP]))[0]       # continuous: within the budget
     assert not excluded(np.array([O.FLAG_ALPHA_MIN]))[0]      # informational only
