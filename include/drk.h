@@ -267,12 +267,13 @@ drk_status_t drk_get_stats(drk_ctx_t *ctx, drk_stats_t *out);
 
 /* Stage timing with CUDA events recorded on the caller's stream around each
  * stage of drk_render / drk_render_backward.  Stages: 0 preprocess (bounds,
- * culling count, scan), 1 pair emission, 2 radix sort and tile ranges,
- * 3 raster forward, 4 raster backward, 5 preprocess backward (6, 7
- * unused).  drk_timing_enable resets the accumulators and switches timing
- * on (enable != 0) or off.  drk_timing_read waits for the recorded events
- * and returns, per stage, the summed milliseconds and the number of timed
- * launches (host arrays of 8). */
+ * culling count, scan), 1 pair emission, 2 radix sort, tile ranges and tile
+ * order, 3 raster forward, 4 raster backward over the contributor records,
+ * 5 preprocess backward, 6 exact replay of tiles whose records overflowed,
+ * 7 grouping of the contributor records.  drk_timing_enable resets the
+ * accumulators and switches timing on (enable != 0) or off.
+ * drk_timing_read waits for the recorded events and returns, per stage, the
+ * summed milliseconds and the number of timed launches (host arrays of 8). */
 drk_status_t drk_timing_enable(drk_ctx_t *ctx, int enable);
 drk_status_t drk_timing_read(drk_ctx_t *ctx, double *ms, int64_t *launches);
 

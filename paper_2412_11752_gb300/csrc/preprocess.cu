@@ -533,9 +533,160 @@ __device__ __forceinline__ bool tile_test(const float* __restrict__ rec, const f
     return chord_ok && dmin2 <= rho_arc * rho_arc * 1.002f;
 }
 
+// ---------------------------------------------------------------------------
+// Row-interval culling (DRK_CULL_TILE).  The kernel's support lies in the
+// union over sectors k of the sector of radius rho_k -- covered by a
+// polygon of kArcSeg tangent segments, which lies inside the polygon the
+// screen rectangle is built from -- cut by the chord of its L1 bound, the
+// triangle (0, L e_k, L e_k1) with L = sqrt(E* / eta) (E >= eta r1^2,
+// Eq. 7 - Eq. 8).  Each piece is convex and lies in front of the near plane
+// (else the primitive takes the per-tile test), so it projects to a convex
+// polygon.  In every row of tiles, the tiles kept are those whose columns
+// hold a pixel centre (integer pixel index) within the x-range of the
+// pieces (and of the filter disc) over the row's band of pixel rows, both
+// widened by 0.1 pixel, far above the float32 error of the projection.
+// The count and the emission run the same code, so they keep the same
+// tiles.
+constexpr int kArcSeg = 4;    // tangent segments per sector arc (the cover exceeds the arc by 1/cos(gap/8))
+constexpr int kPieceV = 2 * kArcSeg + 3;   // centre, 2 kArcSeg + 1 arc points, one cut point
+
+template <int KMAX>
+struct Pieces {
+    float2 v[KMAX][kPieceV];
+    int n[KMAX];
+};
+
+// Lane k < K builds piece k of primitive i in pixel-index coordinates.
+template <int KMAX>
+__device__ void build_pieces(const PreArgs& A, int64_t i, const float* __restrict__ rec,
+                             const float* __restrict__ bnd, Pieces<KMAX>& P) {
+    using RK = Rec<KMAX>;
+    const int lane = threadIdx.x & 31;
+    const int K = A.p.K;
+    if (lane >= K) return;
+    PrimGeom G;
+    prim_geom(A, i, G);
+    const int k = lane, k1 = (k + 1 == K) ? 0 : k + 1;
+    const float tk = k == 0 ? 0.f : rec[RK::TH + k - 1];
+    const float tk1 = rec[RK::TH + k];
+    const float gap = tk1 - tk;
+    const float rho = bnd[B_RHO + k];
+    // the arc of radius rho over [tk, tk1], covered by kArcSeg tangent
+    // segments: points on the arc alternate with the tangents' crossings
+    const float half = gap / (2 * kArcSeg);
+    const float rt = rho / cosf(half);
+    float px[kPieceV], py[kPieceV];
+    int n = 0;
+    px[n] = 0.f; py[n] = 0.f; n++;
+    for (int m = 0; m <= 2 * kArcSeg; m++) {
+        float sa, ca;
+        sincosf(tk + half * m, &sa, &ca);
+        const float rr = (m & 1) ? rt : rho;
+        px[n] = rr * ca; py[n] = rr * sa; n++;
+    }
+    const float L = bnd[Bnd<KMAX>::CL1];
+    float qx[kPieceV], qy[kPieceV];
+    int m = 0;
+    if (L > 0.f) {
+        // keep the side of the chord the centre is on: n . p <= L n . e_k
+        const float ex = rec[RK::EX + k], ey = rec[RK::EY + k];
+        const float nx = rec[RK::EY + k1] - ey, ny = ex - rec[RK::EX + k1];
+        const float lim = L * (nx * ex + ny * ey);
+        for (int a = 0; a < n; a++) {
+            const int b = (a + 1 == n) ? 0 : a + 1;
+            const float da = nx * px[a] + ny * py[a] - lim, db = nx * px[b] + ny * py[b] - lim;
+            if (da <= 0.f) { qx[m] = px[a]; qy[m] = py[a]; m++; }
+            if ((da < 0.f && db > 0.f) || (da > 0.f && db < 0.f)) {
+                const float t = da / (da - db);
+                qx[m] = px[a] + t * (px[b] - px[a]);
+                qy[m] = py[a] + t * (py[b] - py[a]);
+                m++;
+            }
+        }
+    } else {
+        for (int a = 0; a < n; a++) { qx[a] = px[a]; qy[a] = py[a]; }
+        m = n;
+    }
+    for (int a = 0; a < m; a++) {
+        float pc[3];
+        for (int r = 0; r < 3; r++) pc[r] = G.muc[r] + qx[a] * G.Rxp[r] + qy[a] * G.Ryp[r];
+        const float iz = 1.f / pc[2];
+        P.v[k][a] = make_float2(A.cam.fx * pc[0] * iz + A.cam.cx - 0.5f, A.cam.fy * pc[1] * iz + A.cam.cy - 0.5f);
+    }
+    P.n[k] = m;
+}
+
+// Tiles [a, b] of row ty (clamped to the rectangle's columns x0 .. x1) whose
+// columns meet the pieces or the filter disc within the row's pixel band.
+template <int KMAX>
+__device__ void row_span(const Pieces<KMAX>& P, int K, const float* __restrict__ bnd, const FrameConst& fc, int ty,
+                         int x0, int x1, int& a, int& b) {
+    // pixel centres sit at integer pixel indices; 0.1 px covers the float32
+    // error of the projection many times over
+    const float yl = (float)(ty * kTile) - 0.1f;
+    const float yh = (float)min(ty * kTile + kTile - 1, fc.height - 1) + 0.1f;
+    float xmin = 1e30f, xmax = -1e30f;
+    for (int k = 0; k < K; k++) {
+        const int n = P.n[k];
+        for (int e = 0; e < n; e++) {
+            float2 p = P.v[k][e], q = P.v[k][(e + 1 == n) ? 0 : e + 1];
+            if (p.y > q.y) { const float2 t = p; p = q; q = t; }
+            if (q.y < yl || p.y > yh) continue;
+            const float dy = q.y - p.y;
+            const float xa = (p.y >= yl || dy <= 0.f) ? p.x : p.x + (q.x - p.x) * ((yl - p.y) / dy);
+            const float xb = (q.y <= yh || dy <= 0.f) ? q.x : p.x + (q.x - p.x) * ((yh - p.y) / dy);
+            xmin = fminf(xmin, fminf(xa, xb));
+            xmax = fmaxf(xmax, fmaxf(xa, xb));
+        }
+    }
+    const float fr2 = bnd[B_FR2];
+    if (fr2 >= 0.f) {
+        const float fy = bnd[B_FCY];
+        const float d = fmaxf(fmaxf(yl - fy, fy - yh), 0.f);
+        if (d * d <= fr2) {
+            const float dx = sqrtf(fr2 - d * d);
+            xmin = fminf(xmin, bnd[B_FCX] - dx);
+            xmax = fmaxf(xmax, bnd[B_FCX] + dx);
+        }
+    }
+    // integer pixel columns within [xmin - 0.1, xmax + 0.1]
+    const float lx = ceilf(fmaxf(xmin - 0.1f, -1.f)), hx = floorf(fminf(xmax + 0.1f, (float)fc.width));
+    if (!(lx <= hx)) { a = 1; b = 0; return; }
+    a = max(x0, (int)floorf(lx / kTile));
+    b = min(x1, (int)floorf(hx / kTile));
+}
+
+// Lower bound of r_t over the pixels of tile (tx, ty) the primitive can
+// reach (the depth field of its pair key; as in tile_test).
+__device__ __forceinline__ float tile_depth_bound(const float* __restrict__ rec, const float* __restrict__ bnd,
+                                                  const FrameConst& fc, int tx, int ty) {
+    const float x0 = (float)(tx * kTile), y0 = (float)(ty * kTile);
+    const float x1 = (float)min(tx * kTile + kTile - 1, fc.width - 1);
+    const float y1 = (float)min(ty * kTile + kTile - 1, fc.height - 1);
+    const float cx[4] = {x0, x1, x1, x0}, cy[4] = {y0, y0, y1, y1};
+    float wmax = -1e30f;
+    for (int c = 0; c < 4; c++) wmax = fmaxf(wmax, fmaf(rec[R_HW0], cx[c], fmaf(rec[R_HW1], cy[c], rec[R_HW2])));
+    const float tile_lb = wmax > 0.f ? fmaxf(1.f / wmax, fc.near_plane) * (1.f - 2e-6f) : fc.near_plane;
+    bool keep_f = false;
+    if (bnd[B_FR2] >= 0.f) {
+        const float dx = fmaxf(fmaxf(x0 - bnd[B_FCX], bnd[B_FCX] - x1), 0.f);
+        const float dy = fmaxf(fmaxf(y0 - bnd[B_FCY], bnd[B_FCY] - y1), 0.f);
+        keep_f = dx * dx + dy * dy <= bnd[B_FR2];
+    }
+    return keep_f ? tile_lb : fmaxf(tile_lb, bnd[B_ZLB]);
+}
+
+// Does primitive i take the row-interval test?
+__device__ __forceinline__ bool row_culled(const PreArgs& A, const float* __restrict__ bnd) {
+    return A.cull_level == DRK_CULL_TILE && !(reinterpret_cast<const int*>(bnd)[B_FLAGS] & 2);
+}
+
+constexpr int kCullThreads = 256;
+
 // K2a: count the pairs of each primitive (one warp per primitive).
 template <int KMAX>
-__global__ void __launch_bounds__(256) count_kernel(PreArgs A) {
+__global__ void __launch_bounds__(kCullThreads) count_kernel(PreArgs A) {
+    __shared__ Pieces<KMAX> pieces[kCullThreads / 32];
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (i >= A.p.n) return;
@@ -545,6 +696,21 @@ __global__ void __launch_bounds__(256) count_kernel(PreArgs A) {
     const int x0 = bi[B_X0], y0 = bi[B_Y0], x1 = bi[B_X1], y1 = bi[B_Y1];
     if (x1 < x0 || y1 < y0) {
         if (lane == 0) A.count[i] = 0;
+        return;
+    }
+    if (row_culled(A, bnd)) {
+        Pieces<KMAX>& P = pieces[threadIdx.x >> 5];
+        if (lane < KMAX) P.n[lane] = 0;
+        if (bi[B_FLAGS] & 1) build_pieces<KMAX>(A, i, rec, bnd, P);
+        __syncwarp();
+        uint32_t cnt = 0;
+        for (int ty = y0 + lane; ty <= y1; ty += 32) {
+            int a, b;
+            row_span<KMAX>(P, A.p.K, bnd, A.fc, ty, x0, x1, a, b);
+            cnt += b >= a ? (uint32_t)(b - a + 1) : 0u;
+        }
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        if (lane == 0) A.count[i] = cnt;
         return;
     }
     const int wdt = x1 - x0 + 1;
@@ -566,7 +732,8 @@ __global__ void __launch_bounds__(256) count_kernel(PreArgs A) {
 // bound of r_t, value = primitive index.  Pairs of primitive i start at
 // offsets[i]; within a primitive they are in tile order.
 template <int KMAX>
-__global__ void __launch_bounds__(256) emit_kernel(PreArgs A) {
+__global__ void __launch_bounds__(kCullThreads) emit_kernel(PreArgs A) {
+    __shared__ Pieces<KMAX> pieces[kCullThreads / 32];
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (i >= A.p.n) return;
@@ -579,10 +746,45 @@ __global__ void __launch_bounds__(256) emit_kernel(PreArgs A) {
     const DepthQuant dq = *A.dq;
     const uint32_t qmax = (1u << dq.depth_bits) - 1u;
     const int wdt = x1 - x0 + 1;
-    const int area = wdt * (y1 - y0 + 1);
+    int area = wdt * (y1 - y0 + 1);
     uint64_t out = A.offsets[i];
     const uint64_t end = A.offsets[i + 1];
     const int cull = A.cull_level >= DRK_CULL_TILE ? A.cull_level : DRK_CULL_NONE;
+    // depth field of a pair key: the quantised lower bound of r_t (or, in the
+    // cache-sorting mode, the primitive's centre-depth rank)
+    auto depth_field = [&](float lb) -> uint32_t {
+        if (A.rank) return A.rank[i];
+        const float qf = floorf((lb - dq.zmin) * dq.scale);
+        return qf <= 0.f ? 0u : (qf >= (float)qmax ? qmax : (uint32_t)qf);
+    };
+    if (row_culled(A, bnd)) {
+        Pieces<KMAX>& P = pieces[threadIdx.x >> 5];
+        if (lane < KMAX) P.n[lane] = 0;
+        if (bi[B_FLAGS] & 1) build_pieces<KMAX>(A, i, rec, bnd, P);
+        __syncwarp();
+        // each lane writes the tiles of its rows, after those of lower lanes
+        for (int r0 = y0; r0 <= y1; r0 += 32) {
+            const int ty = r0 + lane;
+            int a = 1, b = 0;
+            if (ty <= y1) row_span<KMAX>(P, A.p.K, bnd, A.fc, ty, x0, x1, a, b);
+            const uint32_t c = b >= a ? (uint32_t)(b - a + 1) : 0u;
+            uint32_t incl = c;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            uint64_t pos = out + (incl - c);
+            for (int tx = a; tx <= b; tx++, pos++) {
+                if (pos < end) {   // never write past the slots the count pass allotted
+                    A.keys[pos] = ((uint32_t)(ty * A.fc.tiles_x + tx) << dq.depth_bits) |
+                                  depth_field(tile_depth_bound(rec, bnd, A.fc, tx, ty));
+                    A.vals[pos] = (uint32_t)i;
+                }
+            }
+            out += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        area = 0;   // the per-tile loop below has nothing left to do
+    }
     for (int base = 0; base < area; base += 32) {
         const int j = base + lane;
         bool keep = false;
@@ -591,14 +793,7 @@ __global__ void __launch_bounds__(256) emit_kernel(PreArgs A) {
             const int tx = x0 + j % wdt, ty = y0 + j / wdt;
             float lb;
             keep = tile_test<KMAX>(rec, bnd, A.p.K, A.fc, tx, ty, cull, lb);
-            uint32_t qd;
-            if (A.rank) {
-                qd = A.rank[i];   // pre-sort by centre depth (the paper's cache-sorting mode)
-            } else {
-                const float qf = floorf((lb - dq.zmin) * dq.scale);
-                qd = qf <= 0.f ? 0u : (qf >= (float)qmax ? qmax : (uint32_t)qf);
-            }
-            key = ((uint32_t)(ty * A.fc.tiles_x + tx) << dq.depth_bits) | qd;
+            key = ((uint32_t)(ty * A.fc.tiles_x + tx) << dq.depth_bits) | depth_field(lb);
         }
         const uint32_t m = __ballot_sync(0xffffffffu, keep);
         if (keep) {

@@ -222,30 +222,30 @@ __device__ __forceinline__ void grad_from_info(const RasterArgs& A, const float*
     float dL_dt = 0.f, dL_du = 0.f, dL_dv = 0.f;
     if (e.use_filter) {
         // f = o 2^-Xf, Xf = dp2 d2 t^2 fcoef
-        out.v[A_OPA] = G * e.f / o;
+        out.v[A_OPA] = G * __fdividef(e.f, o);
         const float dXf = -G * e.f * kLn2;
         const float dx = pr.x - r[R_FPX], dy = pr.y - r[R_FPY];
         const float k2 = pr.d2 * t * t * r[R_FCOEF];
         out.v[A_FPX] = dXf * (-2.f * dx * k2);
         out.v[A_FPY] = dXf * (-2.f * dy * k2);
         out.v[A_FCOEF] = dXf * (dx * dx + dy * dy) * pr.d2 * t * t;
-        dL_dt = dXf * 2.f * e.Xf / t;
+        dL_dt = __fdividef(dXf * 2.f * e.Xf, t);
     } else {
         const float tau = r[R_TAU];
         const float g = e.g;
         float slope, dpsi_dtau;
         const float p1 = 1.f + tau, m1 = 1.f - tau;
         if (g < r[R_B1]) {
-            slope = m1 / p1;
-            dpsi_dtau = -2.f * g / (p1 * p1);
+            slope = __fdividef(m1, p1);
+            dpsi_dtau = __fdividef(-2.f * g, p1 * p1);
         } else if (g < r[R_B2]) {
-            slope = p1 / m1;
-            dpsi_dtau = (2.f * g - 1.f) / (m1 * m1);
+            slope = __fdividef(p1, m1);
+            dpsi_dtau = __fdividef(2.f * g - 1.f, m1 * m1);
         } else {
-            slope = m1 / p1;
-            dpsi_dtau = (2.f - 2.f * g) / (p1 * p1);
+            slope = __fdividef(m1, p1);
+            dpsi_dtau = __fdividef(2.f - 2.f * g, p1 * p1);
         }
-        out.v[A_OPA] = G * (e.al_k / o);
+        out.v[A_OPA] = G * __fdividef(e.al_k, o);
         out.v[A_TAU] = G * o * dpsi_dtau;
         const float dX = -G * o * slope * kLn2 * g;
         out.v[A_ETA] = dX * (0.5f * kLog2e) * (e.r1 * e.r1 - e.r2sq * e.Q);
@@ -257,8 +257,8 @@ __device__ __forceinline__ void grad_from_info(const RasterArgs& A, const float*
         const float* sc = A.p.scale + (size_t)K * idx;
         const float sk = __ldg(sc + k), sk1 = __ldg(sc + k1);
         // Q = (A_k + A_k1) + c (A_k - A_k1), A = 1/(2 s^2)
-        float ds_k = d_Q * (1.f + e.c) * (-1.f / (sk * sk * sk));
-        float ds_k1 = d_Q * (1.f - e.c) * (-1.f / (sk1 * sk1 * sk1));
+        float ds_k = -d_Q * (1.f + e.c) * rcp_approx(sk * sk * sk);
+        float ds_k1 = -d_Q * (1.f - e.c) * rcp_approx(sk1 * sk1 * sk1);
         const float d_c = d_Q * e.dif;
         // c = cos(dth), dth = (phi - th_k) pi / gap
         const float d_dth = -d_c * __sinf(e.dth);
@@ -266,9 +266,10 @@ __device__ __forceinline__ void grad_from_info(const RasterArgs& A, const float*
         const float d_phi = d_dth * pg;
         float dth_k = d_dth * pg * (e.dth * (1.f / kPi) - 1.f);
         float dth_k1 = -d_dth * pg * e.dth * (1.f / kPi);
-        if (e.r2sq > 0.f) {
-            dL_du += d_phi * (-e.v / e.r2sq);
-            dL_dv += d_phi * (e.u / e.r2sq);
+        if (e.r2sq > 1e-30f) {
+            const float ir2 = rcp_approx(e.r2sq);
+            dL_du -= d_phi * e.v * ir2;
+            dL_dv += d_phi * e.u * ir2;
         }
         dL_du += d_r2sq * 2.f * e.u;
         dL_dv += d_r2sq * 2.f * e.v;
@@ -281,9 +282,9 @@ __device__ __forceinline__ void grad_from_info(const RasterArgs& A, const float*
         const float wy = (-e1x * sa + ekx * sb) * e.idet;
         dL_du += d_r1 * wx;
         dL_dv += d_r1 * wy;
-        ds_k += d_r1 * (-e.a) * (wx * ekx + wy * eky) / sk;
+        ds_k -= __fdividef(d_r1 * e.a * (wx * ekx + wy * eky), sk);
         dth_k += d_r1 * (-e.a) * (wy * ekx - wx * eky);
-        ds_k1 += d_r1 * (-e.b) * (wx * e1x + wy * e1y) / sk1;
+        ds_k1 -= __fdividef(d_r1 * e.b * (wx * e1x + wy * e1y), sk1);
         dth_k1 += d_r1 * (-e.b) * (wy * e1x - wx * e1y);
         out.k = k;
         out.k1 = k1;
@@ -302,7 +303,7 @@ __device__ __forceinline__ void grad_from_info(const RasterArgs& A, const float*
         out.v[A_H + 3] = dV * pr.x;
         out.v[A_H + 4] = dV * pr.y;
         out.v[A_H + 5] = dV;
-        dL_dt = (dL_du * e.u + dL_dv * e.v) / t;
+        dL_dt = __fdividef(dL_du * e.u + dL_dv * e.v, t);
     }
     // t = 1 / w
     const float dw = -dL_dt * t * t;
@@ -699,11 +700,11 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
 // stage with cp.async one chunk ahead of use; the kernel stage runs only
 // when some lane of the warp passes the geometry stage.  Tasks are taken
 // heaviest tile first (longest list), which keeps the tail short.
-// The batch variant keeps a frame slot per task and needs a few registers
-// more; with a register budget for four CTAs per SM (the shared memory of 16
-// heap slots allows no more) it does not spill.
+// The register budget is that of the CTAs per SM the shared memory allows:
+// four with 16 or more heap slots (and for the batch variant, which keeps a
+// frame slot per task), five with 8.
 template <int KMAX, int CAP, bool BWD, bool BATCH, bool AUX = false>
-__global__ void __launch_bounds__(kRasterThreads, BATCH ? 4 : 5) raster_kernel(RasterArgs A) {
+__global__ void __launch_bounds__(kRasterThreads, (BATCH || CAP >= 16) ? 4 : 5) raster_kernel(RasterArgs A) {
     constexpr int kWarps = kRasterThreads / 32;
     constexpr int HDR4 = Rec<KMAX>::HDR / 4;
     extern __shared__ float4 smem4[];
@@ -807,7 +808,6 @@ __global__ void __launch_bounds__(256) raster_backward_records_kernel(RasterArgs
                                                                       const uint32_t* __restrict__ sslot, uint32_t n) {
     const int lane = threadIdx.x & 31;
     const FrameConst& fc = A.fc;
-    const size_t npix = (size_t)fc.width * fc.height;
     const int K = A.K;
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t g = i < n ? skey[i] : kNoSlot;
@@ -837,7 +837,7 @@ __global__ void __launch_bounds__(256) raster_backward_records_kernel(RasterArgs
             const float T = tp.x;
             const float P[3] = {tp.y, tp.z, tp.w};
             const float wgt = __fmul_rn(a, T);
-            const float inv1ma = 1.f / (1.f - a);
+            const float inv1ma = rcp_approx(1.f - a);
             // the pixel's dL and final colour: one 32-byte sector
             const float4 q0 = A.pixg[2 * (size_t)pix], q1 = A.pixg[2 * (size_t)pix + 1];
             const float dL[3] = {q0.x, q0.y, q0.z}, Cf[3] = {q0.w, q1.x, q1.y};
