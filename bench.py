@@ -42,6 +42,10 @@ OPS_PER_EVAL = 66
 # extra operations per composited contributor in the backward (Eq. 1
 # gradient, chain through Eq. 10 - Eq. 4 to the record quantities)
 OPS_PER_EMIT_BWD = 190
+# transcendental operations per evaluation: the reciprocal of the ray
+# depth, the reciprocal inside the polar angle, the cosine of Eq. 6 and
+# the exponentials of Eq. 8 and Eq. 10
+XU_PER_EVAL = 5
 
 
 def parse():
@@ -301,25 +305,60 @@ def run_drk(args):
     spread = {"min": float(np.min(ms)), "p10": float(np.percentile(ms, 10)), "median": float(np.median(ms)),
               "p90": float(np.percentile(ms, 90)), "max": float(np.max(ms)), "mean": float(np.mean(ms))}
 
-    # ---- roofline of the dominant kernel (FP32 ALU bound)
+    # ---- roofline of the dominant kernel: FP32 FMA pipe and transcendental
+    # unit, both measured on this GPU by the library's own kernels
+    pipes = drk.measure_pipes(local)
     peaks = measured_peaks()
     sms = props.multi_processor_count
     smax = float(peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0)
-    peak_tops = sms * 128 * smax * 1e6 / 1e12
+    fma_peak = pipes["fma_ops"] / 1e12
     fwd_ms = stage["raster"][0] / max(1, stage["raster"][1])
     bwd_ms = stage["raster_bwd"][0] / max(1, stage["raster_bwd"][1])
     if fwd_ms >= bwd_ms:
-        dom, dom_ms, ops = "raster_fwd", fwd_ms, stats["n_evals"] * OPS_PER_EVAL
+        dom, dom_ms, units = "raster_fwd", fwd_ms, stats["n_evals"]
+        ops_unit, xu_unit = OPS_PER_EVAL, XU_PER_EVAL
     else:
-        # the list kernel re-evaluates each composited pair and chains its gradient
-        dom, dom_ms, ops = "raster_bwd", bwd_ms, stats["n_emitted"] * (OPS_PER_EVAL + OPS_PER_EMIT_BWD)
-    achieved = ops / (dom_ms / 1e3) / 1e12
+        # the records kernel re-evaluates each composited pair and chains its gradient
+        dom, dom_ms, units = "raster_bwd", bwd_ms, stats["n_emitted"]
+        ops_unit, xu_unit = OPS_PER_EVAL + OPS_PER_EMIT_BWD, XU_PER_EVAL
+    achieved = units * ops_unit / (dom_ms / 1e3) / 1e12
+    # seconds per transcendental op of the evaluation's mix (2 ex2, 2 rcp, 1 cos)
+    xu_s_per_unit = 2.0 / pipes["ex2_ops"] + 2.0 / pipes["rcp_ops"] + 1.0 / pipes["cos_ops"]
+    xu_peak = xu_unit / xu_s_per_unit / 1e12
+    xu_achieved = units * xu_unit / (dom_ms / 1e3) / 1e12
+    roof_ms = 1e3 * max(units * ops_unit / pipes["fma_ops"], units * xu_s_per_unit)
     sm_load = float(clocks.get("sm_mhz") or smax)
-    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tops, "unit": "Top/s",
-                "frac": achieved / peak_tops, "traffic": raster_traffic(args.workload) if dom == "raster_fwd" else None,
-                "peak_basis": f"{sms} SMs x 128 FP32 lanes x {smax:.0f} MHz (max SM clock, MEASURED_PEAKS.json)",
-                "frac_at_load_clock": achieved / (sms * 128 * sm_load * 1e6 / 1e12),
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fma_peak, "unit": "Top/s",
+                "frac": achieved / fma_peak, "traffic": raster_traffic(args.workload) if dom == "raster_fwd" else None,
+                "peak_basis": "FP32 FMA ops/s measured by drk_measure_pipes on this GPU (of measured)",
+                "ops_per_unit": ops_unit, "units": units,
+                "xu": {"achieved": xu_achieved, "peak": xu_peak, "unit": "Top/s", "frac": xu_achieved / xu_peak,
+                       "ops_per_unit": xu_unit, "peak_basis": "2 ex2 + 2 rcp + 1 cos at the measured MUFU rates"},
+                "roofline_time_ms": roof_ms, "roofline_frac": roof_ms / dom_ms,
+                "nominal_fma_peak": sms * 128 * smax * 1e6 / 1e12,
+                "measured_pipes_tops": {k: v / 1e12 for k, v in pipes.items() if k.endswith("_ops")},
                 "load_clock_mhz": sm_load}
+    # HBM-bound stages: algorithmic bytes per launch over their event times
+    hbm = float(peaks.get("hbm_gbs") or 6800.0)
+    P, N, K = stats["n_pairs"], scene.n, scene.K
+    rec_b = 4 * (24 + 4 * (8 if K <= 8 else 16))
+    bnd_b = 4 * (((10 + (8 if K <= 8 else 16) + 3) + 3) // 4 * 4)
+    par_b = 4 * (3 + 4 + 2 * K + 3 + 3 * (scene.sh_degree + 1) ** 2)
+    stage_bytes = {
+        # 4 passes of 8-bit digits: keys and values read and written; tile ranges read the keys
+        "sort": 4 * P * 16 + 4 * P,
+        # parameters read; raster record, culling bound and colour written; the
+        # culling count reads record and bound and writes a count; scan of the counts
+        "preprocess": N * (par_b + rec_b + bnd_b + 12) + N * (rec_b + bnd_b + 4) + N * 12,
+        # record and bound read per primitive; (key, value) written per pair
+        "emit": N * (rec_b + bnd_b) + P * 8,
+    }
+    hbm_stages = {}
+    for k, b in stage_bytes.items():
+        if stage.get(k, (0, 0))[1]:
+            ms_k = stage[k][0] / stage[k][1]
+            gbs = b / (ms_k / 1e3) / 1e9
+            hbm_stages[k] = {"bytes": b, "ms": ms_k, "achieved_gbs": gbs, "peak_gbs": hbm, "frac": gbs / hbm}
 
     # ---- end to end through the public API with host buffers
     e2e = None
@@ -363,7 +402,8 @@ def run_drk(args):
                            "step": "render + L1-loss gradient + backward to all parameters",
                            "l2": "flushed between timed steps (256 MiB write)",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "roofline": roofline, "hbm_stages": hbm_stages, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches,
                 "clocks": clocks, "step_ms_spread": spread, "statistic": "median step time",
                 "stages_ms": {k: v[0] / max(1, v[1]) for k, v in stage.items() if v[1]},
                 "counters": {k: stats[k] for k in ("n_pairs", "n_evals", "n_geo_evals", "n_contrib_evals", "n_emitted",
@@ -603,13 +643,51 @@ def serve_run(D, torch, dscenes, reqs, max_batch: int, budget: int) -> dict:
                 time.sleep(dt)
             tickets.append(srv.submit(ids[sid], cam, o))
         tm = [srv.wait(t, 600000) for t in tickets]
+        tl = [srv.timeline(t, 600000) for t in tickets]
     bad = [t["status"] for t in tm if t["status"] != 0]
+    overlap = batch_overlap(tl)
     lat = np.array([t["end_ms"] - t["arrival_ms"] for t in tm])
     span_ms = max(t["end_ms"] for t in tm) - min(t["arrival_ms"] for t in tm)
     px = sum(c.width * c.height for _, _, c in reqs)
     return {"max_batch": max_batch, "frames_per_s": len(reqs) / (span_ms / 1e3), "Mpix_per_s": px / (span_ms / 1e3) / 1e6,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "mean_batch": float(np.mean([t["batch_size"] for t in tm])), "failed": len(bad)}
+            "mean_batch": float(np.mean([t["batch_size"] for t in tm])), "failed": len(bad), "overlap": overlap}
+
+
+def batch_overlap(timelines) -> dict:
+    """Device-timeline evidence of overlap between batches: for every batch,
+    the share of its phases A and B (preprocess, culling, emission, sort)
+    that ran while a batch on the other stream was rasterising, and how
+    much of the total device time two batches were active at once."""
+    batches = {}
+    for t in timelines:
+        if t["status"] == 0 and t["dev_r1_ms"] > 0:
+            batches[(t["stream"], t["dev_a0_ms"])] = (t["dev_a0_ms"], t["dev_b1_ms"], t["dev_r1_ms"], t["stream"])
+    bl = sorted(batches.values())
+    if not bl:
+        return {}
+    ab_total = ab_over = 0.0
+    for a0, b1, r1, s in bl:
+        ab_total += b1 - a0
+        for a0o, b1o, r1o, so in bl:
+            if so != s:
+                ab_over += max(0.0, min(b1, r1o) - max(a0, b1o))
+    # time with two batches active (any phase) against the span
+    ev = sorted([(a0, 1) for a0, _, _, _ in bl] + [(r1, -1) for _, _, r1, _ in bl])
+    both = busy = 0.0
+    act, last = 0, ev[0][0]
+    for x, d in ev:
+        if act >= 1:
+            busy += x - last
+        if act >= 2:
+            both += x - last
+        act += d
+        last = x
+    return {"batches": len(bl), "phase_ab_ms": ab_total, "phase_ab_under_other_raster_ms": ab_over,
+            "phase_ab_overlap_frac": ab_over / ab_total if ab_total > 0 else 0.0,
+            "device_busy_ms": busy, "two_batches_active_ms": both,
+            "mean_raster_ms": float(np.mean([r1 - b1 for _, b1, r1, _ in bl])),
+            "mean_phase_ab_ms": ab_total / len(bl)}
 
 
 def _wait_release(srv, tk):
@@ -695,12 +773,14 @@ def serve_sweep(args):
         for lam in grid:
             r = run(m, lam)
             runs[m].append({"rate_hz": lam, "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"],
-                            "frames_per_s": r["frames_per_s"], "mean_batch": r["mean_batch"]})
+                            "frames_per_s": r["frames_per_s"], "mean_batch": r["mean_batch"],
+                            "overlap": r.get("overlap")})
             if r["p99_ms"] <= L:
                 best[m] = lam
     print(json.dumps({"metric": "max Poisson arrival rate with p99 latency <= L*", "unit": "requests/s",
                       "impl": "drk-serve", "data": "synthetic", "requests_per_run": nreq,
                       "saturation_frames_per_s": {m: v["frames_per_s"] for m, v in sat.items()},
+                      "saturation_overlap": {m: v.get("overlap") for m, v in sat.items()},
                       "L_star_ms": L, "L_star_rule": "p99 of sequential rendering at half its saturation rate",
                       "max_rate": best, "runs": runs,
                       "config": {"scenes": [s.n for s in scenes], "resolutions": list(synth.SERVE_RESOLUTIONS),

@@ -277,6 +277,21 @@ drk_status_t drk_get_stats(drk_ctx_t *ctx, drk_stats_t *out);
 drk_status_t drk_timing_enable(drk_ctx_t *ctx, int enable);
 drk_status_t drk_timing_read(drk_ctx_t *ctx, double *ms, int64_t *launches);
 
+/* Measured arithmetic throughput of one GPU (operations per second): the
+ * FP32 FMA pipe (an FMA counted as one operation) and the transcendental
+ * unit for ex2.approx, rcp.approx and cos.approx, each from the library's
+ * own kernels with independent dependent chains filling every SM (best of
+ * five timed launches after a warm-up).  A measurement utility: the paper
+ * has no counterpart; the rasterizer's roofline takes these as its peaks
+ * (it is bound by these two units).  Synchronous, about 20 ms; allocates a
+ * few bytes of device memory. */
+typedef struct {
+    double fma_ops, ex2_ops, rcp_ops, cos_ops;
+    int32_t sms;
+    int32_t reserved;
+} drk_pipe_peaks_t;
+drk_status_t drk_measure_pipes(int device, drk_pipe_peaks_t *out);
+
 /* Number of kernel launches the library has issued so far, process-wide
  * (host counter). */
 int64_t drk_launch_count(void);
@@ -310,6 +325,14 @@ typedef struct {
                              the batch's event) */
     int32_t batch_size;   /* requests in its batch */
     int32_t status;       /* drk_status_t of the request */
+    /* device timeline of its batch (CUDA events on the batch's stream, ms
+     * since an event recorded when the server was created; 0 until the
+     * whole batch has finished): phase A (preprocess, culling count, scan)
+     * began, phase A ended, phase B (emission, sort, tile ranges, batch
+     * tile order) ended = the batch raster began, the raster ended */
+    double dev_a0_ms, dev_a1_ms, dev_b1_ms, dev_r1_ms;
+    int32_t stream;       /* the server stream (0 or 1) the batch ran on */
+    int32_t reserved;
 } drk_serve_timing_t;
 
 /* device: CUDA ordinal; mem_budget: device bytes the in-flight batches may

@@ -18,7 +18,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libdrk.so")
-SOURCES = ["api.cu", "preprocess.cu", "sort.cu", "raster.cu", "noalloc.cu", "serve.cu", "train.cu", "mesh.cu"]
+SOURCES = ["api.cu", "preprocess.cu", "sort.cu", "raster.cu", "noalloc.cu", "serve.cu", "train.cu", "mesh.cu",
+           "peaks.cu"]
 # The pair count and pair emission kernels must take identical culling
 # decisions; without FMA contraction both compile to the same arithmetic.
 FILE_FLAGS = {"preprocess.cu": ["-fmad=false"]}

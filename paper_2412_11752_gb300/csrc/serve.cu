@@ -98,6 +98,10 @@ struct drk_serve {
     size_t ovf_bytes[kStreams] = {0, 0};
     cudaEvent_t ev_phase_a[kStreams] = {nullptr, nullptr};
     cudaEvent_t ev_done[kStreams] = {nullptr, nullptr};
+    // device timeline of the running batch per stream: phase A begin / end,
+    // phase B end (raster begin), raster end; times against ev_ref
+    cudaEvent_t ev_tl[kStreams][4] = {{nullptr, nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr, nullptr}};
+    cudaEvent_t ev_ref = nullptr;
     std::vector<std::unique_ptr<SceneDev>> scenes;
     std::mutex mu;
     std::condition_variable cv_work;   // worker: new request or stop
@@ -168,6 +172,13 @@ void retire(drk_serve* S, std::unique_ptr<BatchInfo>* info) {
         if (e != cudaSuccess) cudaGetLastError();
         const double t = S->now_ms();
         const int m = (int)b->tickets.size();
+        double tl[4] = {0.0, 0.0, 0.0, 0.0};
+        if (e == cudaSuccess)
+            for (int q = 0; q < 4; q++) {
+                float ms = 0.f;
+                if (cudaEventElapsedTime(&ms, S->ev_ref, S->ev_tl[s][q]) == cudaSuccess) tl[q] = ms;
+                else cudaGetLastError();
+            }
         const unsigned long long* hc = S->h_counters[s];
         const unsigned long long batch_bits = hc[(size_t)kMaxBatch * kCountersPer + 4];
         {
@@ -188,6 +199,11 @@ void retire(drk_serve* S, std::unique_ptr<BatchInfo>* info) {
                     sc.pairs_per_pixel = sc.pairs_per_pixel < 0 ? ppp : std::max(ppp, 0.9 * sc.pairs_per_pixel);
                 }
                 if (!b->early[i]) r.t.end_ms = t;
+                r.t.dev_a0_ms = tl[0];
+                r.t.dev_a1_ms = tl[1];
+                r.t.dev_b1_ms = tl[2];
+                r.t.dev_r1_ms = tl[3];
+                r.t.stream = s;
                 r.done = true;
             }
             S->inflight_bytes -= std::min(S->inflight_bytes, b->bytes);
@@ -298,6 +314,7 @@ void run_batch(drk_serve* S, int s, std::vector<Item>& items, int* countdown, st
         cudaGetLastError();
         for (int i = 0; i < m; i++) { b->ok[i] = 0; status[i] = DRK_ERR_CUDA; }
     }
+    cudaEventRecord(S->ev_tl[s][0], st);
     for (int i = 0; i < m; i++) {
         if (!b->ok[i]) continue;
         unsigned long long* ctr = S->d_counters[s] + (size_t)i * kCountersPer;
@@ -305,6 +322,7 @@ void run_batch(drk_serve* S, int s, std::vector<Item>& items, int* countdown, st
                                              reinterpret_cast<int*>(ctr + 4), S->h_totals[s] + i, st, nullptr);
         if (e != DRK_OK) { b->ok[i] = 0; status[i] = e; }
     }
+    cudaEventRecord(S->ev_tl[s][1], st);
     cudaEventRecord(S->ev_phase_a[s], st);
     if (wait_event_retiring(S, S->ev_phase_a[s], info) != cudaSuccess)
         for (int i = 0; i < m; i++)
@@ -394,6 +412,7 @@ void run_batch(drk_serve* S, int s, std::vector<Item>& items, int* countdown, st
         cudaMemcpyAsync(S->d_slots[s], S->h_slots[s], sizeof(FrameSlot) * (size_t)live, cudaMemcpyHostToDevice, st);
         cudaMemcpyAsync(S->d_left[s], S->h_left[s], sizeof(unsigned int) * (size_t)live, cudaMemcpyHostToDevice, st);
         radix_sort_pairs(okeys, ovals, okalt, ovalt, T, 26, oscr, st);
+        cudaEventRecord(S->ev_tl[s][2], st);
         RasterArgs R;
         std::memset(&R, 0, sizeof(R));
         R.fc = S->h_slots[s][0].fc;
@@ -423,7 +442,10 @@ void run_batch(drk_serve* S, int s, std::vector<Item>& items, int* countdown, st
         R.ovf_slots = R.ovf ? (int)(S->ovf_bytes[s] / raster_ovf_bytes(1)) : 0;
         launch_raster_batch(R, kmax, S->opt.kbuf_capacity, st);
         bs = check_launch();
+    } else {
+        cudaEventRecord(S->ev_tl[s][2], st);
     }
+    cudaEventRecord(S->ev_tl[s][3], st);
     if (bs != DRK_OK)
         for (int i = 0; i < m; i++)
             if (b->ok[i]) { b->ok[i] = 0; status[i] = bs; }
@@ -496,8 +518,11 @@ void free_server(drk_serve* S) {
         if (S->h_done[s]) cudaFreeHost(S->h_done[s]);
         if (S->ev_phase_a[s]) cudaEventDestroy(S->ev_phase_a[s]);
         if (S->ev_done[s]) cudaEventDestroy(S->ev_done[s]);
+        for (int q = 0; q < 4; q++)
+            if (S->ev_tl[s][q]) cudaEventDestroy(S->ev_tl[s][q]);
         if (S->streams[s]) cudaStreamDestroy(S->streams[s]);
     }
+    if (S->ev_ref) cudaEventDestroy(S->ev_ref);
     for (auto& sc : S->scenes) cudaFree(sc->mem);
     if (S->pool) cudaMemPoolDestroy(S->pool);
     delete S;
@@ -563,6 +588,11 @@ drk_status_t drk_serve_create(int device, size_t mem_budget, int max_batch, cons
              cudaHostAlloc(&S->h_done[s], sizeof(unsigned int) * kMaxBatch, cudaHostAllocMapped) == cudaSuccess &&
              cudaHostGetDevicePointer(reinterpret_cast<void**>(&S->d_done[s]), S->h_done[s], 0) == cudaSuccess;
     }
+    for (int s = 0; s < kStreams && ok; s++)
+        for (int q = 0; q < 4 && ok; q++) ok = cudaEventCreate(&S->ev_tl[s][q]) == cudaSuccess;
+    // the device-time origin of the batch timelines
+    ok = ok && cudaEventCreate(&S->ev_ref) == cudaSuccess && cudaEventRecord(S->ev_ref, S->streams[0]) == cudaSuccess &&
+         cudaEventSynchronize(S->ev_ref) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         free_server(S);

@@ -78,9 +78,16 @@ class drk_stats_t(C.Structure):
 _lib = None
 
 
+class drk_pipe_peaks_t(C.Structure):
+    _fields_ = [("fma_ops", C.c_double), ("ex2_ops", C.c_double), ("rcp_ops", C.c_double), ("cos_ops", C.c_double),
+                ("sms", C.c_int32), ("reserved", C.c_int32)]
+
+
 class drk_serve_timing_t(C.Structure):
     _fields_ = [("arrival_ms", C.c_double), ("start_ms", C.c_double), ("end_ms", C.c_double),
-                ("batch_size", C.c_int32), ("status", C.c_int32)]
+                ("batch_size", C.c_int32), ("status", C.c_int32),
+                ("dev_a0_ms", C.c_double), ("dev_a1_ms", C.c_double), ("dev_b1_ms", C.c_double),
+                ("dev_r1_ms", C.c_double), ("stream", C.c_int32), ("reserved", C.c_int32)]
 
 
 def library_path() -> str:
@@ -113,6 +120,8 @@ def lib():
         L.drk_sort_pairs.argtypes = [vp, vp, vp, C.c_int64, C.c_int, vp]
         L.drk_sort_pairs_static.argtypes = [vp, vp, C.c_int64, C.c_int, vp]
         L.drk_sort_pairs_static.restype = C.c_int
+        L.drk_measure_pipes.argtypes = [C.c_int, C.POINTER(drk_pipe_peaks_t)]
+        L.drk_measure_pipes.restype = C.c_int
         L.drk_timing_enable.argtypes = [vp, C.c_int]
         L.drk_timing_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
         L.drk_launch_count.restype = C.c_int64
@@ -242,6 +251,14 @@ class Context:
 
 
 STAGES = ("preprocess", "emit", "sort", "raster", "raster_bwd", "preprocess_bwd", "replay_bwd", "record_sort")
+
+
+def measure_pipes(device: int = 0) -> dict:
+    """Measured FP32 FMA and transcendental (ex2, rcp, cos) throughput of one
+    GPU, operations per second (drk_measure_pipes)."""
+    p = drk_pipe_peaks_t()
+    _check(lib().drk_measure_pipes(int(device), C.byref(p)))
+    return {f: getattr(p, f) for f, _ in drk_pipe_peaks_t._fields_ if f != "reserved"}
 
 
 def launch_count() -> int:
@@ -637,6 +654,20 @@ class Server:
         _check(lib().drk_serve_poll(self.handle, C.c_uint64(ticket), C.byref(done), C.byref(t)))
         return bool(done.value), self._timing(t)
 
+    def timeline(self, ticket: int, timeout_ms: float = 60000.0) -> dict:
+        """The ticket's timing record once its batch's device timeline is
+        filled in (the whole batch has finished; a request can complete
+        before its batch does)."""
+        import time as _time
+        t_end = _time.monotonic() + timeout_ms / 1e3
+        while True:
+            done, t = self.poll(ticket)
+            if done and (t["dev_r1_ms"] > 0.0 or t["status"] != DRK_OK):
+                return t
+            if _time.monotonic() > t_end:
+                raise DrkError(5, "timeline not available")
+            _time.sleep(0.001)
+
     def wait(self, ticket: int, timeout_ms: float = 60000.0) -> dict:
         t = drk_serve_timing_t()
         _check(lib().drk_serve_wait(self.handle, C.c_uint64(ticket), float(timeout_ms), C.byref(t)))
@@ -647,3 +678,107 @@ class Server:
 
     def inject_alloc_failure(self, n: int) -> None:
         _check(lib().drk_serve_inject_alloc_failure(self.handle, int(n)))
+
+
+# ---------------------------------------------------------------------------
+# Request-level replicas for serving.
+
+def least_loaded(loads) -> int:
+    """Index of the smallest load (the first one on ties)."""
+    best = 0
+    for i, v in enumerate(loads):
+        if v < loads[best]:
+            best = i
+    return best
+
+
+class Router:
+    """Request-level serving replicas: one Server per entry of `devices` (a
+    device may appear more than once), every scene resident on each, every
+    request routed to the server with the least outstanding work, counted
+    as pixels x primitives of its unfinished requests.  The router
+    allocates each request's image on its server's device; image(ticket)
+    returns it.  There is no collective and no cross-device traffic: the
+    replicas share nothing.
+
+    make_server(device) builds a server (default: Server(device,
+    mem_budget, max_batch, opt)); tests pass a stand-in."""
+
+    def __init__(self, devices, mem_budget: int = 8 << 30, max_batch: int = 16, opt: Options | None = None,
+                 make_server=None):
+        self.devices = [int(d) for d in devices]
+        if not self.devices:
+            raise DrkError(1, "no devices")
+        make = make_server or (lambda d: Server(d, mem_budget=mem_budget, max_batch=max_batch, opt=opt))
+        self.servers = [make(d) for d in self.devices]
+        self.scene_ids = []          # per scene: its id on every server
+        self.scene_n = []            # primitives per scene
+        self.load = [0.0] * len(self.servers)
+        self.open = {}               # router ticket -> (server index, server ticket, cost, image)
+        self.next = 1
+
+    def close(self):
+        for s in self.servers:
+            s.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def add_scene(self, scene) -> int:
+        """scene: a DeviceScene (copied to each server's device as needed) or
+        a host scene with float32 arrays."""
+        ids = []
+        for srv, dev in zip(self.servers, self.devices):
+            if isinstance(scene, DeviceScene):
+                ds = scene if scene.mu.device == torch.device("cuda", dev) else DeviceScene(
+                    **{k: v.to(torch.device("cuda", dev)) for k, v in scene.tensors().items()},
+                    sh_degree=scene.sh_degree)
+            else:
+                ds = DeviceScene.from_scene(scene, torch.device("cuda", dev))
+            ids.append(srv.add_scene(ds))
+        self.scene_ids.append(ids)
+        self.scene_n.append(int(scene.n if isinstance(scene, DeviceScene) else np.shape(scene.mu)[0]))
+        return len(self.scene_ids) - 1
+
+    def _reap(self):
+        """Drops finished requests from the loads."""
+        for tk, (si, st, cost, _img) in list(self.open.items()):
+            if cost > 0.0 and self.servers[si].poll(st)[0]:
+                self.load[si] -= cost
+                self.open[tk] = (si, st, 0.0, _img)
+
+    def submit(self, scene: int, cam) -> int:
+        self._reap()
+        si = least_loaded(self.load)
+        dev = self.devices[si]
+        img = torch.empty((3, int(cam.height), int(cam.width)), dtype=torch.float32, device=torch.device("cuda", dev))
+        st = self.servers[si].submit(self.scene_ids[scene][si], cam, img)
+        cost = float(cam.width) * float(cam.height) * max(1, self.scene_n[scene])
+        self.load[si] += cost
+        tk = self.next
+        self.next += 1
+        self.open[tk] = (si, st, cost, img)
+        return tk
+
+    def server_of(self, ticket: int) -> int:
+        return self.open[ticket][0]
+
+    def wait(self, ticket: int, timeout_ms: float = 60000.0) -> dict:
+        si, st, cost, img = self.open[ticket]
+        t = self.servers[si].wait(st, timeout_ms)
+        if cost > 0.0:
+            self.load[si] -= cost
+            self.open[ticket] = (si, st, 0.0, img)
+        return t
+
+    def image(self, ticket: int) -> torch.Tensor:
+        return self.open[ticket][3]
+
+    def release(self, ticket: int) -> None:
+        si, st, cost, _ = self.open.pop(ticket)
+        if cost > 0.0:
+            self.load[si] -= cost
+        self.servers[si].release(st)

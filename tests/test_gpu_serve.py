@@ -154,3 +154,47 @@ def test_wait_timeout_and_argument_errors(drk):
         with pytest.raises(drk.DrkError) as e:
             srv.submit(sid, bad, torch.zeros((3, 8, 8), device="cuda"))
         assert e.value.code == INVALID
+
+
+def test_served_images_match_the_oracle_at_serving_resolutions(drk):
+    # a mixed batch of 640 x 480 and 3840 x 2160 requests (and one 1280 x
+    # 720) over two resident scenes, rendered by the batch raster; sampled
+    # pixels plus two whole tiles of every request against the FP64 oracle
+    from helpers import image_parity, oracle_options
+    from oracle import drk_oracle as O
+    hs = [synth.scene_clustered(20000, 8, seed=4201), synth.scene_clustered(20000, 8, seed=4202, n_clusters=40)]
+    ds = [drk.DeviceScene.from_scene(s, "cuda") for s in hs]
+    rng = np.random.default_rng(4203)
+    reqs = [(i % 2, synth.camera_on_sphere(rng, *wh))
+            for i, wh in enumerate([(640, 480), (3840, 2160), (640, 480), (3840, 2160), (1280, 720)])]
+    opt = drk.Options()
+    with drk.Server(0, mem_budget=16 << 30, max_batch=8, opt=opt) as srv:
+        ids = [srv.add_scene(d) for d in ds]
+        outs = [torch.full((3, c.height, c.width), float("nan"), device="cuda") for _, c in reqs]
+        tickets = [srv.submit(ids[sid], cam, o) for (sid, cam), o in zip(reqs, outs)]
+        timings = [srv.wait(t, 120000) for t in tickets]
+    assert max(t["batch_size"] for t in timings) > 1
+    for k, ((sid, cam), o, t) in enumerate(zip(reqs, outs, timings)):
+        assert t["status"] == 0
+        tx, ty = (cam.width + 15) // 16, (cam.height + 15) // 16
+        pix = synth.pixel_sample(cam.width, cam.height, 512, seed=4300 + k, tiles=[(tx // 2, ty // 2), (tx - 1, ty - 1)])
+        ref = O.render_pixels(hs[sid], cam, oracle_options(opt), pix)
+        img = o.cpu().numpy()
+        image_parity(img[:, pix[:, 1], pix[:, 0]], ref, 2, f"served {cam.width}x{cam.height}")
+
+
+def test_batch_device_timeline(drk, scenes):
+    # every request reports its batch's device timeline: phase A, phase B
+    # and the raster in order, on one of the two server streams
+    _, ds = scenes
+    reqs = _requests(16, seed=79, n_scenes=len(ds))
+    with drk.Server(0, mem_budget=4 << 30, max_batch=4) as srv:
+        ids = [srv.add_scene(d) for d in ds]
+        outs = [torch.empty((3, c.height, c.width), device="cuda") for _, c in reqs]
+        tickets = [srv.submit(ids[sid], cam, o) for (sid, cam), o in zip(reqs, outs)]
+        for t in tickets:
+            srv.wait(t, 60000)
+        tl = [srv.timeline(t, 60000) for t in tickets]
+    for t in tl:
+        assert t["status"] == 0 and t["stream"] in (0, 1)
+        assert 0.0 < t["dev_a0_ms"] <= t["dev_a1_ms"] <= t["dev_b1_ms"] <= t["dev_r1_ms"]
