@@ -676,9 +676,14 @@ __device__ __forceinline__ float tile_depth_bound(const float* __restrict__ rec,
     return keep_f ? tile_lb : fmaxf(tile_lb, bnd[B_ZLB]);
 }
 
-// Does primitive i take the row-interval test?
+// Does primitive i take the row-interval test?  Only when its rectangle
+// holds more tiles than one warp tests at once: below that the per-tile
+// test costs less than building the pieces.  (Either test is conservative;
+// the count and the emission take the same choice.)
 __device__ __forceinline__ bool row_culled(const PreArgs& A, const float* __restrict__ bnd) {
-    return A.cull_level == DRK_CULL_TILE && !(reinterpret_cast<const int*>(bnd)[B_FLAGS] & 2);
+    const int* bi = reinterpret_cast<const int*>(bnd);
+    const int area = (bi[B_X1] - bi[B_X0] + 1) * (bi[B_Y1] - bi[B_Y0] + 1);
+    return A.cull_level == DRK_CULL_TILE && !(bi[B_FLAGS] & 2) && area > 32;
 }
 
 constexpr int kCullThreads = 256;

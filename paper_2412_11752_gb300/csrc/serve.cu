@@ -8,7 +8,8 @@
 //   phase A per request   preprocess, culling count, scan (pair totals -> host)
 //   wait for the totals   (the worker keeps retiring the other stream's batch)
 //   phase B per request   emission, radix sort, tile ranges
-//   batch tile order      frame by frame, heaviest tile first within a frame
+//   batch tile order      frame by frame (heaviest frame first), heaviest
+//                         tile first within a frame
 //   one raster launch     persistent warps over every tile of every frame
 // and records a completion event.  The next batch's phases A/B run on the
 // other stream while this raster runs.  Each pixel's arithmetic and
@@ -385,10 +386,16 @@ void run_batch(drk_serve* S, int s, std::vector<Item>& items, int* countdown, st
         if (bs == DRK_OK) bs = b->al->get(&oscr, radix_sort_scratch_bytes(T));
     }
     if (live > 0 && bs == DRK_OK) {
+        // frames in decreasing pair count: the raster finishes the heaviest
+        // frames of the batch first (they set the tail latency; the light
+        // ones have slack)
+        std::vector<int> order;
+        for (int i = 0; i < m; i++)
+            if (b->ok[i]) order.push_back(i);
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return W[x].P > W[y].P; });
         int slot = 0;
         int64_t off = 0;
-        for (int i = 0; i < m; i++) {
-            if (!b->ok[i]) continue;
+        for (int i : order) {
             const FrameWork& w = W[i];
             launch_batch_order_keys(w.ranges, w.F.n_tiles, slot, okeys + off, ovals + off, st);
             FrameSlot& fs = S->h_slots[s][slot];
