@@ -94,15 +94,15 @@ struct drk_state {
     int K = 0, kmax = 0, cap = 0, sh_degree = 0, width = 0, height = 0;
     FrameConst fc{};
     float* rec = nullptr;
-    float* rgb = nullptr;
+    float4* rgb = nullptr;
     uint32_t* keys = nullptr;
     uint32_t* vals = nullptr;
     uint2* ranges = nullptr;
     uint32_t* tile_order = nullptr;
     DepthQuant* dq = nullptr;
     float* Cfin = nullptr;
-    uint32_t* rec_key = nullptr;
-    uint32_t* rec_pix = nullptr;
+    uint2* rec_kp = nullptr;
+    uint32_t* rec_count = nullptr;
     float4* rec_tp = nullptr;
     uint32_t rec_cap = 0;
     unsigned int* rec_chunks = nullptr;       // device: chunks this forward took
@@ -260,7 +260,7 @@ drk_status_t frame_phase_a(FrameWork& w, const drk_params_t* params, const drk_c
     drk_status_t s;
     if ((s = al.get(&A.rec, (size_t)n * rec_floats(F.kmax))) != DRK_OK) return s;
     if ((s = al.get(&A.bnd, (size_t)n * bnd_floats(F.kmax))) != DRK_OK) return s;
-    if ((s = al.get(&A.rgb, (size_t)n * 3)) != DRK_OK) return s;
+    if ((s = al.get(&A.rgb, (size_t)n)) != DRK_OK) return s;
     if ((s = al.get(&A.count, (size_t)n + 1)) != DRK_OK) return s;
     if ((s = al.get(&A.offsets, (size_t)n + 1)) != DRK_OK) return s;
     if ((s = al.get(&A.zmax_bits, 1)) != DRK_OK) return s;
@@ -463,10 +463,10 @@ drk_status_t drk_render(drk_ctx_t* ctx, const drk_params_t* params, const drk_ca
         if (opt->record_chunks > 0) chunks = std::min<uint64_t>(chunks, (uint64_t)opt->record_chunks);
         R.rec_cap = (uint32_t)(chunks * kRecChunk);
         R.rec_ctr = ctx->rec_ctr;
-        if ((s = al.get(&R.rec_key, (size_t)R.rec_cap)) != DRK_OK) return s;
-        if ((s = al.get(&R.rec_pix, (size_t)R.rec_cap)) != DRK_OK) return s;
+        if ((s = al.get(&R.rec_kp, (size_t)R.rec_cap)) != DRK_OK) return s;
+        if ((s = al.get(&R.rec_count, (size_t)w.P + 1)) != DRK_OK) return s;
         if ((s = al.get(&R.rec_tp, (size_t)R.rec_cap)) != DRK_OK) return s;
-        DRK_CUDA(cudaMemsetAsync(R.rec_key, 0xff, sizeof(uint32_t) * (size_t)R.rec_cap, st));
+        DRK_CUDA(cudaMemsetAsync(R.rec_count, 0, sizeof(uint32_t) * ((size_t)w.P + 1), st));
         DRK_CUDA(cudaMemsetAsync(ctx->rec_ctr, 0, sizeof(unsigned int), st));
         if ((s = al.get(&R.tile_overflow, (size_t)F.n_tiles)) != DRK_OK) return s;
         DRK_CUDA(cudaMemsetAsync(R.tile_overflow, 0, sizeof(int32_t) * (size_t)F.n_tiles, st));
@@ -503,8 +503,8 @@ drk_status_t drk_render(drk_ctx_t* ctx, const drk_params_t* params, const drk_ca
         S->ranges = w.ranges;
         S->tile_order = w.tile_order;
         S->dq = A.dq;
-        S->rec_key = R.rec_key;
-        S->rec_pix = R.rec_pix;
+        S->rec_kp = R.rec_kp;
+        S->rec_count = R.rec_count;
         S->rec_tp = R.rec_tp;
         S->rec_cap = R.rec_cap;
         S->tile_overflow = R.tile_overflow;
@@ -584,27 +584,29 @@ drk_status_t drk_render_backward(drk_ctx_t* ctx, const drk_params_t* params, con
     R.Cfin = state->Cfin;
     R.gtmp = gtmp;
     R.grads = *grads;
-    R.rec_key = state->rec_key;
-    R.rec_pix = state->rec_pix;
+    R.rec_kp = state->rec_kp;
+    R.rec_count = state->rec_count;
     R.rec_tp = state->rec_tp;
     R.rec_cap = state->rec_cap;
     R.tile_overflow = state->tile_overflow;
     attach_ovf(ctx, opt, F.kmax, state->cap, true, F.n_tiles, st, R);
 
-    // records taken by the forward (one readback; the sort is sized by it)
+    // records taken by the forward (one readback; the grouping is sized by it)
     DRK_CUDA(cudaMemcpyAsync(ctx->h_total + 2, state->rec_chunks, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
     DRK_CUDA(cudaStreamSynchronize(st));
-    const uint64_t nrec = std::min<uint64_t>((uint64_t)(uint32_t)ctx->h_total[2] * kRecChunk, state->rec_cap);
-    // records grouped by list pair: counting sort over the pair index
-    uint32_t *skey = nullptr, *sslot = nullptr;
+    const uint64_t taken = (uint64_t)(uint32_t)ctx->h_total[2] * kRecChunk;
+    const uint64_t nrec = std::min<uint64_t>(taken, state->rec_cap);
+    // a chunk request beyond the pool sent tiles to the replay
+    R.any_overflow = taken > state->rec_cap ? 1 : 0;
+    // records grouped by list pair, from the per-pair counts of the forward
+    uint32_t* sslot = nullptr;
     uint8_t* sort_scr = nullptr;
     const uint32_t n_keys = (uint32_t)state->pairs;
-    if ((s = al.get(&skey, (size_t)nrec)) != DRK_OK) return s;
     if ((s = al.get(&sslot, (size_t)nrec)) != DRK_OK) return s;
-    if ((s = al.get(&sort_scr, counting_sort_scratch_bytes(n_keys))) != DRK_OK) return s;
+    if ((s = al.get(&sort_scr, record_sort_scratch_bytes(n_keys))) != DRK_OK) return s;
     StageTimer& tm = ctx->timer;
     cudaEvent_t ev = tm.begin(st);
-    counting_sort_keys(state->rec_key, (uint32_t)nrec, n_keys, skey, sslot, sort_scr, st);
+    group_records(state->rec_kp, (uint32_t)nrec, n_keys, state->rec_count, sslot, sort_scr, st);
     tm.end(ST_REC_SORT, ev, st);
     ev = tm.begin(st);
     float4* pixg = nullptr;
@@ -612,7 +614,7 @@ drk_status_t drk_render_backward(drk_ctx_t* ctx, const drk_params_t* params, con
     if ((s = al.get(&pixg, 2 * npix)) != DRK_OK) return s;
     launch_pack_pixel_grad(R.dL, R.Cfin, npix, pixg, st);
     R.pixg = pixg;
-    launch_raster_backward_records(R, skey, sslot, (uint32_t)nrec, F.kmax, st);
+    launch_raster_backward_records(R, sslot, (uint32_t)nrec, F.kmax, st);
     tm.end(ST_RASTER_BWD, ev, st);
     ev = tm.begin(st);
     launch_raster(R, F.kmax, state->cap, true, st);      // exact replay of the others

@@ -28,7 +28,7 @@ struct PreArgs {
     int depth_bits;
     float* rec;             // n x Rec<KMAX>::STRIDE
     float* bnd;             // n x Bnd<KMAX>::STRIDE
-    float* rgb;             // n x 3 view-dependent colour
+    float4* rgb;            // n view-dependent colours (r, g, b, 0)
     uint32_t* count;        // n pairs per primitive
     uint64_t* offsets;      // n + 1 exclusive scan of count
     int* zmax_bits;         // max ray depth of any bound (float bits)
@@ -45,7 +45,7 @@ struct PreArgs {
 struct FrameSlot {
     FrameConst fc;
     const float* rec;
-    const float* rgb;
+    const float4* rgb;
     const uint32_t* keys;
     const uint32_t* vals;
     const uint2* ranges;
@@ -61,7 +61,7 @@ struct RasterArgs {
     FrameConst fc;
     int K;
     const float* rec;
-    const float* rgb;
+    const float4* rgb;
     const uint32_t* keys;
     const uint32_t* vals;
     const uint2* ranges;
@@ -89,17 +89,20 @@ struct RasterArgs {
     float* out_normal;     // 3 x H x W sum of T alpha n (camera frame, towards the camera)
     // contributor records written by the forward for the backward (may be
     // null): one per composited contributor, in rec_cap slots handed out in
-    // chunks of kRecChunk; rec_key = global pair index (ranges[tile].x + list
-    // position; kNoSlot for an unused slot), rec_pix = y * width + x,
-    // rec_tp = (T before the contributor, composited colour after it).
-    // tile_overflow[tile] != 0 if a record did not fit (the backward replays
-    // that tile exactly)
-    uint32_t* rec_key;               // filled with kNoSlot before the forward
-    uint32_t* rec_pix;
+    // chunks of kRecChunk; rec_kp = (global pair index ranges[tile].x + list
+    // position, pixel y * width + x), x = kNoSlot for a slot left unused (the
+    // raster marks the unused tail of each warp's last chunk),
+    // rec_tp = (T before the contributor, composited colour after it);
+    // rec_count[pair] counts the records of each pair (zeroed before the
+    // forward).  tile_overflow[tile] != 0 if a record did not fit (the
+    // backward replays that tile exactly)
+    uint2* rec_kp;
     float4* rec_tp;
+    uint32_t* rec_count;
     uint32_t rec_cap;
     unsigned int* rec_ctr;           // chunks taken (zeroed before the forward)
     int32_t* tile_overflow;
+    int any_overflow;                // backward: some record did not fit
     // backward
     drk_params_t p;
     const float* dL;
@@ -147,18 +150,19 @@ void launch_raster(const RasterArgs& A, int kmax, int cap, bool bwd, cudaStream_
 // and the bytes of the overflow columns of `slots` warps
 int raster_slots(int kmax, int cap, bool bwd, bool batch, int n_tiles);
 size_t raster_ovf_bytes(int slots);
-// backward over n records sorted by key (skey, with their slots sslot)
+// backward over n record slots grouped by pair (sslot; kNoSlot entries skipped)
 void launch_pack_pixel_grad(const float* dL, const float* Cfin, size_t npix, float4* out, cudaStream_t st);
-void launch_raster_backward_records(const RasterArgs& A, const uint32_t* skey, const uint32_t* sslot, uint32_t n,
-                                    int kmax, cudaStream_t st);
+void launch_raster_backward_records(const RasterArgs& A, const uint32_t* sslot, uint32_t n, int kmax,
+                                    cudaStream_t st);
 // v[i] = i for i < n
 void launch_iota(uint32_t* v, uint32_t n, cudaStream_t st);
-// counting sort of n keys below n_keys (others dropped): out_keys/out_idx
-// hold the kept keys grouped by key (order within a key unspecified) and
-// their input positions, then kNoSlot
-size_t counting_sort_scratch_bytes(uint32_t n_keys);
-void counting_sort_keys(const uint32_t* keys, uint32_t n, uint32_t n_keys, uint32_t* out_keys, uint32_t* out_idx,
-                        void* scratch, cudaStream_t st);
+// records grouped by pair: out_idx[0 .. total) holds the slots of the n
+// records whose pair is below n_keys (others, kNoSlot, dropped), grouped by
+// pair (order within a pair unspecified), from the per-pair counts the
+// forward took; then kNoSlot up to n
+size_t record_sort_scratch_bytes(uint32_t n_keys);
+void group_records(const uint2* kp, uint32_t n, uint32_t n_keys, const uint32_t* count, uint32_t* out_idx,
+                   void* scratch, cudaStream_t st);
 // batched forward over A.n_batch_tiles tiles of the frames in A.slots
 void launch_raster_batch(const RasterArgs& A, int kmax, int cap, cudaStream_t st);
 

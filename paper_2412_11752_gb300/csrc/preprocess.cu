@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(128) preprocess_kernel(PreArgs A) {
             rgb[c] = fmaxf(acc, 0.f);
         }
     }
-    for (int c = 0; c < 3; c++) A.rgb[3 * i + c] = rgb[c];
+    A.rgb[i] = make_float4(rgb[0], rgb[1], rgb[2], 0.f);
 
     // ---- conservative screen bound
     int flags = 0;

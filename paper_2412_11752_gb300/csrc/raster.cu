@@ -342,9 +342,12 @@ struct RecChunk {
 };
 
 // Called by all 32 lanes: takes the next chunk of kRecChunk record slots
-// from the pool (one atomic per chunk).  When the pool is exhausted the
-// chunk stays empty and the tile is marked for the exact replay.
+// from the pool (one atomic per chunk).  The slots left in the previous
+// chunk are marked unused first (the pool is not cleared).  When the pool
+// is exhausted the chunk stays empty and the tile is marked for the exact
+// replay.
 __device__ __forceinline__ void take_record_chunk(const RasterArgs& A, RecChunk& rc, int tile) {
+    for (uint32_t q = rc.base + (threadIdx.x & 31); q < rc.end; q += 32) A.rec_kp[q] = make_uint2(kNoSlot, 0u);
     uint32_t c = 0;
     if ((threadIdx.x & 31) == 0) c = atomicAdd(A.rec_ctr, 1u);
     c = __shfl_sync(0xffffffffu, c, 0);
@@ -367,7 +370,7 @@ struct WarpCounters {
 // `tile` in the frame (fc, rec, rgb, vals, keys, ranges, dq, out).
 template <int KMAX, int CAP, bool BWD, bool AUX>
 __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& fc, const float* __restrict__ recp,
-                                         const float* __restrict__ rgbp, const uint32_t* __restrict__ valsp,
+                                         const float4* __restrict__ rgbp, const uint32_t* __restrict__ valsp,
                                          const uint32_t* __restrict__ keysp, const uint2* __restrict__ rangesp,
                                          const DepthQuant* __restrict__ dqp, float* __restrict__ outp, bool batched,
                                          int K, int tile, uint32_t task, float4* stage, float* ring, uint4* ovf,
@@ -409,7 +412,7 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
         }
     }
     // contributor records for the backward
-    const bool rec_on = !BWD && A.rec_key != nullptr;
+    const bool rec_on = !BWD && A.rec_kp != nullptr;
     const bool literal = fc.order_mode == DRK_ORDER_CACHE_SORT;
     kb.init(ring + threadIdx.x, reinterpret_cast<uint32_t*>(ring) + CAP * kRasterThreads + threadIdx.x,
             ring + 2 * CAP * kRasterThreads + threadIdx.x, literal ? nullptr : ovf, A.ovf_cap, list);
@@ -432,16 +435,20 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
     const float fxp = AUX ? 1.f / fc.ifx : 0.f, fyp = AUX ? 1.f / fc.ify : 0.f;
 
     // composites contributor (r_t t, alpha a, list position p); `slot` is its
-    // record slot (kNoSlot: not recorded)
-    auto composite = [&](float t, float a, uint32_t p, uint32_t slot) {
+    // record slot (kNoSlot: not recorded).  Returns the pair index recorded
+    // (kNoSlot: none)
+    auto composite = [&](float t, float a, uint32_t p, uint32_t slot) -> uint32_t {
         const float Tn = __fmul_rn(ps.T, __fsub_rn(1.f, a));
         if (Tn < fc.T_min) {
+            // the pixel stops here: its slot of this round stays unused
+            if (!BWD && slot != kNoSlot) A.rec_kp[slot] = make_uint2(kNoSlot, 0u);
             ps.done = true;
-            return;
+            return kNoSlot;
         }
         const uint32_t idx = __ldg(list + p);
-        const float col[3] = {__ldg(rgbp + 3 * (size_t)idx), __ldg(rgbp + 3 * (size_t)idx + 1),
-                              __ldg(rgbp + 3 * (size_t)idx + 2)};
+        const float4 c4 = __ldg(rgbp + idx);
+        const float col[3] = {c4.x, c4.y, c4.z};
+        uint32_t recorded = kNoSlot;
         const float wgt = __fmul_rn(a, ps.T);
         if (AUX) {
             const float* h = recp + (size_t)Rec<KMAX>::STRIDE * idx;
@@ -459,8 +466,8 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
             if (slot != kNoSlot) {
                 // read only by the backward: streaming stores keep them from
                 // evicting the primitive records this kernel re-reads from L2
-                __stcs(A.rec_key + slot, rg.x + p);
-                __stcs(A.rec_pix + slot, (uint32_t)pix);
+                recorded = rg.x + p;
+                __stcs(A.rec_kp + slot, make_uint2(recorded, (uint32_t)pix));
                 __stcs(A.rec_tp + slot, make_float4(T_i, ps.C[0], ps.C[1], ps.C[2]));
             }
         } else {
@@ -478,9 +485,10 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
         }
         ps.T = Tn;
         ps.n_emit++;
+        return recorded;
     };
     // composites the root of this lane's heap
-    auto emit_front = [&](uint32_t slot) { composite(kb.front_t(), kb.front_a(), kb.front_p(), slot); };
+    auto emit_front = [&](uint32_t slot) { return composite(kb.front_t(), kb.front_a(), kb.front_p(), slot); };
 
     // a contributor with key kk at list position j
     auto offer = [&](float t, uint32_t j, float a, uint64_t kk) {
@@ -539,9 +547,16 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
                     rc.base += cnt;
                 }
             }
+            uint32_t rk = kNoSlot;
             if (want) {
-                emit_front(slot);
+                rk = emit_front(slot);
                 if (!ps.done) kb.pop();
+            }
+            if (rec_on) {
+                // records per pair, one atomic per group of lanes that
+                // composited the same pair in this round
+                const unsigned peers = __match_any_sync(0xffffffffu, rk);
+                if (rk != kNoSlot && lane == __ffs(peers) - 1) atomicAdd(A.rec_count + rk, (uint32_t)__popc(peers));
             }
         }
         // nothing left below the smallest dropped key can come before thr
@@ -752,6 +767,9 @@ __global__ void __launch_bounds__(kRasterThreads, (BATCH || CAP >= 16) ? 4 : 5) 
                                      task, stage, ring, ovf, kb, wc, rc);
         }
     }
+    // the unused tail of the warp's last record chunk holds no record
+    if (!BWD && !BATCH && A.rec_kp)
+        for (uint32_t q = rc.base + lane; q < rc.end; q += 32) A.rec_kp[q] = make_uint2(kNoSlot, 0u);
     // counters: one atomic per warp
     if (A.counters) {
         for (int o = 16; o > 0; o >>= 1) {
@@ -804,13 +822,16 @@ __device__ __forceinline__ float seg_sum(float v, int start) {
 }
 
 template <int KMAX>
-__global__ void __launch_bounds__(256) raster_backward_records_kernel(RasterArgs A, const uint32_t* __restrict__ skey,
-                                                                      const uint32_t* __restrict__ sslot, uint32_t n) {
+__global__ void __launch_bounds__(256) raster_backward_records_kernel(RasterArgs A, const uint32_t* __restrict__ sslot,
+                                                                      uint32_t n) {
     const int lane = threadIdx.x & 31;
     const FrameConst& fc = A.fc;
     const int K = A.K;
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    uint32_t g = i < n ? skey[i] : kNoSlot;
+    const uint32_t slot = i < n ? sslot[i] : kNoSlot;
+    uint2 kp = make_uint2(kNoSlot, 0u);
+    if (slot < A.rec_cap) kp = A.rec_kp[slot];
+    uint32_t g = kp.x;
     PairGrad pg;
 #pragma unroll
     for (int j = 0; j < A_NFIX; j++) pg.v[j] = 0.f;
@@ -818,11 +839,10 @@ __global__ void __launch_bounds__(256) raster_backward_records_kernel(RasterArgs
     pg.ds_k = pg.ds_k1 = pg.dth_k = pg.dth_k1 = 0.f;
     uint32_t idx = 0;
     if (g != kNoSlot) {
-        const uint32_t slot = sslot[i];
-        const uint32_t pix = A.rec_pix[slot];
+        const uint32_t pix = kp.y;
         const int y = (int)(pix / (uint32_t)fc.width), x = (int)(pix - (uint32_t)y * fc.width);
         const int tile = (y / kTile) * fc.tiles_x + x / kTile;
-        if (A.tile_overflow[tile] != 0) {
+        if (A.any_overflow && A.tile_overflow[tile] != 0) {
             g = kNoSlot;                      // replayed exactly instead
         } else {
             const float4 tp = A.rec_tp[slot];
@@ -832,8 +852,8 @@ __global__ void __launch_bounds__(256) raster_backward_records_kernel(RasterArgs
             float t, a;
             EvalInfo e;
             eval_pair<KMAX, true>(r, K, pr, fc.near_plane, fc.alpha_min, fc.alpha_max, t, a, &e);
-            const float col[3] = {__ldg(A.rgb + 3 * (size_t)idx), __ldg(A.rgb + 3 * (size_t)idx + 1),
-                                  __ldg(A.rgb + 3 * (size_t)idx + 2)};
+            const float4 c4 = __ldg(A.rgb + idx);
+            const float col[3] = {c4.x, c4.y, c4.z};
             const float T = tp.x;
             const float P[3] = {tp.y, tp.z, tp.w};
             const float wgt = __fmul_rn(a, T);
@@ -857,9 +877,9 @@ __global__ void __launch_bounds__(256) raster_backward_records_kernel(RasterArgs
 #pragma unroll
     for (int j = 0; j < A_NFIX; j++) pg.v[j] = seg_sum(pg.v[j], start);
     // sector terms: runs of equal (key, sector)
-    const int kp = __shfl_up_sync(0xffffffffu, pg.k, 1);
+    const int kprev = __shfl_up_sync(0xffffffffu, pg.k, 1);
     const int kn = __shfl_down_sync(0xffffffffu, pg.k, 1);
-    const bool head2 = head || pg.k != kp;
+    const bool head2 = head || pg.k != kprev;
     const bool tail2 = tail || pg.k != kn;
     const int start2 = 31 - __clz(__ballot_sync(0xffffffffu, head2) & le);
     pg.ds_k = seg_sum(pg.ds_k, start2);
@@ -1001,12 +1021,12 @@ void launch_pack_pixel_grad(const float* dL, const float* Cfin, size_t npix, flo
     note_launch();
 }
 
-void launch_raster_backward_records(const RasterArgs& A, const uint32_t* skey, const uint32_t* sslot, uint32_t n,
-                                    int kmax, cudaStream_t st) {
+void launch_raster_backward_records(const RasterArgs& A, const uint32_t* sslot, uint32_t n, int kmax,
+                                    cudaStream_t st) {
     if (n == 0) return;
     const unsigned blocks = (unsigned)((n + 255u) / 256u);
-    if (kmax == 8) raster_backward_records_kernel<8><<<blocks, 256, 0, st>>>(A, skey, sslot, n);
-    else raster_backward_records_kernel<16><<<blocks, 256, 0, st>>>(A, skey, sslot, n);
+    if (kmax == 8) raster_backward_records_kernel<8><<<blocks, 256, 0, st>>>(A, sslot, n);
+    else raster_backward_records_kernel<16><<<blocks, 256, 0, st>>>(A, sslot, n);
     note_launch();
 }
 

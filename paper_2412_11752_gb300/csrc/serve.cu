@@ -69,7 +69,7 @@ struct Batch {
 // device bytes of one request with P pairs (phase A + phase B + its share
 // of the batch order arrays)
 size_t request_bytes(int64_t n, int kmax, int64_t P, int n_tiles) {
-    const size_t per_prim = (rec_floats(kmax) + bnd_floats(kmax) + 3 + 1) * sizeof(float) + 2 * sizeof(uint64_t);
+    const size_t per_prim = (rec_floats(kmax) + bnd_floats(kmax) + 4 + 1) * sizeof(float) + 2 * sizeof(uint64_t);
     const size_t per_pair = 4 * sizeof(uint32_t);
     return (size_t)n * per_prim + scan_scratch_bytes(n + 1) + (size_t)P * per_pair + radix_sort_scratch_bytes(P) +
            (size_t)n_tiles * (sizeof(uint2) + 6 * sizeof(uint32_t)) + tile_order_work_bytes(n_tiles) + 4096;

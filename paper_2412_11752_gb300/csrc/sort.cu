@@ -296,25 +296,15 @@ void launch_batch_order_keys(const uint2* ranges, int n_tiles, int slot, uint32_
 }
 
 // ---------------------------------------------------------------------------
-// Counting sort of n dense keys (< n_keys; other keys are dropped): count,
-// exclusive scan, scatter.  Entries of one key end up contiguous in an
-// unspecified order; out_keys/out_idx beyond the kept entries hold kNoSlot.
-// Both passes aggregate over the warp: lanes holding equal keys (neighbouring
-// records usually share one) take a single atomic for the group.
-__global__ void key_count_kernel(const uint32_t* __restrict__ keys, uint32_t n, uint32_t n_keys,
-                                 uint32_t* __restrict__ count) {
+// Grouping of the contributor records by pair: the forward counted the
+// records of every pair, so an exclusive scan gives each pair's start and
+// one scatter pass places every record's slot in its pair's range.  The
+// scatter aggregates over the warp: lanes holding the same pair
+// (neighbouring slots usually do) take a single atomic for the group.
+__global__ void record_scatter_kernel(const uint2* __restrict__ kp, uint32_t n, uint32_t n_keys,
+                                      unsigned long long* __restrict__ cursor, uint32_t* __restrict__ out_idx) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t k = i < n ? keys[i] : 0xffffffffu;
-    const unsigned peers = __match_any_sync(0xffffffffu, k);
-    const int lane = threadIdx.x & 31;
-    if (k < n_keys && lane == __ffs(peers) - 1) atomicAdd(count + k, (uint32_t)__popc(peers));
-}
-
-__global__ void key_scatter_kernel(const uint32_t* __restrict__ keys, uint32_t n, uint32_t n_keys,
-                                   unsigned long long* __restrict__ cursor, uint32_t* __restrict__ out_keys,
-                                   uint32_t* __restrict__ out_idx) {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t k = i < n ? keys[i] : 0xffffffffu;
+    const uint32_t k = i < n ? kp[i].x : 0xffffffffu;
     const bool valid = k < n_keys;
     const unsigned peers = __match_any_sync(0xffffffffu, k);
     const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
@@ -322,29 +312,25 @@ __global__ void key_scatter_kernel(const uint32_t* __restrict__ keys, uint32_t n
     if (valid && lane == leader) base = atomicAdd(cursor + k, (unsigned long long)__popc(peers));
     base = __shfl_sync(0xffffffffu, base, leader);
     if (!valid) return;
+    // the counts cover every record, so pos < n; the check keeps a
+    // miscounted pair from writing past the array
     const unsigned long long pos = base + (unsigned long long)__popc(peers & ((1u << lane) - 1u));
-    out_keys[pos] = k;
-    out_idx[pos] = i;
+    if (pos < n) out_idx[pos] = i;
 }
 
-size_t counting_sort_scratch_bytes(uint32_t n_keys) {
-    return ((size_t)n_keys + 1) * (sizeof(uint32_t) + sizeof(uint64_t)) + scan_scratch_bytes((int64_t)n_keys + 1) + 64;
+size_t record_sort_scratch_bytes(uint32_t n_keys) {
+    return ((size_t)n_keys + 1) * sizeof(uint64_t) + scan_scratch_bytes((int64_t)n_keys + 1) + 64;
 }
 
-void counting_sort_keys(const uint32_t* keys, uint32_t n, uint32_t n_keys, uint32_t* out_keys, uint32_t* out_idx,
-                        void* scratch, cudaStream_t st) {
-    cudaMemsetAsync(out_keys, 0xff, sizeof(uint32_t) * (size_t)n, st);
+void group_records(const uint2* kp, uint32_t n, uint32_t n_keys, const uint32_t* count, uint32_t* out_idx,
+                   void* scratch, cudaStream_t st) {
+    cudaMemsetAsync(out_idx, 0xff, sizeof(uint32_t) * (size_t)n, st);
     if (n == 0 || n_keys == 0) return;
-    uint32_t* count = reinterpret_cast<uint32_t*>(scratch);
-    uint64_t* offs = reinterpret_cast<uint64_t*>(
-        (reinterpret_cast<uintptr_t>(count + (size_t)n_keys + 1) + 15) & ~uintptr_t(15));
+    uint64_t* offs = reinterpret_cast<uint64_t*>(scratch);
     void* sscr = reinterpret_cast<void*>((reinterpret_cast<uintptr_t>(offs + (size_t)n_keys + 1) + 15) & ~uintptr_t(15));
-    cudaMemsetAsync(count, 0, sizeof(uint32_t) * ((size_t)n_keys + 1), st);
-    const unsigned blocks = (n + 255u) / 256u;
-    key_count_kernel<<<blocks, 256, 0, st>>>(keys, n, n_keys, count); note_launch();
     exclusive_scan_u32_u64(count, offs, (int64_t)n_keys, sscr, st);
-    key_scatter_kernel<<<blocks, 256, 0, st>>>(keys, n, n_keys, reinterpret_cast<unsigned long long*>(offs), out_keys,
-                                                out_idx); note_launch();
+    record_scatter_kernel<<<(n + 255u) / 256u, 256, 0, st>>>(kp, n, n_keys, reinterpret_cast<unsigned long long*>(offs),
+                                                           out_idx); note_launch();
 }
 
 __global__ void iota_kernel(uint32_t* __restrict__ v, uint32_t n) {
