@@ -69,7 +69,9 @@ constexpr int kOvfCap = 2048;
 // pixel at [s * STRIDE] from its column base, so a warp touching the same
 // slot index hits 32 distinct banks); deeper slots continue in the pixel's
 // overflow column in global memory (lane-contiguous, L1/L2-resident for
-// the usual depths).  Items arrive nearly in depth order, so a push usually
+// the usual depths; slot CAP + j is column entry j + 1, so that the two
+// children of a node in the column, 2i+1 and 2i+2, share one 32-byte
+// sector when CAP is even).  Items arrive nearly in depth order, so a push usually
 // stops at the first parent; a pop sifts down O(log n) levels.  The index
 // of an entry is vals[p] of the tile's list and is only fetched when two
 // depths are exactly equal.
@@ -78,13 +80,14 @@ struct HeapBuf {
     float* st;
     uint32_t* sp;
     float* sa;
-    uint4* col;             // slots CAP .. CAP + ncol - 1 (may be null)
+    uint4* col;             // slots CAP .. CAP + ncol - 1 at col[1 .. ncol] (may be null)
     int ncol;
     const uint32_t* vals;   // the tile's list (primitive index of position p)
     int n;
     float ft;               // r_t of the root (+inf when empty), kept in a register
     __device__ __forceinline__ void init(float* t, uint32_t* p, float* a, uint4* c, int nc, const uint32_t* list) {
-        st = t; sp = p; sa = a; col = c; ncol = c ? nc : 0; vals = list; n = 0; ft = __int_as_float(0x7f800000);
+        st = t; sp = p; sa = a; col = c; ncol = c ? min(nc, kOvfCap - 1) : 0; vals = list; n = 0;
+        ft = __int_as_float(0x7f800000);
     }
     __device__ __forceinline__ int capacity() const { return CAP + ncol; }
     __device__ __forceinline__ bool empty() const { return n == 0; }
@@ -97,7 +100,7 @@ struct HeapBuf {
         if (i < CAP) {
             t = st[i * STRIDE]; p = sp[i * STRIDE]; a = sa[i * STRIDE];
         } else {
-            const uint4 v = col[i - CAP];
+            const uint4 v = col[i - CAP + 1];
             t = __uint_as_float(v.x); p = v.y; a = __uint_as_float(v.z);
         }
     }
@@ -105,7 +108,7 @@ struct HeapBuf {
         if (i < CAP) {
             st[i * STRIDE] = t; sp[i * STRIDE] = p; sa[i * STRIDE] = a;
         } else {
-            col[i - CAP] = make_uint4(__float_as_uint(t), p, __float_as_uint(a), 0u);
+            col[i - CAP + 1] = make_uint4(__float_as_uint(t), p, __float_as_uint(a), 0u);
         }
     }
     // (t1, index of p1) < (t2, index of p2)?
