@@ -261,6 +261,7 @@ drk_status_t frame_phase_a(FrameWork& w, const drk_params_t* params, const drk_c
     if ((s = al.get(&A.rec, (size_t)n * rec_floats(F.kmax))) != DRK_OK) return s;
     if ((s = al.get(&A.bnd, (size_t)n * bnd_floats(F.kmax))) != DRK_OK) return s;
     if ((s = al.get(&A.rgb, (size_t)n)) != DRK_OK) return s;
+    if (opt->cull_level == DRK_CULL_TILE && (s = al.get(&A.spans, (size_t)n * F.fc.tiles_y)) != DRK_OK) return s;
     if ((s = al.get(&A.count, (size_t)n + 1)) != DRK_OK) return s;
     if ((s = al.get(&A.offsets, (size_t)n + 1)) != DRK_OK) return s;
     if ((s = al.get(&A.zmax_bits, 1)) != DRK_OK) return s;

@@ -29,6 +29,8 @@ struct PreArgs {
     float* rec;             // n x Rec<KMAX>::STRIDE
     float* bnd;             // n x Bnd<KMAX>::STRIDE
     float4* rgb;            // n view-dependent colours (r, g, b, 0)
+    uint32_t* spans;        // n x tiles_y: tile span [a, b] (a | b << 16) of each row of a
+                            // primitive taking row-interval culling (written by the count pass)
     uint32_t* count;        // n pairs per primitive
     uint64_t* offsets;      // n + 1 exclusive scan of count
     int* zmax_bits;         // max ray depth of any bound (float bits)

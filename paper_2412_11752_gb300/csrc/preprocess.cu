@@ -545,8 +545,8 @@ __device__ __forceinline__ bool tile_test(const float* __restrict__ rec, const f
 // hold a pixel centre (integer pixel index) within the x-range of the
 // pieces (and of the filter disc) over the row's band of pixel rows, both
 // widened by 0.1 pixel, far above the float32 error of the projection.
-// The count and the emission run the same code, so they keep the same
-// tiles.
+// The count pass stores each row's span of tiles, and the emission writes
+// exactly those tiles.
 constexpr int kArcSeg = 4;    // tangent segments per sector arc (the cover exceeds the arc by 1/cos(gap/8))
 constexpr int kPieceV = 2 * kArcSeg + 3;   // centre, 2 kArcSeg + 1 arc points, one cut point
 
@@ -573,16 +573,24 @@ __device__ void build_pieces(const PreArgs& A, int64_t i, const float* __restric
     const float rho = bnd[B_RHO + k];
     // the arc of radius rho over [tk, tk1], covered by kArcSeg tangent
     // segments: points on the arc alternate with the tangents' crossings
+    // (directions by rotation from theta'_k in steps of gap / (2 kArcSeg); the
+    // last one exact, so neighbouring pieces share their boundary ray; the
+    // rotation's float32 drift, ~1e-6 rad, is far inside rho's 0.2 % margin)
     const float half = gap / (2 * kArcSeg);
-    const float rt = rho / cosf(half);
+    float sh, ch, sa, ca;
+    sincosf(half, &sh, &ch);
+    sincosf(tk, &sa, &ca);
+    const float rt = rho / ch;
     float px[kPieceV], py[kPieceV];
     int n = 0;
     px[n] = 0.f; py[n] = 0.f; n++;
     for (int m = 0; m <= 2 * kArcSeg; m++) {
-        float sa, ca;
-        sincosf(tk + half * m, &sa, &ca);
+        if (m == 2 * kArcSeg) sincosf(tk1, &sa, &ca);
         const float rr = (m & 1) ? rt : rho;
         px[n] = rr * ca; py[n] = rr * sa; n++;
+        const float cn = ca * ch - sa * sh;
+        sa = sa * ch + ca * sh;
+        ca = cn;
     }
     const float L = bnd[Bnd<KMAX>::CL1];
     float qx[kPieceV], qy[kPieceV];
@@ -709,10 +717,12 @@ __global__ void __launch_bounds__(kCullThreads) count_kernel(PreArgs A) {
         if (bi[B_FLAGS] & 1) build_pieces<KMAX>(A, i, rec, bnd, P);
         __syncwarp();
         uint32_t cnt = 0;
+        uint32_t* sp = A.spans + (size_t)A.fc.tiles_y * i;
         for (int ty = y0 + lane; ty <= y1; ty += 32) {
             int a, b;
             row_span<KMAX>(P, A.p.K, bnd, A.fc, ty, x0, x1, a, b);
             cnt += b >= a ? (uint32_t)(b - a + 1) : 0u;
+            sp[ty] = b >= a ? ((uint32_t)a | ((uint32_t)b << 16)) : 1u;   // 1: a = 1 > b = 0, empty
         }
         for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
         if (lane == 0) A.count[i] = cnt;
@@ -738,7 +748,6 @@ __global__ void __launch_bounds__(kCullThreads) count_kernel(PreArgs A) {
 // offsets[i]; within a primitive they are in tile order.
 template <int KMAX>
 __global__ void __launch_bounds__(kCullThreads) emit_kernel(PreArgs A) {
-    __shared__ Pieces<KMAX> pieces[kCullThreads / 32];
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (i >= A.p.n) return;
@@ -763,15 +772,17 @@ __global__ void __launch_bounds__(kCullThreads) emit_kernel(PreArgs A) {
         return qf <= 0.f ? 0u : (qf >= (float)qmax ? qmax : (uint32_t)qf);
     };
     if (row_culled(A, bnd)) {
-        Pieces<KMAX>& P = pieces[threadIdx.x >> 5];
-        if (lane < KMAX) P.n[lane] = 0;
-        if (bi[B_FLAGS] & 1) build_pieces<KMAX>(A, i, rec, bnd, P);
-        __syncwarp();
-        // each lane writes the tiles of its rows, after those of lower lanes
+        // the row spans the count pass found; each lane writes the tiles of
+        // its rows, after those of lower lanes
+        const uint32_t* sp = A.spans + (size_t)A.fc.tiles_y * i;
         for (int r0 = y0; r0 <= y1; r0 += 32) {
             const int ty = r0 + lane;
             int a = 1, b = 0;
-            if (ty <= y1) row_span<KMAX>(P, A.p.K, bnd, A.fc, ty, x0, x1, a, b);
+            if (ty <= y1) {
+                const uint32_t ab = sp[ty];
+                a = (int)(ab & 0xffffu);
+                b = (int)(ab >> 16);
+            }
             const uint32_t c = b >= a ? (uint32_t)(b - a + 1) : 0u;
             uint32_t incl = c;
             for (int o = 1; o < 32; o <<= 1) {

@@ -68,8 +68,8 @@ struct Batch {
 
 // device bytes of one request with P pairs (phase A + phase B + its share
 // of the batch order arrays)
-size_t request_bytes(int64_t n, int kmax, int64_t P, int n_tiles) {
-    const size_t per_prim = (rec_floats(kmax) + bnd_floats(kmax) + 4 + 1) * sizeof(float) + 2 * sizeof(uint64_t);
+size_t request_bytes(int64_t n, int kmax, int64_t P, int n_tiles, int tiles_y) {
+    const size_t per_prim = (rec_floats(kmax) + bnd_floats(kmax) + 4 + 1 + tiles_y) * sizeof(float) + 2 * sizeof(uint64_t);
     const size_t per_pair = 4 * sizeof(uint32_t);
     return (size_t)n * per_prim + scan_scratch_bytes(n + 1) + (size_t)P * per_pair + radix_sort_scratch_bytes(P) +
            (size_t)n_tiles * (sizeof(uint2) + 6 * sizeof(uint32_t)) + tile_order_work_bytes(n_tiles) + 4096;
@@ -337,7 +337,7 @@ void run_batch(drk_serve* S, int s, std::vector<Item>& items, int* countdown, st
         if (!b->ok[i]) continue;
         W[i].P = (int64_t)S->h_totals[s][i];
         bi->pairs[i] = W[i].P;
-        const size_t rb = request_bytes(items[i].p.n, kmax, W[i].P, W[i].F.n_tiles);
+        const size_t rb = request_bytes(items[i].p.n, kmax, W[i].P, W[i].F.n_tiles, W[i].F.fc.tiles_y);
         if (rb > S->budget) {
             b->ok[i] = 0;
             status[i] = fail(DRK_ERR_OOM, "request needs %zu device bytes, budget %zu", rb, S->budget);
@@ -687,7 +687,7 @@ drk_status_t drk_serve_submit(drk_serve_t* S, int scene_id, const drk_camera_t* 
     r.scene = scene_id;
     r.cam = *cam;
     r.out = out_rgb;
-    r.est_bytes = request_bytes(sc.p.n, sc.kmax, (int64_t)pairs, n_tiles);
+    r.est_bytes = request_bytes(sc.p.n, sc.kmax, (int64_t)pairs, n_tiles, (cam->height + kTile - 1) / kTile);
     r.t.arrival_ms = S->now_ms();
     r.t.status = DRK_OK;
     const uint64_t tk = S->next_ticket++;
