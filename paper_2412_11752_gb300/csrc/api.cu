@@ -465,9 +465,9 @@ drk_status_t drk_render(drk_ctx_t* ctx, const drk_params_t* params, const drk_ca
         R.rec_cap = (uint32_t)(chunks * kRecChunk);
         R.rec_ctr = ctx->rec_ctr;
         if ((s = al.get(&R.rec_kp, (size_t)R.rec_cap)) != DRK_OK) return s;
-        if ((s = al.get(&R.rec_count, (size_t)w.P + 1)) != DRK_OK) return s;
+        if ((s = al.get(&R.rec_count, (size_t)n + 1)) != DRK_OK) return s;
         if ((s = al.get(&R.rec_tp, (size_t)R.rec_cap)) != DRK_OK) return s;
-        DRK_CUDA(cudaMemsetAsync(R.rec_count, 0, sizeof(uint32_t) * ((size_t)w.P + 1), st));
+        DRK_CUDA(cudaMemsetAsync(R.rec_count, 0, sizeof(uint32_t) * ((size_t)n + 1), st));
         DRK_CUDA(cudaMemsetAsync(ctx->rec_ctr, 0, sizeof(unsigned int), st));
         if ((s = al.get(&R.tile_overflow, (size_t)F.n_tiles)) != DRK_OK) return s;
         DRK_CUDA(cudaMemsetAsync(R.tile_overflow, 0, sizeof(int32_t) * (size_t)F.n_tiles, st));
@@ -599,10 +599,10 @@ drk_status_t drk_render_backward(drk_ctx_t* ctx, const drk_params_t* params, con
     const uint64_t nrec = std::min<uint64_t>(taken, state->rec_cap);
     // a chunk request beyond the pool sent tiles to the replay
     R.any_overflow = taken > state->rec_cap ? 1 : 0;
-    // records grouped by list pair, from the per-pair counts of the forward
+    // records grouped by primitive, from the per-primitive counts of the forward
     uint32_t* sslot = nullptr;
     uint8_t* sort_scr = nullptr;
-    const uint32_t n_keys = (uint32_t)state->pairs;
+    const uint32_t n_keys = (uint32_t)state->n;
     if ((s = al.get(&sslot, (size_t)nrec)) != DRK_OK) return s;
     if ((s = al.get(&sort_scr, record_sort_scratch_bytes(n_keys))) != DRK_OK) return s;
     StageTimer& tm = ctx->timer;

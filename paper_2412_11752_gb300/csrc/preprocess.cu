@@ -553,6 +553,7 @@ constexpr int kPieceV = 2 * kArcSeg + 3;   // centre, 2 kArcSeg + 1 arc points, 
 template <int KMAX>
 struct Pieces {
     float2 v[KMAX][kPieceV];
+    float ylo[KMAX], yhi[KMAX];   // the piece's extent in pixel rows
     int n[KMAX];
 };
 
@@ -615,12 +616,18 @@ __device__ void build_pieces(const PreArgs& A, int64_t i, const float* __restric
         for (int a = 0; a < n; a++) { qx[a] = px[a]; qy[a] = py[a]; }
         m = n;
     }
+    float ylo = 1e30f, yhi = -1e30f;
     for (int a = 0; a < m; a++) {
         float pc[3];
         for (int r = 0; r < 3; r++) pc[r] = G.muc[r] + qx[a] * G.Rxp[r] + qy[a] * G.Ryp[r];
         const float iz = 1.f / pc[2];
-        P.v[k][a] = make_float2(A.cam.fx * pc[0] * iz + A.cam.cx - 0.5f, A.cam.fy * pc[1] * iz + A.cam.cy - 0.5f);
+        const float2 q = make_float2(A.cam.fx * pc[0] * iz + A.cam.cx - 0.5f, A.cam.fy * pc[1] * iz + A.cam.cy - 0.5f);
+        P.v[k][a] = q;
+        ylo = fminf(ylo, q.y);
+        yhi = fmaxf(yhi, q.y);
     }
+    P.ylo[k] = ylo;
+    P.yhi[k] = yhi;
     P.n[k] = m;
 }
 
@@ -636,6 +643,7 @@ __device__ void row_span(const Pieces<KMAX>& P, int K, const float* __restrict__
     float xmin = 1e30f, xmax = -1e30f;
     for (int k = 0; k < K; k++) {
         const int n = P.n[k];
+        if (n == 0 || P.yhi[k] < yl || P.ylo[k] > yh) continue;   // the piece misses the band
         for (int e = 0; e < n; e++) {
             float2 p = P.v[k][e], q = P.v[k][(e + 1 == n) ? 0 : e + 1];
             if (p.y > q.y) { const float2 t = p; p = q; q = t; }

@@ -15,12 +15,12 @@
 //   dC/dc_i = T_i alpha_i,  dC/dalpha_i = T_i c_i - S_i / (1 - alpha_i),
 // with S_i = C_final - P_i the colour composited behind i (P_i the prefix
 // including i).  The forward writes one record per composited contributor
-// (list pair, pixel, T_i, P_i) in the order it composites, which is the
+// (primitive, pixel, T_i, P_i) in the order it composites, which is the
 // front-to-back order the supplementary "Cache-Sorting" paragraph asks the
 // backward to follow; each record then carries its own T_i and P_i, so the
-// backward treats records independently: sorted by list pair, a warp
-// recomputes 32 of them and sums the gradients of equal pairs with
-// segmented shuffles before one global atomic per pair and component.
+// backward treats records independently: grouped by primitive, a warp
+// recomputes 32 of them and sums the gradients of equal primitives with
+// segmented shuffles before one global atomic per run and component.
 // Tiles whose records did not fit the pool use the replay kernel instead,
 // which re-runs the forward traversal exactly and accumulates with global
 // atomics.
@@ -64,17 +64,16 @@ constexpr int kOvfCap = 2048;
 
 // Per-pixel depth-order buffer (the exact form of the paper's cache-sorting,
 // Sec. 4.4 and the supplementary algorithm): a binary min-heap of pending
-// contributors (r_t, list position p, alpha) ordered by (r_t, primitive
-// index).  Its first CAP slots live in shared memory (element s of this
-// pixel at [s * STRIDE] from its column base, so a warp touching the same
-// slot index hits 32 distinct banks); deeper slots continue in the pixel's
-// overflow column in global memory (lane-contiguous, L1/L2-resident for
-// the usual depths; slot CAP + j is column entry j + 1, so that the two
-// children of a node in the column, 2i+1 and 2i+2, share one 32-byte
-// sector when CAP is even).  Items arrive nearly in depth order, so a push usually
-// stops at the first parent; a pop sifts down O(log n) levels.  The index
-// of an entry is vals[p] of the tile's list and is only fetched when two
-// depths are exactly equal.
+// contributors (r_t, primitive index, alpha) ordered by (r_t, index).  Its
+// first CAP slots live in shared memory (element s of this pixel at
+// [s * STRIDE] from its column base, so a warp touching the same slot index
+// hits 32 distinct banks); deeper slots continue in the pixel's overflow
+// column in global memory (lane-contiguous, L1/L2-resident for the usual
+// depths; slot CAP + j is column entry j + 1, so that the two children of a
+// node in the column, 2i+1 and 2i+2, share one 32-byte sector when CAP is
+// even).  Items arrive nearly in depth order, so a push usually stops at the
+// first parent; a pop sifts down O(log n) levels.  Holding the index itself
+// (not the list position) spares compositing and ties a dependent load.
 template <int CAP, int STRIDE>
 struct HeapBuf {
     float* st;
@@ -82,18 +81,17 @@ struct HeapBuf {
     float* sa;
     uint4* col;             // slots CAP .. CAP + ncol - 1 at col[1 .. ncol] (may be null)
     int ncol;
-    const uint32_t* vals;   // the tile's list (primitive index of position p)
     int n;
     float ft;               // r_t of the root (+inf when empty), kept in a register
-    __device__ __forceinline__ void init(float* t, uint32_t* p, float* a, uint4* c, int nc, const uint32_t* list) {
-        st = t; sp = p; sa = a; col = c; ncol = c ? min(nc, kOvfCap - 1) : 0; vals = list; n = 0;
+    __device__ __forceinline__ void init(float* t, uint32_t* p, float* a, uint4* c, int nc) {
+        st = t; sp = p; sa = a; col = c; ncol = c ? min(nc, kOvfCap - 1) : 0; n = 0;
         ft = __int_as_float(0x7f800000);
     }
     __device__ __forceinline__ int capacity() const { return CAP + ncol; }
     __device__ __forceinline__ bool empty() const { return n == 0; }
     __device__ __forceinline__ bool full() const { return n >= CAP + ncol; }
     __device__ __forceinline__ float front_t() const { return ft; }
-    __device__ __forceinline__ uint32_t front_p() const { return sp[0]; }
+    __device__ __forceinline__ uint32_t front_i() const { return sp[0]; }
     __device__ __forceinline__ float front_a() const { return sa[0]; }
     __device__ __forceinline__ void clear() { n = 0; ft = __int_as_float(0x7f800000); }
     __device__ __forceinline__ void get(int i, float& t, uint32_t& p, float& a) const {
@@ -111,13 +109,13 @@ struct HeapBuf {
             col[i - CAP + 1] = make_uint4(__float_as_uint(t), p, __float_as_uint(a), 0u);
         }
     }
-    // (t1, index of p1) < (t2, index of p2)?
-    __device__ __forceinline__ bool less(float t1, uint32_t p1, float t2, uint32_t p2) const {
-        return t1 < t2 || (t1 == t2 && __ldg(vals + p1) < __ldg(vals + p2));
+    // (t1, i1) < (t2, i2)?
+    __device__ __forceinline__ bool less(float t1, uint32_t i1, float t2, uint32_t i2) const {
+        return t1 < t2 || (t1 == t2 && i1 < i2);
     }
     // the root's key is at or after (t, idx)?
     __device__ __forceinline__ bool front_at_or_after(float t, uint32_t idx) const {
-        return ft > t || (ft == t && __ldg(vals + sp[0]) >= idx);
+        return ft > t || (ft == t && sp[0] >= idx);
     }
     // requires !full()
     __device__ __forceinline__ void push(float t, uint32_t p, float a) {
@@ -151,8 +149,8 @@ struct HeapBuf {
                 m = i; mt = it; mp = ip; ma = ia;
             }
         }
-        if (!less(t, p, mt, mp)) return key_of(t, __ldg(vals + p));
-        const uint64_t out = key_of(mt, __ldg(vals + mp));
+        if (!less(t, p, mt, mp)) return key_of(t, p);
+        const uint64_t out = key_of(mt, mp);
         int i = m;
         while (i > 0) {
             const int up = (i - 1) >> 1;
@@ -418,7 +416,7 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
     const bool rec_on = !BWD && A.rec_kp != nullptr;
     const bool literal = fc.order_mode == DRK_ORDER_CACHE_SORT;
     kb.init(ring + threadIdx.x, reinterpret_cast<uint32_t*>(ring) + CAP * kRasterThreads + threadIdx.x,
-            ring + 2 * CAP * kRasterThreads + threadIdx.x, literal ? nullptr : ovf, A.ovf_cap, list);
+            ring + 2 * CAP * kRasterThreads + threadIdx.x, literal ? nullptr : ovf, A.ovf_cap);
     // Exact order with a bounded heap.  When a contributor finds the heap
     // full, the largest key among the heap and the new entry is dropped;
     // `lost` is the smallest dropped key (every key in the heap stays below
@@ -437,10 +435,10 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
     float aux_d = 0.f, aux_n[3] = {0.f, 0.f, 0.f};
     const float fxp = AUX ? 1.f / fc.ifx : 0.f, fyp = AUX ? 1.f / fc.ify : 0.f;
 
-    // composites contributor (r_t t, alpha a, list position p); `slot` is its
-    // record slot (kNoSlot: not recorded).  Returns the pair index recorded
-    // (kNoSlot: none)
-    auto composite = [&](float t, float a, uint32_t p, uint32_t slot) -> uint32_t {
+    // composites contributor (r_t t, alpha a, primitive idx); `slot` is its
+    // record slot (kNoSlot: not recorded).  Returns the primitive index
+    // recorded (kNoSlot: none)
+    auto composite = [&](float t, float a, uint32_t idx, uint32_t slot) -> uint32_t {
         const float Tn = __fmul_rn(ps.T, __fsub_rn(1.f, a));
         if (Tn < fc.T_min) {
             // the pixel stops here: its slot of this round stays unused
@@ -448,7 +446,6 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
             ps.done = true;
             return kNoSlot;
         }
-        const uint32_t idx = __ldg(list + p);
         const float4 c4 = __ldg(rgbp + idx);
         const float col[3] = {c4.x, c4.y, c4.z};
         uint32_t recorded = kNoSlot;
@@ -469,7 +466,7 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
             if (slot != kNoSlot) {
                 // read only by the backward: streaming stores keep them from
                 // evicting the primitive records this kernel re-reads from L2
-                recorded = rg.x + p;
+                recorded = idx;
                 __stcs(A.rec_kp + slot, make_uint2(recorded, (uint32_t)pix));
                 __stcs(A.rec_tp + slot, make_float4(T_i, ps.C[0], ps.C[1], ps.C[2]));
             }
@@ -491,20 +488,20 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
         return recorded;
     };
     // composites the root of this lane's heap
-    auto emit_front = [&](uint32_t slot) { return composite(kb.front_t(), kb.front_a(), kb.front_p(), slot); };
+    auto emit_front = [&](uint32_t slot) { return composite(kb.front_t(), kb.front_a(), kb.front_i(), slot); };
 
-    // a contributor with key kk at list position j
+    // a contributor of primitive j with key kk = (t, j)
     auto offer = [&](float t, uint32_t j, float a, uint64_t kk) {
         if (literal) {
             // the paper's cache-sorting: a full cache composites the smaller
             // of its smallest entry and the new one (Sec. 4.4)
             if (!kb.full()) {
                 kb.push(t, j, a);
-            } else if (kb.less(t, j, kb.front_t(), kb.front_p())) {
+            } else if (kb.less(t, j, kb.front_t(), kb.front_i())) {
                 composite(t, a, j, kNoSlot);
             } else {
                 const float ra = kb.front_a(), rt = kb.front_t();
-                const uint32_t rp = kb.front_p();
+                const uint32_t rp = kb.front_i();
                 composite(rt, ra, rp, kNoSlot);
                 if (!ps.done) {
                     kb.pop();
@@ -634,7 +631,6 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
             }
             for (uint32_t jj = 0; jj < cn; jj++) {
                 const uint32_t idx = __shfl_sync(0xffffffffu, idx_a, jj);
-                const uint32_t j = c0 + jj;
                 float h[R_FIX4 * 4];
                 Geo gm;
                 bool geo = false;
@@ -660,7 +656,7 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
                         if (eval_kernel<KMAX, false>(h, reinterpret_cast<const float*>(sg), K, pr, gm, fc.alpha_min,
                                                      fc.alpha_max, a)) {
                             wc.contrib++;
-                            offer(gm.t, j, a, key_of(gm.t, idx));
+                            offer(gm.t, idx, a, key_of(gm.t, idx));
                             if (ps.done) pass_done = true;
                         }
                     }
@@ -803,15 +799,16 @@ __device__ __forceinline__ float warp_sum32(float v) {
 }
 
 // ---------------------------------------------------------------------------
-// Backward over the contributor records, sorted by list pair (tile, item).
+// Backward over the contributor records, grouped by primitive.
 // Each record (pixel, T before, colour prefix after) is independent: the
 // warp takes 32 consecutive records, recomputes each pair with all
 // intermediates, forms dC/dalpha = T c - S / (1 - alpha) with
 // S = C_final - P, chains through Eq. 10 - Eq. 4 to the record quantities,
-// and sums over runs of equal keys (the pixels of one tile that composited
-// one item) with segmented shuffles; the last lane of a run adds the sums
-// to global memory.  Sector terms are summed over runs of equal
-// (key, sector).  Records of tiles marked for the replay are skipped.
+// and sums over runs of equal primitive index (the pixels, over all tiles,
+// where one primitive was composited) with segmented shuffles; the last
+// lane of a run adds the sums to global memory.  Sector terms are summed
+// over runs of equal (index, sector).  Records of tiles marked for the
+// replay are skipped.
 
 // inclusive sum over lanes [start, lane] (start <= lane; every lane calls it)
 __device__ __forceinline__ float seg_sum(float v, int start) {
@@ -826,15 +823,21 @@ __device__ __forceinline__ float seg_sum(float v, int start) {
 
 template <int KMAX>
 __global__ void __launch_bounds__(256) raster_backward_records_kernel(RasterArgs A, const uint32_t* __restrict__ sslot,
-                                                                      uint32_t n) {
+                                                                      uint32_t n, uint32_t wave) {
     const int lane = threadIdx.x & 31;
     const FrameConst& fc = A.fc;
     const int K = A.K;
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    // Block b takes chunk (b % wave) * C + b / wave of 256 records (the grid
+    // is wave * C blocks, wave = the blocks resident at once): the blocks
+    // that run together are C chunks apart, so they rarely work on the same
+    // primitive, and their global atomics rarely meet on one address.
+    const uint32_t C = gridDim.x / wave;
+    const uint32_t cb = (blockIdx.x % wave) * C + blockIdx.x / wave;
+    const uint64_t i = (uint64_t)cb * blockDim.x + threadIdx.x;
     const uint32_t slot = i < n ? sslot[i] : kNoSlot;
     uint2 kp = make_uint2(kNoSlot, 0u);
     if (slot < A.rec_cap) kp = A.rec_kp[slot];
-    uint32_t g = kp.x;
+    uint32_t g = kp.x;   // primitive index
     PairGrad pg;
 #pragma unroll
     for (int j = 0; j < A_NFIX; j++) pg.v[j] = 0.f;
@@ -849,7 +852,7 @@ __global__ void __launch_bounds__(256) raster_backward_records_kernel(RasterArgs
             g = kNoSlot;                      // replayed exactly instead
         } else {
             const float4 tp = A.rec_tp[slot];
-            idx = __ldg(A.vals + g);
+            idx = g;
             const float* r = A.rec + (size_t)Rec<KMAX>::STRIDE * idx;
             const PixelRay pr = make_ray(fc, x, y);
             float t, a;
@@ -1024,12 +1027,28 @@ void launch_pack_pixel_grad(const float* dL, const float* Cfin, size_t npix, flo
     note_launch();
 }
 
+// blocks of the records kernel resident at once on this device (computed once)
+template <int KMAX>
+static unsigned records_wave() {
+    static unsigned wave = 0;
+    if (wave == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raster_backward_records_kernel<KMAX>, 256, 0);
+        wave = (unsigned)std::max(1, sms * std::max(per_sm, 1));
+    }
+    return wave;
+}
+
 void launch_raster_backward_records(const RasterArgs& A, const uint32_t* sslot, uint32_t n, int kmax,
                                     cudaStream_t st) {
     if (n == 0) return;
     const unsigned blocks = (unsigned)((n + 255u) / 256u);
-    if (kmax == 8) raster_backward_records_kernel<8><<<blocks, 256, 0, st>>>(A, sslot, n);
-    else raster_backward_records_kernel<16><<<blocks, 256, 0, st>>>(A, sslot, n);
+    const unsigned wave = kmax == 8 ? records_wave<8>() : records_wave<16>();
+    const unsigned gb = (blocks + wave - 1u) / wave * wave;
+    if (kmax == 8) raster_backward_records_kernel<8><<<gb, 256, 0, st>>>(A, sslot, n, wave);
+    else raster_backward_records_kernel<16><<<gb, 256, 0, st>>>(A, sslot, n, wave);
     note_launch();
 }
 
