@@ -101,9 +101,9 @@ struct drk_state {
     uint32_t* tile_order = nullptr;
     DepthQuant* dq = nullptr;
     float* Cfin = nullptr;
-    uint2* rec_kp = nullptr;
+    uint32_t* rec_key = nullptr;
     uint32_t* rec_count = nullptr;
-    float4* rec_tp = nullptr;
+    uint4* rec_rd = nullptr;
     uint32_t rec_cap = 0;
     unsigned int* rec_chunks = nullptr;       // device: chunks this forward took
     int32_t* tile_overflow = nullptr;
@@ -464,9 +464,9 @@ drk_status_t drk_render(drk_ctx_t* ctx, const drk_params_t* params, const drk_ca
         if (opt->record_chunks > 0) chunks = std::min<uint64_t>(chunks, (uint64_t)opt->record_chunks);
         R.rec_cap = (uint32_t)(chunks * kRecChunk);
         R.rec_ctr = ctx->rec_ctr;
-        if ((s = al.get(&R.rec_kp, (size_t)R.rec_cap)) != DRK_OK) return s;
+        if ((s = al.get(&R.rec_key, (size_t)R.rec_cap)) != DRK_OK) return s;
         if ((s = al.get(&R.rec_count, (size_t)n + 1)) != DRK_OK) return s;
-        if ((s = al.get(&R.rec_tp, (size_t)R.rec_cap)) != DRK_OK) return s;
+        if ((s = al.get(&R.rec_rd, 2 * (size_t)R.rec_cap)) != DRK_OK) return s;
         DRK_CUDA(cudaMemsetAsync(R.rec_count, 0, sizeof(uint32_t) * ((size_t)n + 1), st));
         DRK_CUDA(cudaMemsetAsync(ctx->rec_ctr, 0, sizeof(unsigned int), st));
         if ((s = al.get(&R.tile_overflow, (size_t)F.n_tiles)) != DRK_OK) return s;
@@ -504,9 +504,9 @@ drk_status_t drk_render(drk_ctx_t* ctx, const drk_params_t* params, const drk_ca
         S->ranges = w.ranges;
         S->tile_order = w.tile_order;
         S->dq = A.dq;
-        S->rec_kp = R.rec_kp;
+        S->rec_key = R.rec_key;
         S->rec_count = R.rec_count;
-        S->rec_tp = R.rec_tp;
+        S->rec_rd = R.rec_rd;
         S->rec_cap = R.rec_cap;
         S->tile_overflow = R.tile_overflow;
         const size_t npix = (size_t)cam->width * cam->height;
@@ -585,9 +585,9 @@ drk_status_t drk_render_backward(drk_ctx_t* ctx, const drk_params_t* params, con
     R.Cfin = state->Cfin;
     R.gtmp = gtmp;
     R.grads = *grads;
-    R.rec_kp = state->rec_kp;
+    R.rec_key = state->rec_key;
     R.rec_count = state->rec_count;
-    R.rec_tp = state->rec_tp;
+    R.rec_rd = state->rec_rd;
     R.rec_cap = state->rec_cap;
     R.tile_overflow = state->tile_overflow;
     attach_ovf(ctx, opt, F.kmax, state->cap, true, F.n_tiles, st, R);
@@ -607,7 +607,7 @@ drk_status_t drk_render_backward(drk_ctx_t* ctx, const drk_params_t* params, con
     if ((s = al.get(&sort_scr, record_sort_scratch_bytes(n_keys))) != DRK_OK) return s;
     StageTimer& tm = ctx->timer;
     cudaEvent_t ev = tm.begin(st);
-    group_records(state->rec_kp, (uint32_t)nrec, n_keys, state->rec_count, sslot, sort_scr, st);
+    group_records(state->rec_key, (uint32_t)nrec, n_keys, state->rec_count, sslot, sort_scr, st);
     tm.end(ST_REC_SORT, ev, st);
     ev = tm.begin(st);
     float4* pixg = nullptr;

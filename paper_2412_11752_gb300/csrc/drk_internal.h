@@ -91,14 +91,16 @@ struct RasterArgs {
     float* out_normal;     // 3 x H x W sum of T alpha n (camera frame, towards the camera)
     // contributor records written by the forward for the backward (may be
     // null): one per composited contributor, in rec_cap slots handed out in
-    // chunks of kRecChunk; rec_kp = (primitive index, pixel y * width + x),
-    // x = kNoSlot for a slot left unused (the raster marks the unused tail
-    // of each warp's last chunk), rec_tp = (T before the contributor,
-    // composited colour after it); rec_count[i] counts the records of
-    // primitive i (zeroed before the forward).  tile_overflow[tile] != 0 if a record did not fit (the
+    // chunks of kRecChunk; rec_key = primitive index, kNoSlot for a slot
+    // left unused (the raster marks the unused tail of each warp's last
+    // chunk); rec_rd = the record itself, one 32-byte sector per slot:
+    // (index, pixel y * width + x, T before the contributor, composited
+    // colour after it, two unused words), so that reading one record costs
+    // one sector whatever its neighbours; rec_count[i] counts the records
+    // of primitive i (zeroed before the forward).  tile_overflow[tile] != 0 if a record did not fit (the
     // backward replays that tile exactly)
-    uint2* rec_kp;
-    float4* rec_tp;
+    uint32_t* rec_key;
+    uint4* rec_rd;                   // 2 per slot
     uint32_t* rec_count;
     uint32_t rec_cap;
     unsigned int* rec_ctr;           // chunks taken (zeroed before the forward)
@@ -157,12 +159,12 @@ void launch_raster_backward_records(const RasterArgs& A, const uint32_t* sslot, 
                                     cudaStream_t st);
 // v[i] = i for i < n
 void launch_iota(uint32_t* v, uint32_t n, cudaStream_t st);
-// records grouped by key (rec_kp x): out_idx[0 .. total) holds the slots of
+// records grouped by key (rec_key): out_idx[0 .. total) holds the slots of
 // the n records whose key is below n_keys (others, kNoSlot, dropped),
 // grouped by key (order within a key unspecified), from the per-key counts
 // the forward took; then kNoSlot up to n
 size_t record_sort_scratch_bytes(uint32_t n_keys);
-void group_records(const uint2* kp, uint32_t n, uint32_t n_keys, const uint32_t* count, uint32_t* out_idx,
+void group_records(const uint32_t* key, uint32_t n, uint32_t n_keys, const uint32_t* count, uint32_t* out_idx,
                    void* scratch, cudaStream_t st);
 // batched forward over A.n_batch_tiles tiles of the frames in A.slots
 void launch_raster_batch(const RasterArgs& A, int kmax, int cap, cudaStream_t st);

@@ -348,7 +348,7 @@ struct RecChunk {
 // is exhausted the chunk stays empty and the tile is marked for the exact
 // replay.
 __device__ __forceinline__ void take_record_chunk(const RasterArgs& A, RecChunk& rc, int tile) {
-    for (uint32_t q = rc.base + (threadIdx.x & 31); q < rc.end; q += 32) A.rec_kp[q] = make_uint2(kNoSlot, 0u);
+    for (uint32_t q = rc.base + (threadIdx.x & 31); q < rc.end; q += 32) A.rec_key[q] = kNoSlot;
     uint32_t c = 0;
     if ((threadIdx.x & 31) == 0) c = atomicAdd(A.rec_ctr, 1u);
     c = __shfl_sync(0xffffffffu, c, 0);
@@ -413,7 +413,7 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
         }
     }
     // contributor records for the backward
-    const bool rec_on = !BWD && A.rec_kp != nullptr;
+    const bool rec_on = !BWD && A.rec_key != nullptr;
     const bool literal = fc.order_mode == DRK_ORDER_CACHE_SORT;
     kb.init(ring + threadIdx.x, reinterpret_cast<uint32_t*>(ring) + CAP * kRasterThreads + threadIdx.x,
             ring + 2 * CAP * kRasterThreads + threadIdx.x, literal ? nullptr : ovf, A.ovf_cap);
@@ -442,7 +442,7 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
         const float Tn = __fmul_rn(ps.T, __fsub_rn(1.f, a));
         if (Tn < fc.T_min) {
             // the pixel stops here: its slot of this round stays unused
-            if (!BWD && slot != kNoSlot) A.rec_kp[slot] = make_uint2(kNoSlot, 0u);
+            if (!BWD && slot != kNoSlot) A.rec_key[slot] = kNoSlot;
             ps.done = true;
             return kNoSlot;
         }
@@ -467,8 +467,11 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
                 // read only by the backward: streaming stores keep them from
                 // evicting the primitive records this kernel re-reads from L2
                 recorded = idx;
-                __stcs(A.rec_kp + slot, make_uint2(recorded, (uint32_t)pix));
-                __stcs(A.rec_tp + slot, make_float4(T_i, ps.C[0], ps.C[1], ps.C[2]));
+                __stcs(A.rec_key + slot, recorded);
+                __stcs(A.rec_rd + 2 * (size_t)slot, make_uint4(recorded, (uint32_t)pix, __float_as_uint(T_i),
+                                                               __float_as_uint(ps.C[0])));
+                __stcs(A.rec_rd + 2 * (size_t)slot + 1,
+                       make_uint4(__float_as_uint(ps.C[1]), __float_as_uint(ps.C[2]), 0u, 0u));
             }
         } else {
             float G = 0.f;
@@ -767,8 +770,8 @@ __global__ void __launch_bounds__(kRasterThreads, (BATCH || CAP >= 16) ? 4 : 5) 
         }
     }
     // the unused tail of the warp's last record chunk holds no record
-    if (!BWD && !BATCH && A.rec_kp)
-        for (uint32_t q = rc.base + lane; q < rc.end; q += 32) A.rec_kp[q] = make_uint2(kNoSlot, 0u);
+    if (!BWD && !BATCH && A.rec_key)
+        for (uint32_t q = rc.base + lane; q < rc.end; q += 32) A.rec_key[q] = kNoSlot;
     // counters: one atomic per warp
     if (A.counters) {
         for (int o = 16; o > 0; o >>= 1) {
@@ -835,9 +838,13 @@ __global__ void __launch_bounds__(256) raster_backward_records_kernel(RasterArgs
     const uint32_t cb = (blockIdx.x % wave) * C + blockIdx.x / wave;
     const uint64_t i = (uint64_t)cb * blockDim.x + threadIdx.x;
     const uint32_t slot = i < n ? sslot[i] : kNoSlot;
-    uint2 kp = make_uint2(kNoSlot, 0u);
-    if (slot < A.rec_cap) kp = A.rec_kp[slot];
-    uint32_t g = kp.x;   // primitive index
+    // the record: one 32-byte sector
+    uint4 r0 = make_uint4(kNoSlot, 0u, 0u, 0u), r1 = make_uint4(0u, 0u, 0u, 0u);
+    if (slot < A.rec_cap) {
+        r0 = A.rec_rd[2 * (size_t)slot];
+        r1 = A.rec_rd[2 * (size_t)slot + 1];
+    }
+    uint32_t g = r0.x;   // primitive index
     PairGrad pg;
 #pragma unroll
     for (int j = 0; j < A_NFIX; j++) pg.v[j] = 0.f;
@@ -845,13 +852,12 @@ __global__ void __launch_bounds__(256) raster_backward_records_kernel(RasterArgs
     pg.ds_k = pg.ds_k1 = pg.dth_k = pg.dth_k1 = 0.f;
     uint32_t idx = 0;
     if (g != kNoSlot) {
-        const uint32_t pix = kp.y;
+        const uint32_t pix = r0.y;
         const int y = (int)(pix / (uint32_t)fc.width), x = (int)(pix - (uint32_t)y * fc.width);
         const int tile = (y / kTile) * fc.tiles_x + x / kTile;
         if (A.any_overflow && A.tile_overflow[tile] != 0) {
             g = kNoSlot;                      // replayed exactly instead
         } else {
-            const float4 tp = A.rec_tp[slot];
             idx = g;
             const float* r = A.rec + (size_t)Rec<KMAX>::STRIDE * idx;
             const PixelRay pr = make_ray(fc, x, y);
@@ -860,8 +866,8 @@ __global__ void __launch_bounds__(256) raster_backward_records_kernel(RasterArgs
             eval_pair<KMAX, true>(r, K, pr, fc.near_plane, fc.alpha_min, fc.alpha_max, t, a, &e);
             const float4 c4 = __ldg(A.rgb + idx);
             const float col[3] = {c4.x, c4.y, c4.z};
-            const float T = tp.x;
-            const float P[3] = {tp.y, tp.z, tp.w};
+            const float T = __uint_as_float(r0.z);
+            const float P[3] = {__uint_as_float(r0.w), __uint_as_float(r1.x), __uint_as_float(r1.y)};
             const float wgt = __fmul_rn(a, T);
             const float inv1ma = rcp_approx(1.f - a);
             // the pixel's dL and final colour: one 32-byte sector

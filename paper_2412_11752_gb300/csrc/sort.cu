@@ -301,10 +301,10 @@ void launch_batch_order_keys(const uint2* ranges, int n_tiles, int slot, uint32_
 // one scatter pass places every record's slot in its pair's range.  The
 // scatter aggregates over the warp: lanes holding the same pair
 // (neighbouring slots usually do) take a single atomic for the group.
-__global__ void record_scatter_kernel(const uint2* __restrict__ kp, uint32_t n, uint32_t n_keys,
+__global__ void record_scatter_kernel(const uint32_t* __restrict__ key, uint32_t n, uint32_t n_keys,
                                       unsigned long long* __restrict__ cursor, uint32_t* __restrict__ out_idx) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t k = i < n ? kp[i].x : 0xffffffffu;
+    const uint32_t k = i < n ? key[i] : 0xffffffffu;
     const bool valid = k < n_keys;
     const unsigned peers = __match_any_sync(0xffffffffu, k);
     const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
@@ -322,14 +322,14 @@ size_t record_sort_scratch_bytes(uint32_t n_keys) {
     return ((size_t)n_keys + 1) * sizeof(uint64_t) + scan_scratch_bytes((int64_t)n_keys + 1) + 64;
 }
 
-void group_records(const uint2* kp, uint32_t n, uint32_t n_keys, const uint32_t* count, uint32_t* out_idx,
+void group_records(const uint32_t* key, uint32_t n, uint32_t n_keys, const uint32_t* count, uint32_t* out_idx,
                    void* scratch, cudaStream_t st) {
     cudaMemsetAsync(out_idx, 0xff, sizeof(uint32_t) * (size_t)n, st);
     if (n == 0 || n_keys == 0) return;
     uint64_t* offs = reinterpret_cast<uint64_t*>(scratch);
     void* sscr = reinterpret_cast<void*>((reinterpret_cast<uintptr_t>(offs + (size_t)n_keys + 1) + 15) & ~uintptr_t(15));
     exclusive_scan_u32_u64(count, offs, (int64_t)n_keys, sscr, st);
-    record_scatter_kernel<<<(n + 255u) / 256u, 256, 0, st>>>(kp, n, n_keys, reinterpret_cast<unsigned long long*>(offs),
+    record_scatter_kernel<<<(n + 255u) / 256u, 256, 0, st>>>(key, n, n_keys, reinterpret_cast<unsigned long long*>(offs),
                                                            out_idx); note_launch();
 }
 
