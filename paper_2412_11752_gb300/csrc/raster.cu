@@ -435,10 +435,10 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
     float aux_d = 0.f, aux_n[3] = {0.f, 0.f, 0.f};
     const float fxp = AUX ? 1.f / fc.ifx : 0.f, fyp = AUX ? 1.f / fc.ify : 0.f;
 
-    // composites contributor (r_t t, alpha a, primitive idx); `slot` is its
-    // record slot (kNoSlot: not recorded).  Returns the primitive index
-    // recorded (kNoSlot: none)
-    auto composite = [&](float t, float a, uint32_t idx, uint32_t slot) -> uint32_t {
+    // composites contributor (r_t t, alpha a, primitive idx, colour c4);
+    // `slot` is its record slot (kNoSlot: not recorded).  Returns the
+    // primitive index recorded (kNoSlot: none)
+    auto composite = [&](float t, float a, uint32_t idx, const float4 c4, uint32_t slot) -> uint32_t {
         const float Tn = __fmul_rn(ps.T, __fsub_rn(1.f, a));
         if (Tn < fc.T_min) {
             // the pixel stops here: its slot of this round stays unused
@@ -446,7 +446,6 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
             ps.done = true;
             return kNoSlot;
         }
-        const float4 c4 = __ldg(rgbp + idx);
         const float col[3] = {c4.x, c4.y, c4.z};
         uint32_t recorded = kNoSlot;
         const float wgt = __fmul_rn(a, ps.T);
@@ -491,7 +490,16 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
         return recorded;
     };
     // composites the root of this lane's heap
-    auto emit_front = [&](uint32_t slot) { return composite(kb.front_t(), kb.front_a(), kb.front_i(), slot); };
+    // composites the root of this lane's heap and removes it: the colour
+    // load is issued first so that the removal's memory accesses overlap it
+    // (a pixel that stops here leaves its heap unused)
+    auto emit_front = [&](uint32_t slot) {
+        const float t = kb.front_t(), a = kb.front_a();
+        const uint32_t i = kb.front_i();
+        const float4 c4 = __ldg(rgbp + i);
+        kb.pop();
+        return composite(t, a, i, c4, slot);
+    };
 
     // a contributor of primitive j with key kk = (t, j)
     auto offer = [&](float t, uint32_t j, float a, uint64_t kk) {
@@ -501,11 +509,11 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
             if (!kb.full()) {
                 kb.push(t, j, a);
             } else if (kb.less(t, j, kb.front_t(), kb.front_i())) {
-                composite(t, a, j, kNoSlot);
+                composite(t, a, j, __ldg(rgbp + j), kNoSlot);
             } else {
                 const float ra = kb.front_a(), rt = kb.front_t();
                 const uint32_t rp = kb.front_i();
-                composite(rt, ra, rp, kNoSlot);
+                composite(rt, ra, rp, __ldg(rgbp + rp), kNoSlot);
                 if (!ps.done) {
                     kb.pop();
                     kb.push(t, j, a);
@@ -551,13 +559,10 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
                 }
             }
             uint32_t rk = kNoSlot;
-            if (want) {
-                rk = emit_front(slot);
-                if (!ps.done) kb.pop();
-            }
+            if (want) rk = emit_front(slot);
             if (rec_on) {
-                // records per pair, one atomic per group of lanes that
-                // composited the same pair in this round
+                // records per primitive, one atomic per group of lanes that
+                // composited the same primitive in this round
                 const unsigned peers = __match_any_sync(0xffffffffu, rk);
                 if (rk != kNoSlot && lane == __ffs(peers) - 1) atomicAdd(A.rec_count + rk, (uint32_t)__popc(peers));
             }
