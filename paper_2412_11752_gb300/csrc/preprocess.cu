@@ -726,11 +726,17 @@ __global__ void __launch_bounds__(kCullThreads) count_kernel(PreArgs A) {
         __syncwarp();
         uint32_t cnt = 0;
         uint32_t* sp = A.spans + (size_t)A.fc.tiles_y * i;
-        for (int ty = y0 + lane; ty <= y1; ty += 32) {
-            int a, b;
-            row_span<KMAX>(P, A.p.K, bnd, A.fc, ty, x0, x1, a, b);
-            cnt += b >= a ? (uint32_t)(b - a + 1) : 0u;
-            sp[ty] = b >= a ? ((uint32_t)a | ((uint32_t)b << 16)) : 1u;   // 1: a = 1 > b = 0, empty
+        // the same trip count on every lane: a shuffle after a loop whose
+        // trip count differed between lanes returned stale values to the
+        // lanes that ran longer (observed with nvcc 13.0 on sm_103a)
+        for (int r0 = y0; r0 <= y1; r0 += 32) {
+            const int ty = r0 + lane;
+            if (ty <= y1) {
+                int a, b;
+                row_span<KMAX>(P, A.p.K, bnd, A.fc, ty, x0, x1, a, b);
+                cnt += b >= a ? (uint32_t)(b - a + 1) : 0u;
+                sp[ty] = b >= a ? ((uint32_t)a | ((uint32_t)b << 16)) : 1u;   // 1: a = 1 > b = 0, empty
+            }
         }
         for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
         if (lane == 0) A.count[i] = cnt;

@@ -348,7 +348,13 @@ struct RecChunk {
 // is exhausted the chunk stays empty and the tile is marked for the exact
 // replay.
 __device__ __forceinline__ void take_record_chunk(const RasterArgs& A, RecChunk& rc, int tile) {
-    for (uint32_t q = rc.base + (threadIdx.x & 31); q < rc.end; q += 32) A.rec_key[q] = kNoSlot;
+    // the same trip count on every lane: a shuffle after a loop whose trip
+    // count differed between lanes returned stale values to the lanes that
+    // ran longer (observed with nvcc 13.0 on sm_103a)
+    for (uint32_t q0 = rc.base; q0 < rc.end; q0 += 32) {
+        const uint32_t q = q0 + (threadIdx.x & 31);
+        if (q < rc.end) A.rec_key[q] = kNoSlot;
+    }
     uint32_t c = 0;
     if ((threadIdx.x & 31) == 0) c = atomicAdd(A.rec_ctr, 1u);
     c = __shfl_sync(0xffffffffu, c, 0);
@@ -776,7 +782,8 @@ __global__ void __launch_bounds__(kRasterThreads, (BATCH || CAP >= 16) ? 4 : 5) 
     }
     // the unused tail of the warp's last record chunk holds no record
     if (!BWD && !BATCH && A.rec_key)
-        for (uint32_t q = rc.base + lane; q < rc.end; q += 32) A.rec_key[q] = kNoSlot;
+        for (uint32_t q0 = rc.base; q0 < rc.end; q0 += 32)
+            if (q0 + lane < rc.end) A.rec_key[q0 + lane] = kNoSlot;
     // counters: one atomic per warp
     if (A.counters) {
         for (int o = 16; o > 0; o >>= 1) {
@@ -799,129 +806,178 @@ __global__ void __launch_bounds__(kRasterThreads, (BATCH || CAP >= 16) ? 4 : 5) 
 
 }
 
-// Sum of v over all 32 lanes (every lane of the warp calls it).
-__device__ __forceinline__ float warp_sum32(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 // ---------------------------------------------------------------------------
 // Backward over the contributor records, grouped by primitive.
-// Each record (pixel, T before, colour prefix after) is independent: the
-// warp takes 32 consecutive records, recomputes each pair with all
-// intermediates, forms dC/dalpha = T c - S / (1 - alpha) with
-// S = C_final - P, chains through Eq. 10 - Eq. 4 to the record quantities,
-// and sums over runs of equal primitive index (the pixels, over all tiles,
-// where one primitive was composited) with segmented shuffles; the last
-// lane of a run adds the sums to global memory.  Sector terms are summed
-// over runs of equal (index, sector).  Records of tiles marked for the
-// replay are skipped.
+// Each record (pixel, T before, colour prefix after) is independent: a lane
+// recomputes its pair with all intermediates, forms
+// dC/dalpha = T c - S / (1 - alpha) with S = C_final - P, and chains
+// through Eq. 10 - Eq. 4 to the record quantities.  Records of one
+// primitive (all its pixels, over all tiles) are contiguous, a few thousand
+// on average, so a warp walks a range of kRecWin windows of 32 records and
+// keeps per-lane partial sums of the current primitive: the fixed terms in
+// registers, the per-basis terms (scale and angle of the pixel's sector
+// and of the next one) in a per-lane shared-memory column.  Only when the
+// primitive changes are the partial sums added over the warp and sent to
+// global memory, one atomic per parameter.  Records of tiles marked for
+// the replay are skipped.
+constexpr int kRecWin = 16;          // 32-record windows per warp
+constexpr int kRecThreads = 128;     // 4 warps per block
 
-// inclusive sum over lanes [start, lane] (start <= lane; every lane calls it)
-__device__ __forceinline__ float seg_sum(float v, int start) {
+template <int KMAX>
+struct RecAcc {
+    static constexpr int ROWS = A_NFIX + 2 * KMAX;   // fixed terms, then scale[KMAX], theta[KMAX]
+    float* sh;                                       // this warp's [ROWS][32] columns
+    float v[A_NFIX];
+};
+
+// Adds the warp's partial sums of primitive g to its gradients and clears
+// them (every lane calls it).
+template <int KMAX>
+__device__ __forceinline__ void rec_flush(const RasterArgs& A, RecAcc<KMAX>& acc, uint32_t g) {
     const int lane = threadIdx.x & 31;
+    float* sh = acc.sh;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const float w = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane - o >= start) v += w;
+    for (int j = 0; j < A_NFIX; j++) {
+        sh[j * 32 + lane] = acc.v[j];
+        acc.v[j] = 0.f;
     }
-    return v;
+    __syncwarp();
+    const int K = A.K;
+    // every lane runs the same passes (see take_record_chunk)
+#pragma unroll
+    for (int pass = 0; pass < (RecAcc<KMAX>::ROWS + 31) / 32; pass++) {
+        const int r = pass * 32 + lane;
+        // rotated reads: the lanes of one step hit 32 distinct banks
+        float s = 0.f;
+        if (r < RecAcc<KMAX>::ROWS) {
+#pragma unroll 8
+            for (int m = 0; m < 32; m++) s += sh[r * 32 + ((m + lane) & 31)];
+        }
+        if (r >= RecAcc<KMAX>::ROWS || s == 0.f) continue;
+        if (r < A_OPA) {
+            atomicAdd(A.gtmp + (size_t)G_STRIDE * g + r, s);
+        } else if (r == A_OPA) {
+            atomicAdd(A.grads.opacity + g, s);
+        } else if (r == A_TAU) {
+            atomicAdd(A.grads.tau + g, s);
+        } else if (r == A_ETA) {
+            atomicAdd(A.grads.eta + g, s);
+        } else if (r < A_NFIX + KMAX) {
+            const int q = r - A_NFIX;
+            if (q < K) atomicAdd(A.grads.scale + (size_t)K * g + q, s);
+        } else {
+            // theta'_0 = 0 and theta'_K = 2 pi are constants of the frame
+            const int q = r - A_NFIX - KMAX;
+            if (q >= 1 && q < K) atomicAdd(A.grads.theta + (size_t)K * g + q, s);
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int r = A_NFIX; r < RecAcc<KMAX>::ROWS; r++) sh[r * 32 + lane] = 0.f;
+    __syncwarp();
 }
 
 template <int KMAX>
-__global__ void __launch_bounds__(256) raster_backward_records_kernel(RasterArgs A, const uint32_t* __restrict__ sslot,
-                                                                      uint32_t n, uint32_t wave) {
-    const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(kRecThreads) raster_backward_records_kernel(RasterArgs A,
+                                                                              const uint32_t* __restrict__ sslot,
+                                                                              uint32_t n) {
+    constexpr int kWarps = kRecThreads / 32;
+    constexpr int ROWS = RecAcc<KMAX>::ROWS;
+    __shared__ float sh_all[kWarps * ROWS * 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t base = ((uint64_t)blockIdx.x * kWarps + warp) * (32u * kRecWin);
+    if (base >= n) return;
     const FrameConst& fc = A.fc;
     const int K = A.K;
-    // Block b takes chunk (b % wave) * C + b / wave of 256 records (the grid
-    // is wave * C blocks, wave = the blocks resident at once): the blocks
-    // that run together are C chunks apart, so they rarely work on the same
-    // primitive, and their global atomics rarely meet on one address.
-    const uint32_t C = gridDim.x / wave;
-    const uint32_t cb = (blockIdx.x % wave) * C + blockIdx.x / wave;
-    const uint64_t i = (uint64_t)cb * blockDim.x + threadIdx.x;
-    const uint32_t slot = i < n ? sslot[i] : kNoSlot;
-    // the record: one 32-byte sector
-    uint4 r0 = make_uint4(kNoSlot, 0u, 0u, 0u), r1 = make_uint4(0u, 0u, 0u, 0u);
-    if (slot < A.rec_cap) {
-        r0 = A.rec_rd[2 * (size_t)slot];
-        r1 = A.rec_rd[2 * (size_t)slot + 1];
-    }
-    uint32_t g = r0.x;   // primitive index
-    PairGrad pg;
+    RecAcc<KMAX> acc;
+    acc.sh = sh_all + warp * ROWS * 32;
 #pragma unroll
-    for (int j = 0; j < A_NFIX; j++) pg.v[j] = 0.f;
-    pg.k = 0; pg.k1 = 0;
-    pg.ds_k = pg.ds_k1 = pg.dth_k = pg.dth_k1 = 0.f;
-    uint32_t idx = 0;
-    if (g != kNoSlot) {
-        const uint32_t pix = r0.y;
-        const int y = (int)(pix / (uint32_t)fc.width), x = (int)(pix - (uint32_t)y * fc.width);
-        const int tile = (y / kTile) * fc.tiles_x + x / kTile;
-        if (A.any_overflow && A.tile_overflow[tile] != 0) {
-            g = kNoSlot;                      // replayed exactly instead
-        } else {
-            idx = g;
-            const float* r = A.rec + (size_t)Rec<KMAX>::STRIDE * idx;
-            const PixelRay pr = make_ray(fc, x, y);
-            float t, a;
-            EvalInfo e;
-            eval_pair<KMAX, true>(r, K, pr, fc.near_plane, fc.alpha_min, fc.alpha_max, t, a, &e);
-            const float4 c4 = __ldg(A.rgb + idx);
-            const float col[3] = {c4.x, c4.y, c4.z};
-            const float T = __uint_as_float(r0.z);
-            const float P[3] = {__uint_as_float(r0.w), __uint_as_float(r1.x), __uint_as_float(r1.y)};
-            const float wgt = __fmul_rn(a, T);
-            const float inv1ma = rcp_approx(1.f - a);
-            // the pixel's dL and final colour: one 32-byte sector
-            const float4 q0 = A.pixg[2 * (size_t)pix], q1 = A.pixg[2 * (size_t)pix + 1];
-            const float dL[3] = {q0.x, q0.y, q0.z}, Cf[3] = {q0.w, q1.x, q1.y};
-            float G = 0.f;
-            for (int c = 0; c < 3; c++) G += dL[c] * (T * col[c] - (Cf[c] - P[c]) * inv1ma);
-            grad_from_info<KMAX>(A, r, idx, pr, e, G, pg);
-            for (int c = 0; c < 3; c++) pg.v[A_RGB + c] = dL[c] * wgt;
+    for (int j = 0; j < A_NFIX; j++) acc.v[j] = 0.f;
+#pragma unroll
+    for (int r = A_NFIX; r < ROWS; r++) acc.sh[r * 32 + lane] = 0.f;
+    __syncwarp();
+    float* S = acc.sh + A_NFIX * 32 + lane;            // scale column
+    float* H = acc.sh + (A_NFIX + KMAX) * 32 + lane;   // theta column
+
+    // software pipeline: the records of window w + 1 and the slots of
+    // window w + 2 are loaded while window w is computed
+    auto load_rec = [&](uint32_t slot, uint4& r0, uint4& r1) {
+        r0 = make_uint4(kNoSlot, 0u, 0u, 0u);
+        r1 = make_uint4(0u, 0u, 0u, 0u);
+        if (slot < A.rec_cap) {
+            r0 = A.rec_rd[2 * (size_t)slot];
+            r1 = A.rec_rd[2 * (size_t)slot + 1];
         }
-    }
-    // runs of equal keys are contiguous (sorted); kNoSlot lanes carry zeros
-    const unsigned le = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
-    const uint32_t gp = __shfl_up_sync(0xffffffffu, g, 1);
-    const uint32_t gn = __shfl_down_sync(0xffffffffu, g, 1);
-    const bool head = lane == 0 || g != gp;
-    const bool tail = lane == 31 || g != gn;
-    const int start = 31 - __clz(__ballot_sync(0xffffffffu, head) & le);
+    };
+    uint64_t i = base + lane;
+    uint4 r0, r1;
+    load_rec(i < n ? sslot[i] : kNoSlot, r0, r1);
+    uint32_t slot_n = i + 32 < n ? sslot[i + 32] : kNoSlot;
+    uint32_t gcur = kNoSlot;   // primitive of the partial sums (warp-uniform)
+    for (int w = 0; w < kRecWin; w++) {
+        if (base + 32u * w >= n) break;
+        uint4 n0, n1;
+        load_rec(w + 1 < kRecWin ? slot_n : kNoSlot, n0, n1);
+        const uint64_t i2 = i + 64;
+        const uint32_t slot_nn = (w + 2 < kRecWin && i2 < n) ? sslot[i2] : kNoSlot;
+
+        uint32_t g = r0.x;   // primitive index
+        PairGrad pg;
 #pragma unroll
-    for (int j = 0; j < A_NFIX; j++) pg.v[j] = seg_sum(pg.v[j], start);
-    // sector terms: runs of equal (key, sector)
-    const int kprev = __shfl_up_sync(0xffffffffu, pg.k, 1);
-    const int kn = __shfl_down_sync(0xffffffffu, pg.k, 1);
-    const bool head2 = head || pg.k != kprev;
-    const bool tail2 = tail || pg.k != kn;
-    const int start2 = 31 - __clz(__ballot_sync(0xffffffffu, head2) & le);
-    pg.ds_k = seg_sum(pg.ds_k, start2);
-    pg.ds_k1 = seg_sum(pg.ds_k1, start2);
-    pg.dth_k = seg_sum(pg.dth_k, start2);
-    pg.dth_k1 = seg_sum(pg.dth_k1, start2);
-    if (g == kNoSlot) return;
-    if (tail) {
-        float* gt = A.gtmp + (size_t)G_STRIDE * idx;
+        for (int j = 0; j < A_NFIX; j++) pg.v[j] = 0.f;
+        pg.k = 0; pg.k1 = 0;
+        pg.ds_k = pg.ds_k1 = pg.dth_k = pg.dth_k1 = 0.f;
+        if (g != kNoSlot) {
+            const uint32_t pix = r0.y;
+            const int y = (int)(pix / (uint32_t)fc.width), x = (int)(pix - (uint32_t)y * fc.width);
+            const int tile = (y / kTile) * fc.tiles_x + x / kTile;
+            if (A.any_overflow && A.tile_overflow[tile] != 0) {
+                g = kNoSlot;                      // replayed exactly instead
+            } else {
+                // the pixel's dL and final colour: one 32-byte sector
+                const float4 q0 = A.pixg[2 * (size_t)pix], q1 = A.pixg[2 * (size_t)pix + 1];
+                const float* r = A.rec + (size_t)Rec<KMAX>::STRIDE * g;
+                const PixelRay pr = make_ray(fc, x, y);
+                float t, a;
+                EvalInfo e;
+                eval_pair<KMAX, true>(r, K, pr, fc.near_plane, fc.alpha_min, fc.alpha_max, t, a, &e);
+                const float4 c4 = __ldg(A.rgb + g);
+                const float col[3] = {c4.x, c4.y, c4.z};
+                const float T = __uint_as_float(r0.z);
+                const float P[3] = {__uint_as_float(r0.w), __uint_as_float(r1.x), __uint_as_float(r1.y)};
+                const float wgt = __fmul_rn(a, T);
+                const float inv1ma = rcp_approx(1.f - a);
+                const float dL[3] = {q0.x, q0.y, q0.z}, Cf[3] = {q0.w, q1.x, q1.y};
+                float G = 0.f;
+                for (int c = 0; c < 3; c++) G += dL[c] * (T * col[c] - (Cf[c] - P[c]) * inv1ma);
+                grad_from_info<KMAX>(A, r, g, pr, e, G, pg);
+                for (int c = 0; c < 3; c++) pg.v[A_RGB + c] = dL[c] * wgt;
+            }
+        }
+        // runs of equal primitive: lanes of the current one add to the
+        // partial sums; a new primitive flushes them first
+        while (true) {
+            if (g != kNoSlot && g == gcur) {
 #pragma unroll
-        for (int j = 0; j < A_OPA; j++)
-            if (pg.v[j] != 0.f) atomicAdd(gt + j, pg.v[j]);
-        if (pg.v[A_OPA] != 0.f) atomicAdd(A.grads.opacity + idx, pg.v[A_OPA]);
-        if (pg.v[A_TAU] != 0.f) atomicAdd(A.grads.tau + idx, pg.v[A_TAU]);
-        if (pg.v[A_ETA] != 0.f) atomicAdd(A.grads.eta + idx, pg.v[A_ETA]);
+                for (int j = 0; j < A_NFIX; j++) acc.v[j] += pg.v[j];
+                S[pg.k * 32] += pg.ds_k;
+                S[pg.k1 * 32] += pg.ds_k1;
+                H[pg.k * 32] += pg.dth_k;
+                if (pg.k + 1 < KMAX) H[(pg.k + 1) * 32] += pg.dth_k1;
+                g = kNoSlot;
+            }
+            const unsigned rest = __ballot_sync(0xffffffffu, g != kNoSlot);
+            if (rest == 0u) break;
+            __syncwarp();
+            if (gcur != kNoSlot) rec_flush<KMAX>(A, acc, gcur);
+            gcur = __shfl_sync(0xffffffffu, g, __ffs(rest) - 1);
+        }
+        r0 = n0; r1 = n1;
+        slot_n = slot_nn;
+        i += 32;
     }
-    if (tail2) {
-        // theta'_0 = 0 and theta'_K = 2 pi are constants of the frame
-        const int k = pg.k, k1 = (k + 1 == K) ? 0 : k + 1;
-        const size_t base = (size_t)K * idx;
-        if (pg.ds_k != 0.f) atomicAdd(A.grads.scale + base + k, pg.ds_k);
-        if (pg.ds_k1 != 0.f) atomicAdd(A.grads.scale + base + k1, pg.ds_k1);
-        if (k >= 1 && pg.dth_k != 0.f) atomicAdd(A.grads.theta + base + k, pg.dth_k);
-        if (k + 1 < K && pg.dth_k1 != 0.f) atomicAdd(A.grads.theta + base + k + 1, pg.dth_k1);
-    }
+    __syncwarp();
+    if (gcur != kNoSlot) rec_flush<KMAX>(A, acc, gcur);
 }
 
 template <int KMAX, int CAP>
@@ -1038,28 +1094,13 @@ void launch_pack_pixel_grad(const float* dL, const float* Cfin, size_t npix, flo
     note_launch();
 }
 
-// blocks of the records kernel resident at once on this device (computed once)
-template <int KMAX>
-static unsigned records_wave() {
-    static unsigned wave = 0;
-    if (wave == 0) {
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raster_backward_records_kernel<KMAX>, 256, 0);
-        wave = (unsigned)std::max(1, sms * std::max(per_sm, 1));
-    }
-    return wave;
-}
-
 void launch_raster_backward_records(const RasterArgs& A, const uint32_t* sslot, uint32_t n, int kmax,
                                     cudaStream_t st) {
     if (n == 0) return;
-    const unsigned blocks = (unsigned)((n + 255u) / 256u);
-    const unsigned wave = kmax == 8 ? records_wave<8>() : records_wave<16>();
-    const unsigned gb = (blocks + wave - 1u) / wave * wave;
-    if (kmax == 8) raster_backward_records_kernel<8><<<gb, 256, 0, st>>>(A, sslot, n, wave);
-    else raster_backward_records_kernel<16><<<gb, 256, 0, st>>>(A, sslot, n, wave);
+    constexpr uint32_t per_block = kRecThreads * kRecWin;
+    const unsigned blocks = (unsigned)((n + per_block - 1u) / per_block);
+    if (kmax == 8) raster_backward_records_kernel<8><<<blocks, kRecThreads, 0, st>>>(A, sslot, n);
+    else raster_backward_records_kernel<16><<<blocks, kRecThreads, 0, st>>>(A, sslot, n);
     note_launch();
 }
 
