@@ -59,54 +59,78 @@ __device__ __forceinline__ uint64_t key_of(float t, uint32_t idx) {
     return ((uint64_t)__float_as_uint(t) << 32) | idx;
 }
 
-// Entries of a pixel's overflow column in global memory (16 B each).
+// Entries of a pixel's overflow column in global memory.
 constexpr int kOvfCap = 2048;
+// Children per node of the depth-order heap.
+constexpr int kHeapArity = 8;
+// Shared heap slots for a capacity option of cap (8, 16, 32): at least one
+// more, and 1 modulo the arity, so that no group of siblings straddles
+// shared and global memory.
+template <int CAP>
+struct HeapSlots {
+    static constexpr int value = (CAP + kHeapArity - 1) / kHeapArity * kHeapArity + 1;
+    static_assert(value % kHeapArity == 1 % kHeapArity, "sibling groups must not straddle the shared slots");
+};
 
 // Per-pixel depth-order buffer (the exact form of the paper's cache-sorting,
-// Sec. 4.4 and the supplementary algorithm): a binary min-heap of pending
-// contributors (r_t, primitive index, alpha) ordered by (r_t, index).  Its
-// first CAP slots live in shared memory (element s of this pixel at
-// [s * STRIDE] from its column base, so a warp touching the same slot index
-// hits 32 distinct banks); deeper slots continue in the pixel's overflow
-// column in global memory (lane-contiguous, L1/L2-resident for the usual
-// depths; slot CAP + j is column entry j + 1, so that the two children of a
-// node in the column, 2i+1 and 2i+2, share one 32-byte sector when CAP is
-// even).  Items arrive nearly in depth order, so a push usually stops at the
-// first parent; a pop sifts down O(log n) levels.  Holding the index itself
-// (not the list position) spares compositing and ties a dependent load.
-template <int CAP, int STRIDE>
+// Sec. 4.4 and the supplementary algorithm): a D-ary min-heap of pending
+// contributors keyed by (r_t, primitive index) as one 64-bit word (r_t > 0,
+// so its float bits order like the value; the index breaks ties), with
+// alpha beside it.  Its first SLOTS slots live in shared memory (slot s of
+// this pixel at [s * STRIDE] from its column base, so a warp touching the
+// same slot index hits distinct banks); deeper slots continue in the
+// pixel's overflow column in global memory (keys and alphas in two arrays,
+// lane-contiguous, L1/L2-resident for the usual depths).  The D children
+// of node i are slots D i + 1 .. D i + D; with SLOTS = 1 (mod D) a group of
+// siblings lies wholly in shared or wholly in global memory, where its keys
+// fill one aligned 8 D-byte block and its alphas one 4 D-byte block, read
+// together.  A removal walks log_D(n) levels (a binary heap of the same
+// size walks twice as many, most of them in global memory).  Items arrive
+// nearly in depth order, so an insertion usually stops at the first parent.
+// In the cache-sorting mode the heap holds at most `lim` entries (the
+// paper's cache length) and has no global part.
+template <int D, int SLOTS, int STRIDE>
 struct HeapBuf {
-    float* st;
-    uint32_t* sp;
-    float* sa;
-    uint4* col;             // slots CAP .. CAP + ncol - 1 at col[1 .. ncol] (may be null)
-    int ncol;
+    static_assert(SLOTS % D == 1 % D, "sibling groups must not straddle the shared slots");
+    static constexpr int OFF = 0;   // slot SLOTS + j is column entry OFF + j (groups start on multiples of D)
+    uint64_t* sk;           // shared keys
+    float* sa;              // shared alphas
+    uint64_t* ck;           // column keys (null: no global part)
+    float* ca;              // column alphas
+    int lim;                // capacity (entries)
     int n;
-    float ft;               // r_t of the root (+inf when empty), kept in a register
-    __device__ __forceinline__ void init(float* t, uint32_t* p, float* a, uint4* c, int nc) {
-        st = t; sp = p; sa = a; col = c; ncol = c ? min(nc, kOvfCap - 1) : 0; n = 0;
-        ft = __int_as_float(0x7f800000);
-    }
-    __device__ __forceinline__ int capacity() const { return CAP + ncol; }
-    __device__ __forceinline__ bool empty() const { return n == 0; }
-    __device__ __forceinline__ bool full() const { return n >= CAP + ncol; }
-    __device__ __forceinline__ float front_t() const { return ft; }
-    __device__ __forceinline__ uint32_t front_i() const { return sp[0]; }
-    __device__ __forceinline__ float front_a() const { return sa[0]; }
-    __device__ __forceinline__ void clear() { n = 0; ft = __int_as_float(0x7f800000); }
-    __device__ __forceinline__ void get(int i, float& t, uint32_t& p, float& a) const {
-        if (i < CAP) {
-            t = st[i * STRIDE]; p = sp[i * STRIDE]; a = sa[i * STRIDE];
+    uint64_t fk;            // key of the root (~0 when empty), kept in a register
+    __device__ __forceinline__ void init(uint64_t* k, float* a, uint4* col, int ncol_req, int cache_len) {
+        sk = k; sa = a;
+        if (col) {
+            ck = reinterpret_cast<uint64_t*>(col);
+            ca = reinterpret_cast<float*>(ck + kOvfCap);
+            lim = SLOTS + min(ncol_req, kOvfCap - D);
         } else {
-            const uint4 v = col[i - CAP + 1];
-            t = __uint_as_float(v.x); p = v.y; a = __uint_as_float(v.z);
+            ck = nullptr; ca = nullptr;
+            lim = cache_len > 0 ? min(cache_len, SLOTS) : SLOTS;
         }
+        n = 0;
+        fk = ~0ull;
     }
-    __device__ __forceinline__ void put(int i, float t, uint32_t p, float a) {
-        if (i < CAP) {
-            st[i * STRIDE] = t; sp[i * STRIDE] = p; sa[i * STRIDE] = a;
+    __device__ __forceinline__ int capacity() const { return lim; }
+    __device__ __forceinline__ bool empty() const { return n == 0; }
+    __device__ __forceinline__ bool full() const { return n >= lim; }
+    __device__ __forceinline__ float front_t() const { return __uint_as_float((uint32_t)(fk >> 32)); }
+    __device__ __forceinline__ uint32_t front_i() const { return (uint32_t)fk; }
+    __device__ __forceinline__ float front_a() const { return sa[0]; }
+    __device__ __forceinline__ void clear() { n = 0; fk = ~0ull; }
+    __device__ __forceinline__ uint64_t getk(int i) const {
+        return i < SLOTS ? sk[i * STRIDE] : ck[OFF + i - SLOTS];
+    }
+    __device__ __forceinline__ float geta(int i) const {
+        return i < SLOTS ? sa[i * STRIDE] : ca[OFF + i - SLOTS];
+    }
+    __device__ __forceinline__ void put(int i, uint64_t k, float a) {
+        if (i < SLOTS) {
+            sk[i * STRIDE] = k; sa[i * STRIDE] = a;
         } else {
-            col[i - CAP + 1] = make_uint4(__float_as_uint(t), p, __float_as_uint(a), 0u);
+            ck[OFF + i - SLOTS] = k; ca[OFF + i - SLOTS] = a;
         }
     }
     // (t1, i1) < (t2, i2)?
@@ -114,88 +138,98 @@ struct HeapBuf {
         return t1 < t2 || (t1 == t2 && i1 < i2);
     }
     // the root's key is at or after (t, idx)?
-    __device__ __forceinline__ bool front_at_or_after(float t, uint32_t idx) const {
-        return ft > t || (ft == t && sp[0] >= idx);
+    __device__ __forceinline__ bool front_at_or_after(float t, uint32_t idx) const { return fk >= key_of(t, idx); }
+    __device__ __forceinline__ void sift_up(int i, uint64_t k, float a) {
+        while (i > 0) {
+            const int up = (i - 1) / D;
+            const uint64_t uk = getk(up);
+            if (!(k < uk)) break;
+            put(i, uk, geta(up));
+            i = up;
+        }
+        put(i, k, a);
+        if (i == 0) fk = k;
     }
     // requires !full()
-    __device__ __forceinline__ void push(float t, uint32_t p, float a) {
-        int i = n++;
-        while (i > 0) {
-            const int up = (i - 1) >> 1;
-            float ut, ua;
-            uint32_t upp;
-            get(up, ut, upp, ua);
-            if (!less(t, p, ut, upp)) break;
-            put(i, ut, upp, ua);
-            i = up;
-        }
-        put(i, t, p, a);
-        if (i == 0) ft = t;
-    }
+    __device__ __forceinline__ void push(float t, uint32_t p, float a) { sift_up(n++, key_of(t, p), a); }
     // Full heap: keeps the smallest keys among the old entries and the new
     // one, so every pass composites at least one entry.  The largest key is
-    // on a leaf (slots n/2 .. n-1); it leaves unless the new entry is larger.
-    // Returns the key of the entry that does not stay.
+    // on a leaf (slots ceil((n - 1) / D) .. n - 1); it leaves unless the new
+    // entry is larger.  Returns the key of the entry that does not stay.
     __device__ __forceinline__ uint64_t push_full(float t, uint32_t p, float a) {
-        int m = n >> 1;
-        float mt, ma;
-        uint32_t mp;
-        get(m, mt, mp, ma);
+        const uint64_t k = key_of(t, p);
+        int m = (n + D - 2) / D;
+        uint64_t mk = getk(m);
         for (int i = m + 1; i < n; i++) {
-            float it, ia;
-            uint32_t ip;
-            get(i, it, ip, ia);
-            if (less(mt, mp, it, ip)) {
-                m = i; mt = it; mp = ip; ma = ia;
+            const uint64_t ik = getk(i);
+            if (ik > mk) { m = i; mk = ik; }
+        }
+        if (!(k < mk)) return k;
+        sift_up(m, k, a);
+        return mk;
+    }
+    // the keys and alphas of the sibling group starting at slot c (all of
+    // it below n or not: entries at or past n read as +inf keys)
+    __device__ __forceinline__ void group(int c, uint64_t (&gk)[D], float (&ga)[D]) const {
+        if (c < SLOTS) {
+#pragma unroll
+            for (int j = 0; j < D; j++) {
+                gk[j] = sk[(c + j) * STRIDE];
+                ga[j] = sa[(c + j) * STRIDE];
+            }
+        } else {
+            const int e = OFF + c - SLOTS;
+            static_assert(D % 2 == 0, "column groups are read in 16-byte pieces");
+            const ulonglong2* k2 = reinterpret_cast<const ulonglong2*>(ck + e);
+#pragma unroll
+            for (int j = 0; j < D / 2; j++) {
+                const ulonglong2 v = k2[j];
+                gk[2 * j] = v.x; gk[2 * j + 1] = v.y;
+            }
+            if (D % 4 == 0) {
+                const float4* a4 = reinterpret_cast<const float4*>(ca + e);
+#pragma unroll
+                for (int j = 0; j < D / 4; j++) {
+                    const float4 v = a4[j];
+                    ga[4 * j] = v.x; ga[4 * j + 1] = v.y; ga[4 * j + 2] = v.z; ga[4 * j + 3] = v.w;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < D; j++) ga[j] = ca[e + j];
             }
         }
-        if (!less(t, p, mt, mp)) return key_of(t, p);
-        const uint64_t out = key_of(mt, mp);
-        int i = m;
-        while (i > 0) {
-            const int up = (i - 1) >> 1;
-            float ut, ua;
-            uint32_t upp;
-            get(up, ut, upp, ua);
-            if (!less(t, p, ut, upp)) break;
-            put(i, ut, upp, ua);
-            i = up;
-        }
-        put(i, t, p, a);
-        if (i == 0) ft = t;
-        return out;
+#pragma unroll
+        for (int j = 0; j < D; j++)
+            if (c + j >= n) gk[j] = ~0ull;
     }
     // removes the root; requires !empty()
     __device__ __forceinline__ void pop() {
         n--;
         if (n == 0) {
-            ft = __int_as_float(0x7f800000);
+            fk = ~0ull;
             return;
         }
-        float lt, la;
-        uint32_t lp;
-        get(n, lt, lp, la);
+        const uint64_t lk = getk(n);
+        const float la = geta(n);
         int i = 0;
         while (true) {
-            int c = 2 * i + 1;
+            const int c = D * i + 1;
             if (c >= n) break;
-            float ct, ca;
-            uint32_t cp;
-            get(c, ct, cp, ca);
-            if (c + 1 < n) {
-                float dt, da;
-                uint32_t dp;
-                get(c + 1, dt, dp, da);
-                if (less(dt, dp, ct, cp)) {
-                    c = c + 1; ct = dt; cp = dp; ca = da;
-                }
-            }
-            if (!less(ct, cp, lt, lp)) break;
-            put(i, ct, cp, ca);
-            i = c;
+            uint64_t gk[D];
+            float ga[D];
+            group(c, gk, ga);
+            int m = 0;
+            uint64_t mk = gk[0];
+            float ma = ga[0];
+#pragma unroll
+            for (int j = 1; j < D; j++)
+                if (gk[j] < mk) { mk = gk[j]; ma = ga[j]; m = j; }
+            if (!(mk < lk)) break;
+            put(i, mk, ma);
+            i = c + m;
         }
-        put(i, lt, lp, la);
-        ft = st[0];
+        put(i, lk, la);
+        fk = sk[0];
     }
 };
 
@@ -381,7 +415,7 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
                                          const uint32_t* __restrict__ keysp, const uint2* __restrict__ rangesp,
                                          const DepthQuant* __restrict__ dqp, float* __restrict__ outp, bool batched,
                                          int K, int tile, uint32_t task, float4* stage, float* ring, uint4* ovf,
-                                         HeapBuf<CAP, kRasterThreads>& kb, WarpCounters& wc, RecChunk& rc) {
+                                         HeapBuf<kHeapArity, HeapSlots<CAP>::value, kRasterThreads>& kb, WarpCounters& wc, RecChunk& rc) {
     constexpr int HDR4 = Rec<KMAX>::HDR / 4;
     constexpr int STRIDE4 = Rec<KMAX>::STRIDE4;
     constexpr int kHalf4 = (HDR4 + 1) / 2;
@@ -421,8 +455,10 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
     // contributor records for the backward
     const bool rec_on = !BWD && A.rec_key != nullptr;
     const bool literal = fc.order_mode == DRK_ORDER_CACHE_SORT;
-    kb.init(ring + threadIdx.x, reinterpret_cast<uint32_t*>(ring) + CAP * kRasterThreads + threadIdx.x,
-            ring + 2 * CAP * kRasterThreads + threadIdx.x, literal ? nullptr : ovf, A.ovf_cap);
+    // shared heap: keys [slots][threads] (u64), then alphas [slots][threads]
+    constexpr int kSlots = HeapSlots<CAP>::value;
+    kb.init(reinterpret_cast<uint64_t*>(ring) + threadIdx.x, ring + 2 * kSlots * kRasterThreads + threadIdx.x,
+            literal ? nullptr : ovf, A.ovf_cap, literal ? CAP : 0);
     // Exact order with a bounded heap.  When a contributor finds the heap
     // full, the largest key among the heap and the new entry is dropped;
     // `lost` is the smallest dropped key (every key in the heap stays below
@@ -529,7 +565,7 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
         }
         if (kk < lo || kk >= lost) return;
         if (!kb.full()) {
-            if (kb.n >= CAP) wc.spills++;
+            if (kb.n >= HeapSlots<CAP>::value) wc.spills++;
             kb.push(t, j, a);
         } else {
             const uint64_t d = kb.push_full(t, j, a);
@@ -752,7 +788,7 @@ __global__ void __launch_bounds__(kRasterThreads, (BATCH || CAP >= 16) ? 4 : 5) 
     const uint32_t n_tasks = BATCH ? (uint32_t)A.n_batch_tiles * 8u : (uint32_t)(A.fc.tiles_x * A.fc.tiles_y) * 8u;
     WarpCounters wc;
 
-    HeapBuf<CAP, kRasterThreads> kb;
+    HeapBuf<kHeapArity, HeapSlots<CAP>::value, kRasterThreads> kb;
     RecChunk rc{0u, 0u};
 
     while (true) {
@@ -983,7 +1019,7 @@ __global__ void __launch_bounds__(kRecThreads) raster_backward_records_kernel(Ra
 template <int KMAX, int CAP>
 constexpr size_t raster_smem() {
     return (size_t)(kRasterThreads / 32) * 2 * kChunk * (Rec<KMAX>::HDR / 4) * sizeof(float4) +
-           (size_t)3 * CAP * kRasterThreads * sizeof(float);
+           (size_t)3 * HeapSlots<CAP>::value * kRasterThreads * sizeof(float);
 }
 
 // resident CTAs x SMs of one instantiation (computed once)
