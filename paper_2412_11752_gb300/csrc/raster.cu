@@ -92,6 +92,7 @@ struct HeapSlots {
 template <int D, int SLOTS, int STRIDE>
 struct HeapBuf {
     static_assert(SLOTS % D == 1 % D, "sibling groups must not straddle the shared slots");
+    static_assert(D % 4 == 0, "column groups are read in 16-byte pieces");
     static constexpr int OFF = 0;   // slot SLOTS + j is column entry OFF + j (groups start on multiples of D)
     uint64_t* sk;           // shared keys
     float* sa;              // shared alphas
@@ -168,40 +169,6 @@ struct HeapBuf {
         sift_up(m, k, a);
         return mk;
     }
-    // the keys and alphas of the sibling group starting at slot c (all of
-    // it below n or not: entries at or past n read as +inf keys)
-    __device__ __forceinline__ void group(int c, uint64_t (&gk)[D], float (&ga)[D]) const {
-        if (c < SLOTS) {
-#pragma unroll
-            for (int j = 0; j < D; j++) {
-                gk[j] = sk[(c + j) * STRIDE];
-                ga[j] = sa[(c + j) * STRIDE];
-            }
-        } else {
-            const int e = OFF + c - SLOTS;
-            static_assert(D % 2 == 0, "column groups are read in 16-byte pieces");
-            const ulonglong2* k2 = reinterpret_cast<const ulonglong2*>(ck + e);
-#pragma unroll
-            for (int j = 0; j < D / 2; j++) {
-                const ulonglong2 v = k2[j];
-                gk[2 * j] = v.x; gk[2 * j + 1] = v.y;
-            }
-            if (D % 4 == 0) {
-                const float4* a4 = reinterpret_cast<const float4*>(ca + e);
-#pragma unroll
-                for (int j = 0; j < D / 4; j++) {
-                    const float4 v = a4[j];
-                    ga[4 * j] = v.x; ga[4 * j + 1] = v.y; ga[4 * j + 2] = v.z; ga[4 * j + 3] = v.w;
-                }
-            } else {
-#pragma unroll
-                for (int j = 0; j < D; j++) ga[j] = ca[e + j];
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < D; j++)
-            if (c + j >= n) gk[j] = ~0ull;
-    }
     // removes the root; requires !empty()
     __device__ __forceinline__ void pop() {
         n--;
@@ -215,16 +182,55 @@ struct HeapBuf {
         while (true) {
             const int c = D * i + 1;
             if (c >= n) break;
+            // the smallest key of the sibling group c .. c + D - 1 (slots at
+            // or past n read as +inf); alpha is selected along with it
             uint64_t gk[D];
-            float ga[D];
-            group(c, gk, ga);
+            uint64_t mk;
+            float ma;
             int m = 0;
-            uint64_t mk = gk[0];
-            float ma = ga[0];
+            if (c < SLOTS) {
 #pragma unroll
-            for (int j = 1; j < D; j++)
-                if (gk[j] < mk) { mk = gk[j]; ma = ga[j]; m = j; }
-            if (!(mk < lk)) break;
+                for (int j = 0; j < D; j++) gk[j] = sk[(c + j) * STRIDE];
+                if (c + D > n) {
+#pragma unroll
+                    for (int j = 1; j < D; j++)
+                        if (c + j >= n) gk[j] = ~0ull;
+                }
+                mk = gk[0];
+#pragma unroll
+                for (int j = 1; j < D; j++)
+                    if (gk[j] < mk) { mk = gk[j]; m = j; }
+                if (!(mk < lk)) break;
+                ma = sa[(c + m) * STRIDE];   // one shared load for the chosen child
+            } else {
+                // global: keys and alphas of the group in aligned 16-byte
+                // pieces, loaded together (a dependent load costs more here)
+                const int e = OFF + c - SLOTS;
+                float ga[D];
+                const ulonglong2* k2 = reinterpret_cast<const ulonglong2*>(ck + e);
+#pragma unroll
+                for (int j = 0; j < D / 2; j++) {
+                    const ulonglong2 v = k2[j];
+                    gk[2 * j] = v.x; gk[2 * j + 1] = v.y;
+                }
+                const float4* a4 = reinterpret_cast<const float4*>(ca + e);
+#pragma unroll
+                for (int j = 0; j < D / 4; j++) {
+                    const float4 v = a4[j];
+                    ga[4 * j] = v.x; ga[4 * j + 1] = v.y; ga[4 * j + 2] = v.z; ga[4 * j + 3] = v.w;
+                }
+                if (c + D > n) {
+#pragma unroll
+                    for (int j = 1; j < D; j++)
+                        if (c + j >= n) gk[j] = ~0ull;
+                }
+                mk = gk[0];
+                ma = ga[0];
+#pragma unroll
+                for (int j = 1; j < D; j++)
+                    if (gk[j] < mk) { mk = gk[j]; ma = ga[j]; m = j; }
+                if (!(mk < lk)) break;
+            }
             put(i, mk, ma);
             i = c + m;
         }
