@@ -140,11 +140,16 @@ __global__ void __launch_bounds__(kSortThreads) radix_upsweep_kernel(const uint3
     for (int i = threadIdx.x; i < kWarps * kBins; i += kSortThreads) (&cnt[0][0])[i] = 0;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kSortTile + (int64_t)wid * kWarpItems;
-#pragma unroll 4
+    // all of the warp's loads first, then the counting: the loads overlap
+    uint32_t dg[kWarpItems / 32];
+#pragma unroll
     for (int r = 0; r < kWarpItems / 32; r++) {
         const int64_t i = base + r * 32 + lane;
-        if (i < n) atomicAdd(&cnt[wid][(__ldg(keys + i) >> shift) & 0xffu], 1u);
+        dg[r] = i < n ? (__ldg(keys + i) >> shift) & 0xffu : kBins;
     }
+#pragma unroll
+    for (int r = 0; r < kWarpItems / 32; r++)
+        if (dg[r] < kBins) atomicAdd(&cnt[wid][dg[r]], 1u);
     __syncthreads();
     const int d = threadIdx.x;   // one bin per thread
     uint32_t s = 0;
@@ -153,7 +158,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_upsweep_kernel(const uint3
     hist[(int64_t)d * nblocks + blockIdx.x] = s;
 }
 
-__global__ void __launch_bounds__(kSortThreads) radix_downsweep_kernel(
+__global__ void __launch_bounds__(kSortThreads, 3) radix_downsweep_kernel(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, uint32_t* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out, int64_t n, int shift, const uint64_t* __restrict__ hist_scan, int64_t nblocks) {
     __shared__ uint32_t skey[kSortTile];
@@ -168,12 +173,19 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep_kernel(
     const int64_t wbase = bbase + (int64_t)wid * kWarpItems;
     const uint32_t lt_mask = (1u << lane) - 1u;
     uint32_t k[kWarpItems / 32], v[kWarpItems / 32], rk[kWarpItems / 32];
+    // all of the warp's loads first (the ranking below is a chain of warp
+    // barriers, which loads are not moved across), then the ranking
 #pragma unroll
     for (int r = 0; r < kWarpItems / 32; r++) {
         const int64_t i = wbase + r * 32 + lane;
         const bool valid = i < n;
         k[r] = valid ? __ldg(keys_in + i) : 0u;
         v[r] = valid ? __ldg(vals_in + i) : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < kWarpItems / 32; r++) {
+        const int64_t i = wbase + r * 32 + lane;
+        const bool valid = i < n;
         const int d = valid ? (int)((k[r] >> shift) & 0xffu) : -1;
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
         const uint32_t before = valid ? wcnt[wid][d] : 0u;
@@ -296,11 +308,13 @@ void launch_batch_order_keys(const uint2* ranges, int n_tiles, int slot, uint32_
 }
 
 // ---------------------------------------------------------------------------
-// Grouping of the contributor records by pair: the forward counted the
-// records of every pair, so an exclusive scan gives each pair's start and
-// one scatter pass places every record's slot in its pair's range.  The
-// scatter aggregates over the warp: lanes holding the same pair
-// (neighbouring slots usually do) take a single atomic for the group.
+// Grouping of the contributor records by primitive: the forward counted the
+// records of every primitive, so an exclusive scan gives each primitive's
+// start and one scatter pass places every record's slot in its
+// primitive's range.  The scatter aggregates over the warp: lanes holding
+// the same primitive (neighbouring slots often do) take a single atomic
+// for the group.  (A block-wide aggregation through a shared hash table,
+// with the slots of each primitive written as one run, measured slower.)
 __global__ void record_scatter_kernel(const uint32_t* __restrict__ key, uint32_t n, uint32_t n_keys,
                                       unsigned long long* __restrict__ cursor, uint32_t* __restrict__ out_idx) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -313,9 +327,17 @@ __global__ void record_scatter_kernel(const uint32_t* __restrict__ key, uint32_t
     base = __shfl_sync(0xffffffffu, base, leader);
     if (!valid) return;
     // the counts cover every record, so pos < n; the check keeps a
-    // miscounted pair from writing past the array
+    // miscounted primitive from writing past the array
     const unsigned long long pos = base + (unsigned long long)__popc(peers & ((1u << lane) - 1u));
     if (pos < n) out_idx[pos] = i;
+}
+
+// out_idx[offs[n_keys] .. n) = no record
+__global__ void record_tail_kernel(const unsigned long long* __restrict__ total, uint32_t n,
+                                   uint32_t* __restrict__ out_idx) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = *total + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        out_idx[i] = kNoSlot;
 }
 
 size_t record_sort_scratch_bytes(uint32_t n_keys) {
@@ -324,13 +346,21 @@ size_t record_sort_scratch_bytes(uint32_t n_keys) {
 
 void group_records(const uint32_t* key, uint32_t n, uint32_t n_keys, const uint32_t* count, uint32_t* out_idx,
                    void* scratch, cudaStream_t st) {
-    cudaMemsetAsync(out_idx, 0xff, sizeof(uint32_t) * (size_t)n, st);
-    if (n == 0 || n_keys == 0) return;
+    if (n == 0) return;
+    if (n_keys == 0) {
+        cudaMemsetAsync(out_idx, 0xff, sizeof(uint32_t) * (size_t)n, st);
+        return;
+    }
     uint64_t* offs = reinterpret_cast<uint64_t*>(scratch);
     void* sscr = reinterpret_cast<void*>((reinterpret_cast<uintptr_t>(offs + (size_t)n_keys + 1) + 15) & ~uintptr_t(15));
     exclusive_scan_u32_u64(count, offs, (int64_t)n_keys, sscr, st);
+    // only the unused tail needs the no-record mark (the scatter writes the
+    // rest): out_idx[total .. n), total = offs[n_keys]
+    record_tail_kernel<<<1024, 256, 0, st>>>(reinterpret_cast<const unsigned long long*>(offs + n_keys), n, out_idx);
+    note_launch();
     record_scatter_kernel<<<(n + 255u) / 256u, 256, 0, st>>>(key, n, n_keys, reinterpret_cast<unsigned long long*>(offs),
-                                                           out_idx); note_launch();
+                                                           out_idx);
+    note_launch();
 }
 
 __global__ void iota_kernel(uint32_t* __restrict__ v, uint32_t n) {
