@@ -862,7 +862,7 @@ __global__ void __launch_bounds__(kRasterThreads, (BATCH || CAP >= 16) ? 4 : 5) 
 // primitive changes are the partial sums added over the warp and sent to
 // global memory, one atomic per parameter.  Records of tiles marked for
 // the replay are skipped.
-constexpr int kRecWin = 16;          // 32-record windows per warp
+constexpr int kRecWin = 32;          // 32-record windows per warp
 constexpr int kRecThreads = 128;     // 4 warps per block
 
 template <int KMAX>
