@@ -785,6 +785,7 @@ __global__ void __launch_bounds__(kRasterThreads, (BATCH || CAP >= 16) ? 4 : 5) 
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float4* stage = stage_all + warp * (2 * kChunk * HDR4);
+    __shared__ FrameConst fc_sh[BATCH ? kWarps : 1];   // batch: the current task's frame constants
     const int slot = blockIdx.x * kWarps + warp;
     // lane-contiguous columns: a lane's deep heap levels are adjacent, and
     // the footprint is what the pixels actually hold
@@ -805,8 +806,18 @@ __global__ void __launch_bounds__(kRasterThreads, (BATCH || CAP >= 16) ? 4 : 5) 
         const int tile = A.tile_order ? (int)A.tile_order[task >> 3] : (int)(task >> 3);
         if (BATCH) {
             const FrameSlot& sl = A.slots[(uint32_t)tile >> 20];
-            run_task<KMAX, CAP, BWD, false>(A, sl.fc, sl.rec, sl.rgb, sl.vals, sl.keys, sl.ranges, sl.dq, sl.out_rgb, true,
-                                     sl.K, tile & ((1 << 20) - 1), task, stage, ring, ovf, kb, wc, rc);
+            // the frame's constants, read in every evaluation, into this
+            // warp's shared slot (the single-frame kernel has them in its
+            // parameter space; read through the global slot they cost an
+            // L1 access per use)
+            constexpr int kFcWords = (int)(sizeof(FrameConst) / sizeof(int));
+            static_assert(sizeof(FrameConst) % sizeof(int) == 0 && kFcWords <= 32, "frame constants fit one warp copy");
+            __syncwarp();
+            if (lane < kFcWords) reinterpret_cast<int*>(&fc_sh[warp])[lane] = reinterpret_cast<const int*>(&sl.fc)[lane];
+            __syncwarp();
+            run_task<KMAX, CAP, BWD, false>(A, fc_sh[warp], sl.rec, sl.rgb, sl.vals, sl.keys, sl.ranges, sl.dq,
+                                            sl.out_rgb, true, sl.K, tile & ((1 << 20) - 1), task, stage, ring, ovf, kb,
+                                            wc, rc);
             // the warp that finishes a frame's last task publishes it: its
             // image is complete in device memory once the flag is visible
             __syncwarp();

@@ -12,7 +12,8 @@
 //                         tile first within a frame
 //   one raster launch     persistent warps over every tile of every frame
 // and records a completion event.  The next batch's phases A/B run on the
-// other stream while this raster runs.  Each pixel's arithmetic and
+// other stream while this raster runs; its raster waits for this one to
+// end (one raster on the SMs at a time).  Each pixel's arithmetic and
 // compositing order are those of drk_render, so the images are identical.
 #include <algorithm>
 #include <chrono>
@@ -419,6 +420,13 @@ void run_batch(drk_serve* S, int s, std::vector<Item>& items, int* countdown, st
         cudaMemcpyAsync(S->d_slots[s], S->h_slots[s], sizeof(FrameSlot) * (size_t)live, cudaMemcpyHostToDevice, st);
         cudaMemcpyAsync(S->d_left[s], S->h_left[s], sizeof(unsigned int) * (size_t)live, cudaMemcpyHostToDevice, st);
         radix_sort_pairs(okeys, ovals, okalt, ovalt, T, 26, oscr, st);
+        // one raster at a time: this batch's raster starts when the other
+        // stream's has ended (the event holds its latest batch's raster
+        // end; an idle stream's has long completed).  Phases A/B and the
+        // tile order above ran beside that raster; the older batch's
+        // frames keep every SM to themselves, so a heavy frame is not
+        // slowed by the requests that arrive while it rasterises.
+        cudaStreamWaitEvent(st, S->ev_tl[1 - s][3], 0);
         cudaEventRecord(S->ev_tl[s][2], st);
         RasterArgs R;
         std::memset(&R, 0, sizeof(R));
