@@ -102,6 +102,9 @@ typedef struct {
 #define ORD_FLAG_DEPTH_TIE 4   /* two contributors with near-equal depth and visible order effect */
 #define ORD_FLAG_STEEP     8   /* float32 error of the alphas could exceed half the tolerance
                                   (near-hard edges: Psi's middle slope (1+tau)/(1-tau)) */
+#define ORD_FLAG_KINK      32  /* a composited contributor within float32 rounding of a point where
+                                  the derivative of its alpha_tilde changes branch (see branch_kink):
+                                  images are continuous there, gradients take a side */
 #define ORD_FLAG_CULL      16  /* a contributor whose paper-culling decision for the pixel's
                                   tile is within float32 margin */
 
@@ -460,6 +463,7 @@ typedef struct {
     int64_t idx;
     double alpha, dalpha;   /* alpha_tilde and its float32 error model */
     int cull_und;           /* the paper's culling decision is within float32 margin */
+    int kink;               /* alpha_tilde within float32 rounding of a branch point (branch_kink) */
 } contrib;
 
 /* Rounding-error model of a float32 evaluation of alpha_tilde.  It decides
@@ -490,71 +494,150 @@ typedef struct {
  * in; Eq. 6 - Eq. 7 are continuous across sectors.  For the filter of
  * Eq. 10 the exponent carries 4e-6 (1 + 2 X_f) / 2 plus the grazing term.
  * A clamped alpha has no error.                                            */
-static double alpha_fp32_error(const ord_params *P, int64_t i, const pair_eval *pe)
+/* float32 error of the filter branch of Eq. 10 (see above) */
+static double filter_alpha_err(const pair_eval *pe, double o)
 {
-    if (pe->clamped) return 0.0;
+    double Xf = -log(pe->filt / o);
+    return pe->filt * (0.5 * 4e-6 * (1.0 + 2.0 * Xf) + Xf * 2.4e-7 / pe->cosv);
+}
+
+/* float32 error of the kernel branch (Eq. 6 - Eq. 9, see above); *dg gets
+ * the matching bound on g of Eq. 8 (the same perturbations, measured on g) */
+static double kernel_alpha_err(const ord_params *P, int64_t i, const pair_eval *pe, double *dg)
+{
     const double tau = P->tau[i], o = P->opacity[i];
     double dnorm = sqrt(dot3(pe->d, pe->d));
     double cosv = fabs(pe->dn) / dnorm;
-    if (pe->use_filter) {
-        double Xf = -log(pe->filt / o);
-        return pe->filt * (0.5 * 4e-6 * (1.0 + 2.0 * Xf) + Xf * 2.4e-7 / cosv);
-    }
     const int K = P->K;
     const double *s0 = P->scale + (int64_t)K * i, *th0 = P->theta + (int64_t)K * i;
     const double eta = P->eta[i];
-    const double a0 = pe->ke.alpha;
+    const double a0 = pe->ke.alpha, g0 = pe->ke.g;
     double dpsi, dtau;
     psi_grad(pe->ke.g, tau, &dpsi, &dtau);
     double err = o * dpsi * pe->ke.g * 0.5 * 4e-6 * (1.0 + pe->ke.E) + 3e-7 * a0;
+    double errg = pe->ke.g * 0.5 * 4e-6 * (1.0 + pe->ke.E);
     double r2 = sqrt(pe->ke.r2sq);
-    if (r2 <= 0.0) return err;
+    if (r2 <= 0.0) {
+        *dg = errg;
+        return err;
+    }
     const double d_r = 2e-6 + (pe->t * dnorm / r2) * 1.2e-7 / cosv;
     const double d_phi = d_r + 5e-7;
     double s[ORD_MAXK], th[ORD_MAXK];
     memcpy(s, s0, sizeof(double) * (size_t)K);
     memcpy(th, th0, sizeof(double) * (size_t)K);
     kernel_eval ke;
-    double worst;
+    double worst, worstg;
     /* radial */
-    worst = 0.0;
+    worst = worstg = 0.0;
     for (int sg = -1; sg <= 1; sg += 2) {
         const double f = 1.0 + sg * d_r;
         kernel_uv(K, s, th, eta, tau, o, pe->u * f, pe->v * f, &ke);
         worst = fmax(worst, fabs(ke.alpha - a0));
+        worstg = fmax(worstg, fabs(ke.g - g0));
     }
     err += worst;
+    errg += worstg;
     /* angular */
-    worst = 0.0;
+    worst = worstg = 0.0;
     for (int sg = -1; sg <= 1; sg += 2) {
         const double c = cos(sg * d_phi), sn = sin(sg * d_phi);
         kernel_uv(K, s, th, eta, tau, o, c * pe->u - sn * pe->v, sn * pe->u + c * pe->v, &ke);
         worst = fmax(worst, fabs(ke.alpha - a0));
+        worstg = fmax(worstg, fabs(ke.g - g0));
     }
     err += worst;
+    errg += worstg;
     /* sector endpoints and scales of the pair's sector (each one alone;
      * angles stay ascending because every gap is far above 5e-7) */
     const int ks[2] = {pe->ke.k, pe->ke.k1};
     for (int e = 0; e < 2; e++) {
         const int k = ks[e];
-        worst = 0.0;
+        worst = worstg = 0.0;
         for (int sg = -1; sg <= 1; sg += 2) {
             th[k] = th0[k] + sg * 5e-7;
             kernel_uv(K, s, th, eta, tau, o, pe->u, pe->v, &ke);
             worst = fmax(worst, fabs(ke.alpha - a0));
+            worstg = fmax(worstg, fabs(ke.g - g0));
         }
         th[k] = th0[k];
         err += worst;
-        worst = 0.0;
+        errg += worstg;
+        worst = worstg = 0.0;
         for (int sg = -1; sg <= 1; sg += 2) {
             s[k] = s0[k] * (1.0 + sg * 3e-7);
             kernel_uv(K, s, th, eta, tau, o, pe->u, pe->v, &ke);
             worst = fmax(worst, fabs(ke.alpha - a0));
+            worstg = fmax(worstg, fabs(ke.g - g0));
         }
         s[k] = s0[k];
         err += worst;
+        errg += worstg;
     }
+    *dg = errg;
     return err;
+}
+
+static double alpha_fp32_error(const ord_params *P, int64_t i, const pair_eval *pe)
+{
+    if (pe->clamped) return 0.0;
+    if (pe->use_filter) return filter_alpha_err(pe, P->opacity[i]);
+    double dg;
+    return kernel_alpha_err(P, i, pe, &dg);
+}
+
+/* Does alpha_tilde of this contributing pair sit, within float32 rounding,
+ * at a point where its derivative changes branch?  Four such points:
+ *   - g of Eq. 8 at a breakpoint of Psi (Eq. 9), g = (1 + tau)/4 or
+ *     (3 - tau)/4, while the kernel sets alpha_tilde: Psi is continuous
+ *     there but its slope jumps from (1 - tau)/(1 + tau) to its inverse
+ *     (a factor 40000 at tau = 0.99), and so do its tau derivatives;
+ *   - the kernel and the filter equal in the max of Eq. 10;
+ *   - max(kernel, filter) at the clamp alpha_max;
+ *   - the polar angle at a sector boundary theta_k (Eq. 6 - Eq. 7).
+ * The image is continuous at all four, so it needs no flag; the gradient
+ * is not, and a float32 evaluation on the other side of the point is
+ * equally right.  The margins are the float32 error models of g and of the
+ * two alpha branches, plus the rounding of the breakpoints and of alpha_max
+ * to float32.                                                              */
+static int branch_kink(const ord_params *P, int64_t i, const pair_eval *pe, const ord_options *opt)
+{
+    const double tau = P->tau[i], o = P->opacity[i];
+    double dg;
+    const double dk = kernel_alpha_err(P, i, pe, &dg);
+    const double ak = pe->ke.alpha;
+    const double df = pe->filt_on && pe->filt > 0.0 ? filter_alpha_err(pe, o) : 0.0;
+    const double af = pe->filt_on ? pe->filt : 0.0;
+    const double raw = fmax(ak, af);
+    const double draw = ak >= af ? dk : df;
+    /* the clamp */
+    if (fabs(raw - opt->alpha_max) <= draw + 1e-7 * opt->alpha_max) return 1;
+    if (pe->clamped) return 0;
+    /* the max of Eq. 10 */
+    if (pe->filt_on && fabs(ak - af) <= dk + df + 1e-12) return 1;
+    if (pe->use_filter) return 0;
+    /* the breakpoints of Psi (no slope jump when tau = 0) */
+    if (fabs(tau) > 1e-6) {
+        const double g = pe->ke.g;
+        const double b1 = 0.25 * (1.0 + tau), b2 = 0.25 * (3.0 - tau);
+        if (fabs(g - b1) <= dg + 1e-7 * b1 || fabs(g - b2) <= dg + 1e-7 * b2) return 1;
+    }
+    /* a sector boundary: the polar angle within its float32 error (the
+     * error model's angle term plus the endpoint's own 5e-7) of theta_k or
+     * theta_k+1.  Eq. 6 - Eq. 7 are continuous there, but the L1 term
+     * |a| + |b| changes basis and has a kink, and the angle derivatives
+     * change sector.  Near the centre every angle is uncertain, but the
+     * jump of the derivative shrinks with the radius: below 1e-3 of the
+     * sector's smaller scale it is negligible and not flagged */
+    const double r2 = sqrt(pe->ke.r2sq);
+    const double *sc = P->scale + (int64_t)P->K * i;
+    if (r2 > 1e-3 * fmin(sc[pe->ke.k], sc[pe->ke.k1])) {
+        const double dnorm = sqrt(dot3(pe->d, pe->d));
+        const double cosv = fabs(pe->dn) / dnorm;
+        const double d_phi = 2e-6 + (pe->t * dnorm / r2) * 1.2e-7 / cosv + 5e-7 + 5e-7;
+        if (pe->ke.phi - pe->ke.th_k <= d_phi || pe->ke.th_k1 - pe->ke.phi <= d_phi) return 1;
+    }
+    return 0;
 }
 
 /* A batch of (pixel, primitive) pairs: alpha_tilde (0 where the ray misses
@@ -854,6 +937,7 @@ static int64_t gather_contributors(const ord_params *P, const ord_camera *cam, c
                     und[*n_und].alpha = pe.alpha_tilde;
                     und[*n_und].dalpha = 0.0;
                     und[*n_und].cull_und = 1;
+                    und[*n_und].kink = 0;
                     (*n_und)++;
                 }
                 continue;
@@ -866,6 +950,7 @@ static int64_t gather_contributors(const ord_params *P, const ord_camera *cam, c
             buf[cnt].alpha = pe.alpha_tilde;
             buf[cnt].dalpha = alpha_fp32_error(P, i, &pe);
             buf[cnt].cull_und = undecided;
+            buf[cnt].kink = branch_kink(P, i, &pe, opt);
             cnt++;
         }
     }
@@ -977,6 +1062,7 @@ int ord_render(const ord_params *P, const ord_camera *cam, const ord_options *op
                 }
                 budget += T * da * 2.0 * cm;
                 if (j == nc) break;
+                if (buf[j].kink) flag |= ORD_FLAG_KINK;
                 if (buf[j].cull_und) extra += T * a * 2.0 * cm;
                 /* near-equal depths whose swap is visible */
                 for (int64_t l = j + 1; opt->order_mode == 0 && l < cnt && buf[l].t - buf[j].t <= 2e-6 * buf[l].t; l++) {

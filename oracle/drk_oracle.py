@@ -32,6 +32,7 @@ FLAG_T_MIN = 2
 FLAG_DEPTH_TIE = 4
 FLAG_STEEP = 8
 FLAG_CULL = 16
+FLAG_KINK = 32          # a composited alpha within float32 rounding of a derivative branch point
 
 
 @dataclass

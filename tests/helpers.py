@@ -34,6 +34,15 @@ def excluded(flags: np.ndarray) -> np.ndarray:
     return (flags & (O.FLAG_T_MIN | O.FLAG_DEPTH_TIE | O.FLAG_STEEP | O.FLAG_CULL)) != 0
 
 
+def grad_excluded(flags: np.ndarray) -> np.ndarray:
+    """Pixels that carry no dL in gradient tests: the excluded ones, and
+    those with a composited alpha within float32 rounding of a point where
+    its derivative changes branch (a breakpoint of Psi, Eq. 9; the max of
+    Eq. 10; the alpha_max clamp), where the two one-sided gradients differ
+    and either is right."""
+    return excluded(flags) | ((flags & O.FLAG_KINK) != 0)
+
+
 def image_parity(gpu_rgb: np.ndarray, ref: dict, max_over_strict: int = 2, what: str = "") -> dict:
     """Every pixel of a GPU image against the oracle.
 
