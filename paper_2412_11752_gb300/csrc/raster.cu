@@ -953,26 +953,28 @@ __global__ void __launch_bounds__(kRecThreads) raster_backward_records_kernel(Ra
     float* H = acc.sh + (A_NFIX + KMAX) * 32 + lane;   // theta column
 
     // software pipeline: the records of window w + 1 and the slots of
-    // window w + 2 are loaded while window w is computed
+    // window w + 2 are loaded while window w is computed.  Records and
+    // slots are read once: streaming loads (evict first) keep them from
+    // evicting the per-pixel inputs and the primitive headers from L2
     auto load_rec = [&](uint32_t slot, uint4& r0, uint4& r1) {
         r0 = make_uint4(kNoSlot, 0u, 0u, 0u);
         r1 = make_uint4(0u, 0u, 0u, 0u);
         if (slot < A.rec_cap) {
-            r0 = A.rec_rd[2 * (size_t)slot];
-            r1 = A.rec_rd[2 * (size_t)slot + 1];
+            r0 = __ldcs(A.rec_rd + 2 * (size_t)slot);
+            r1 = __ldcs(A.rec_rd + 2 * (size_t)slot + 1);
         }
     };
     uint64_t i = base + lane;
     uint4 r0, r1;
-    load_rec(i < n ? sslot[i] : kNoSlot, r0, r1);
-    uint32_t slot_n = i + 32 < n ? sslot[i + 32] : kNoSlot;
+    load_rec(i < n ? __ldcs(sslot + i) : kNoSlot, r0, r1);
+    uint32_t slot_n = i + 32 < n ? __ldcs(sslot + i + 32) : kNoSlot;
     uint32_t gcur = kNoSlot;   // primitive of the partial sums (warp-uniform)
     for (int w = 0; w < kRecWin; w++) {
         if (base + 32u * w >= n) break;
         uint4 n0, n1;
         load_rec(w + 1 < kRecWin ? slot_n : kNoSlot, n0, n1);
         const uint64_t i2 = i + 64;
-        const uint32_t slot_nn = (w + 2 < kRecWin && i2 < n) ? sslot[i2] : kNoSlot;
+        const uint32_t slot_nn = (w + 2 < kRecWin && i2 < n) ? __ldcs(sslot + i2) : kNoSlot;
 
         uint32_t g = r0.x;   // primitive index
         PairGrad pg;
