@@ -685,35 +685,86 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
                 const bool ok = drain(!pass_done, thr0);
                 if (!pass_done && (!ok || ps.done)) pass_done = true;
             }
-            for (uint32_t jj = 0; jj < cn; jj++) {
-                const uint32_t idx = __shfl_sync(0xffffffffu, idx_a, jj);
-                float h[R_FIX4 * 4];
-                Geo gm;
-                bool geo = false;
-                const float4* sg = stage + (buf * kChunk + jj) * HDR4;
-                if (!pass_done) {
-                    wc.evals++;
+            if (!literal) {
+                // exact order: two items per step, both evaluated before
+                // either is offered (in list order), so that their two
+                // dependency chains interleave
+                for (uint32_t jj = 0; jj < cn; jj += 2) {
+                    const bool two = jj + 1 < cn;
+                    const uint32_t idxA = __shfl_sync(0xffffffffu, idx_a, jj);
+                    const uint32_t idxB = __shfl_sync(0xffffffffu, idx_a, two ? jj + 1 : jj);
+                    const float4* sgA = stage + (buf * kChunk + jj) * HDR4;
+                    const float4* sgB = sgA + HDR4;
+                    float hA[R_FIX4 * 4], hB[R_FIX4 * 4];
+                    Geo gA{0.f, 0.f, 0.f, 0.f}, gB{0.f, 0.f, 0.f, 0.f};
+                    bool geoA = false, geoB = false;
+                    if (!pass_done) {
+                        wc.evals += two ? 2 : 1;
 #pragma unroll
-                    for (int q = 0; q < R_GEO4; q++) {
-                        const float4 v = sg[q];
-                        h[4 * q] = v.x; h[4 * q + 1] = v.y; h[4 * q + 2] = v.z; h[4 * q + 3] = v.w;
+                        for (int q = 0; q < R_GEO4; q++) {
+                            const float4 v = sgA[q];
+                            hA[4 * q] = v.x; hA[4 * q + 1] = v.y; hA[4 * q + 2] = v.z; hA[4 * q + 3] = v.w;
+                            const float4 w = sgB[q];
+                            hB[4 * q] = w.x; hB[4 * q + 1] = w.y; hB[4 * q + 2] = w.z; hB[4 * q + 3] = w.w;
+                        }
+                        geoA = eval_geometry(hA, pr, fc.near_plane, gA);
+                        geoB = two && eval_geometry(hB, pr, fc.near_plane, gB);
                     }
-                    geo = eval_geometry(h, pr, fc.near_plane, gm);
-                }
-                if (__any_sync(0xffffffffu, geo)) {
-                    if (geo) {
-                        wc.geo++;
+                    if (__any_sync(0xffffffffu, geoA || geoB)) {
+                        wc.geo += (geoA ? 1 : 0) + (geoB ? 1 : 0);
 #pragma unroll
                         for (int q = R_GEO4; q < R_FIX4; q++) {
+                            const float4 v = sgA[q];
+                            hA[4 * q] = v.x; hA[4 * q + 1] = v.y; hA[4 * q + 2] = v.z; hA[4 * q + 3] = v.w;
+                            const float4 w = sgB[q];
+                            hB[4 * q] = w.x; hB[4 * q + 1] = w.y; hB[4 * q + 2] = w.z; hB[4 * q + 3] = w.w;
+                        }
+                        float aA = 0.f, aB = 0.f;
+                        const bool okA = eval_kernel<KMAX, false>(hA, reinterpret_cast<const float*>(sgA), K, pr, gA,
+                                                                  fc.alpha_min, fc.alpha_max, aA) && geoA;
+                        const bool okB = eval_kernel<KMAX, false>(hB, reinterpret_cast<const float*>(sgB), K, pr, gB,
+                                                                  fc.alpha_min, fc.alpha_max, aB) && geoB;
+                        if (okA) {
+                            wc.contrib++;
+                            offer(gA.t, idxA, aA, key_of(gA.t, idxA));
+                        }
+                        if (okB) {
+                            wc.contrib++;
+                            offer(gB.t, idxB, aB, key_of(gB.t, idxB));
+                        }
+                    }
+                }
+            } else {
+                for (uint32_t jj = 0; jj < cn; jj++) {
+                    const uint32_t idx = __shfl_sync(0xffffffffu, idx_a, jj);
+                    float h[R_FIX4 * 4];
+                    Geo gm;
+                    bool geo = false;
+                    const float4* sg = stage + (buf * kChunk + jj) * HDR4;
+                    if (!pass_done) {
+                        wc.evals++;
+    #pragma unroll
+                        for (int q = 0; q < R_GEO4; q++) {
                             const float4 v = sg[q];
                             h[4 * q] = v.x; h[4 * q + 1] = v.y; h[4 * q + 2] = v.z; h[4 * q + 3] = v.w;
                         }
-                        float a;
-                        if (eval_kernel<KMAX, false>(h, reinterpret_cast<const float*>(sg), K, pr, gm, fc.alpha_min,
-                                                     fc.alpha_max, a)) {
-                            wc.contrib++;
-                            offer(gm.t, idx, a, key_of(gm.t, idx));
-                            if (ps.done) pass_done = true;
+                        geo = eval_geometry(h, pr, fc.near_plane, gm);
+                    }
+                    if (__any_sync(0xffffffffu, geo)) {
+                        if (geo) {
+                            wc.geo++;
+    #pragma unroll
+                            for (int q = R_GEO4; q < R_FIX4; q++) {
+                                const float4 v = sg[q];
+                                h[4 * q] = v.x; h[4 * q + 1] = v.y; h[4 * q + 2] = v.z; h[4 * q + 3] = v.w;
+                            }
+                            float a;
+                            if (eval_kernel<KMAX, false>(h, reinterpret_cast<const float*>(sg), K, pr, gm, fc.alpha_min,
+                                                         fc.alpha_max, a)) {
+                                wc.contrib++;
+                                offer(gm.t, idx, a, key_of(gm.t, idx));
+                                if (ps.done) pass_done = true;
+                            }
                         }
                     }
                 }
