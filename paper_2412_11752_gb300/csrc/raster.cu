@@ -30,13 +30,46 @@
 
 namespace drk {
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+// Staging of record headers by the bulk-copy (TMA) engine: one
+// cp.async.bulk per header row, completed on an mbarrier of the warp.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// one arrival that also announces the bytes the copies will deliver
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* b, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0u;
+}
+// global -> shared bulk copy of `bytes` (16-byte aligned ends and size)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* b) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(b))
+                 : "memory");
+}
+// bound of a stage wait (try_wait polls, each with the hardware's own
+// time limit): far beyond any copy's latency; past it the raster records
+// DRK_ERR_TIMEOUT, and the warp issues no further copies and waits no
+// more (its images are then wrong, but the kernel ends)
+constexpr int kStageSpin = 1 << 20;
+
+// The warp's two stage buffers: their mbarriers, the parity of each one's
+// current phase and which ones have copies in flight.
+struct StageSync {
+    uint64_t* mbar;        // 2 mbarriers in shared memory
+    unsigned phase;        // bit b: parity of buffer b's current phase
+    unsigned pending;      // bit b: buffer b has copies not yet waited for
+    bool failed;           // a wait ran out: no more copies or waits
+};
 
 constexpr int kMaxPasses = 1 << 20;
 constexpr int kRasterThreads = 128;   // persistent raster CTAs: 4 independent warps
@@ -420,11 +453,11 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
                                          const float4* __restrict__ rgbp, const uint32_t* __restrict__ valsp,
                                          const uint32_t* __restrict__ keysp, const uint2* __restrict__ rangesp,
                                          const DepthQuant* __restrict__ dqp, float* __restrict__ outp, bool batched,
-                                         int K, int tile, uint32_t task, float4* stage, float* ring, uint4* ovf,
+                                         int K, int tile, uint32_t task, float4* stage, StageSync& ss, float* ring,
+                                         uint4* ovf,
                                          HeapBuf<kHeapArity, HeapSlots<CAP>::value, kRasterThreads>& kb, WarpCounters& wc, RecChunk& rc) {
     constexpr int HDR4 = Rec<KMAX>::HDR / 4;
     constexpr int STRIDE4 = Rec<KMAX>::STRIDE4;
-    constexpr int kHalf4 = (HDR4 + 1) / 2;
     const int lane = threadIdx.x & 31;
     const DepthQuant dq = *dqp;
     const uint32_t qmask = (1u << dq.depth_bits) - 1u;
@@ -621,17 +654,40 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
     };
 
     // copies the headers of the chunk starting at list position base, whose
-    // indices lanes 0 .. kChunk-1 hold in idxv, into the stage buffer bufp
-    // (two lanes per item)
-    auto stage_chunk = [&](uint32_t base, uint32_t idxv, float4* bufp) {
-        const int it = lane >> 1, half = lane & 1;
-        const uint32_t id = __shfl_sync(0xffffffffu, idxv, it);
-        if (base + (uint32_t)it < L) {
-            const float4* src = rec4 + (size_t)id * STRIDE4;
-#pragma unroll
-            for (int q = half * kHalf4; q < (half + 1) * kHalf4; q++)
-                if (q < HDR4) cp_async16(bufp + it * HDR4 + q, src + q);
+    // indices lanes 0 .. kChunk-1 hold in idxv, into stage buffer b: lane 0
+    // arms the buffer's mbarrier with the chunk's bytes, then lane l < kChunk
+    // issues one bulk copy of item l's header row (called by all lanes)
+    constexpr unsigned kHdrBytes = (unsigned)(HDR4 * sizeof(float4));
+    auto stage_chunk = [&](uint32_t base, uint32_t idxv, int b) {
+        const uint32_t avail = base < L ? min((uint32_t)kChunk, L - base) : 0u;
+        if (avail == 0u || ss.failed) return;
+        float4* bufp = stage + b * kChunk * HDR4;
+        // the warp's earlier reads of this buffer come before the copies
+        // into it (generic then async proxy)
+        __syncwarp();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (lane == 0) mbar_arrive_expect_tx(ss.mbar + b, avail * kHdrBytes);
+        __syncwarp();
+        if ((uint32_t)lane < avail) bulk_g2s(bufp + lane * HDR4, rec4 + (size_t)idxv * STRIDE4, kHdrBytes, ss.mbar + b);
+        ss.pending |= 1u << b;
+    };
+    // waits for buffer b's copies (called by all lanes)
+    auto stage_wait = [&](int b) {
+        if (!((ss.pending >> b) & 1u) || ss.failed) return;
+        const unsigned par = (ss.phase >> b) & 1u;
+        // every lane polls; the loop ends for the whole warp at once (the
+        // same trip count on every lane, see take_record_chunk)
+        for (int spins = 0;; spins++) {
+            if (__all_sync(0xffffffffu, mbar_try_wait(ss.mbar + b, par))) break;
+            if (spins >= kStageSpin) {
+                ss.failed = true;
+                if (lane == 0 && A.status) atomicOr(A.status, 1 << DRK_ERR_TIMEOUT);
+                break;
+            }
         }
+        ss.phase ^= 1u << b;
+        ss.pending &= ~(1u << b);
+        __syncwarp();
     };
 
     while (true) {   // passes over the list
@@ -642,18 +698,15 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
         uint32_t key_a = lo_lane && (uint32_t)lane < L ? __ldg(lkeys + lane) : 0u;
         uint32_t idx_b = lo_lane && kChunk + (uint32_t)lane < L ? __ldg(list + kChunk + lane) : 0u;
         uint32_t key_b = lo_lane && kChunk + (uint32_t)lane < L ? __ldg(lkeys + kChunk + lane) : 0u;
-        stage_chunk(0u, idx_a, stage);
-        cp_async_commit();
+        stage_chunk(0u, idx_a, 0);
         for (uint32_t c0 = 0; c0 < L; c0 += kChunk) {
             const int buf = (int)((c0 / kChunk) & 1u);
             // stage the next chunk's headers, fetch the one after's entries
-            stage_chunk(c0 + kChunk, idx_b, stage + (buf ^ 1) * kChunk * HDR4);
-            cp_async_commit();
+            stage_chunk(c0 + kChunk, idx_b, buf ^ 1);
             const uint32_t n2 = c0 + 2 * kChunk + lane;
             const uint32_t idx_c = lo_lane && n2 < L ? __ldg(list + n2) : 0u;
             const uint32_t key_c = lo_lane && n2 < L ? __ldg(lkeys + n2) : 0u;
-            cp_async_wait_1();
-            __syncwarp();
+            stage_wait(buf);
             const uint32_t cn = min((uint32_t)kChunk, L - c0);
             // Composite, once per chunk and with every lane together, each
             // pending entry that no item of this chunk or later can precede
@@ -774,8 +827,9 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
             idx_b = idx_c; key_b = key_c;
             if (__all_sync(0xffffffffu, pass_done)) break;
         }
-        cp_async_wait_all();
-        __syncwarp();
+        // a pass that ended early leaves the next chunk's copies in flight
+        stage_wait(0);
+        stage_wait(1);
         // end of the list for this pass: composite what is left in order
         drain(!ps.done, __int_as_float(0x7f800000));
         bool need = !ps.done && lost != ~0ull;
@@ -837,6 +891,15 @@ __global__ void __launch_bounds__(kRasterThreads, (BATCH || CAP >= 16) ? 4 : 5) 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float4* stage = stage_all + warp * (2 * kChunk * HDR4);
     __shared__ FrameConst fc_sh[BATCH ? kWarps : 1];   // batch: the current task's frame constants
+    __shared__ __align__(8) uint64_t stage_mbar[kWarps][2];
+    StageSync ss{stage_mbar[warp], 0u, 0u, false};
+    if (lane == 0) {
+        mbar_init(ss.mbar, 1u);
+        mbar_init(ss.mbar + 1, 1u);
+    }
+    // the initialised barriers are visible to the bulk-copy engine
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    __syncwarp();
     const int slot = blockIdx.x * kWarps + warp;
     // lane-contiguous columns: a lane's deep heap levels are adjacent, and
     // the footprint is what the pixels actually hold
@@ -867,8 +930,8 @@ __global__ void __launch_bounds__(kRasterThreads, (BATCH || CAP >= 16) ? 4 : 5) 
             if (lane < kFcWords) reinterpret_cast<int*>(&fc_sh[warp])[lane] = reinterpret_cast<const int*>(&sl.fc)[lane];
             __syncwarp();
             run_task<KMAX, CAP, BWD, false>(A, fc_sh[warp], sl.rec, sl.rgb, sl.vals, sl.keys, sl.ranges, sl.dq,
-                                            sl.out_rgb, true, sl.K, tile & ((1 << 20) - 1), task, stage, ring, ovf, kb,
-                                            wc, rc);
+                                            sl.out_rgb, true, sl.K, tile & ((1 << 20) - 1), task, stage, ss, ring, ovf,
+                                            kb, wc, rc);
             // the warp that finishes a frame's last task publishes it: its
             // image is complete in device memory once the flag is visible
             __syncwarp();
@@ -881,7 +944,7 @@ __global__ void __launch_bounds__(kRasterThreads, (BATCH || CAP >= 16) ? 4 : 5) 
             }
         } else {
             run_task<KMAX, CAP, BWD, AUX>(A, A.fc, A.rec, A.rgb, A.vals, A.keys, A.ranges, A.dq, A.out_rgb, false, A.K, tile,
-                                     task, stage, ring, ovf, kb, wc, rc);
+                                     task, stage, ss, ring, ovf, kb, wc, rc);
         }
     }
     // the unused tail of the warp's last record chunk holds no record
