@@ -870,11 +870,13 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
 // 8 per tile); each warp takes tasks from a global counter until none are
 // left and walks the tile's list on its own, so there is no block-wide
 // barrier anywhere.  List entries (primitive index, depth key) are fetched
-// 32 at a time with one coalesced load and broadcast by shuffle; the
-// headers of the next 32 records are copied into the warp's shared-memory
-// stage with cp.async one chunk ahead of use; the kernel stage runs only
-// when some lane of the warp passes the geometry stage.  Tasks are taken
-// heaviest tile first (longest list), which keeps the tail short.
+// 16 at a time with one coalesced load and broadcast by shuffle; the
+// headers of the next 16 records are copied into the warp's shared-memory
+// stage by bulk copies (one per header row) one chunk ahead of use,
+// completed on the warp's mbarrier of that stage buffer; two items are
+// evaluated per step, and the kernel stage runs only when some lane of the
+// warp passes the geometry stage.  Tasks are taken heaviest tile first
+// (longest list), which keeps the tail short.
 // The register budget is that of the CTAs per SM the shared memory allows:
 // four with 16 or more heap slots (and for the batch variant, which keeps a
 // frame slot per task), five with 8.
