@@ -442,8 +442,11 @@ __device__ __forceinline__ void take_record_chunk(const RasterArgs& A, RecChunk&
 
 // ---------------------------------------------------------------------------
 // Counters a warp accumulates over its tasks.
+// Per lane in 32 bits (a lane would need 2^32 evaluations in one launch to
+// wrap; the counters are statistics), summed over the warp in 32 bits and
+// added to the 64-bit device counters.
 struct WarpCounters {
-    unsigned long long evals = 0, emit = 0, passes = 0, contrib = 0, geo = 0, spills = 0;
+    uint32_t evals = 0, emit = 0, passes = 0, contrib = 0, geo = 0, spills = 0;
 };
 
 // One task of the forward (or replay) traversal: the 8 x 4 block `blk` of
@@ -859,7 +862,7 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
                 for (int c = 0; c < 3; c++) A.out_normal[c * npix + pix] = aux_n[c];
         }
     }
-    wc.emit += (unsigned long long)ps.n_emit;
+    wc.emit += (uint32_t)ps.n_emit;
 }
 
 // Forward traversal; with BWD it is the exact replay used by the backward of
@@ -964,12 +967,12 @@ __global__ void __launch_bounds__(kRasterThreads, (BATCH || CAP >= 16) ? 4 : 5) 
             wc.spills += __shfl_down_sync(0xffffffffu, wc.spills, o);
         }
         if (lane == 0) {
-            atomicAdd(A.counters + 0, wc.evals);
-            atomicAdd(A.counters + 1, wc.emit);
-            atomicAdd(A.counters + 2, wc.passes);
-            atomicAdd(A.counters + 5, wc.contrib);
-            atomicAdd(A.counters + 6, wc.geo);
-            atomicAdd(A.counters + 8, wc.spills);
+            atomicAdd(A.counters + 0, (unsigned long long)wc.evals);
+            atomicAdd(A.counters + 1, (unsigned long long)wc.emit);
+            atomicAdd(A.counters + 2, (unsigned long long)wc.passes);
+            atomicAdd(A.counters + 5, (unsigned long long)wc.contrib);
+            atomicAdd(A.counters + 6, (unsigned long long)wc.geo);
+            atomicAdd(A.counters + 8, (unsigned long long)wc.spills);
         }
     }
 
