@@ -59,7 +59,8 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
 // bound of a stage wait (try_wait polls, each with the hardware's own
 // time limit): far beyond any copy's latency; past it the raster records
 // DRK_ERR_TIMEOUT, and the warp issues no further copies and waits no
-// more (its images are then wrong, but the kernel ends)
+// more until its last task is done (its images are then wrong, but the
+// kernel ends)
 constexpr int kStageSpin = 1 << 20;
 
 // The warp's two stage buffers: their mbarriers, the parity of each one's
@@ -70,6 +71,19 @@ struct StageSync {
     unsigned pending;      // bit b: buffer b has copies not yet waited for
     bool failed;           // a wait ran out: no more copies or waits
 };
+
+// After a wait ran out: waits once more, with the same bound, for the
+// copies still in flight into the warp's buffers, so that none of them
+// lands in shared memory after the CTA has ended (called by all lanes).
+__device__ __forceinline__ void stage_settle(const StageSync& ss) {
+    for (int b = 0; b < 2; b++) {
+        if (!((ss.pending >> b) & 1u)) continue;
+        const unsigned par = (ss.phase >> b) & 1u;
+        for (int spins = 0; spins < kStageSpin; spins++)
+            if (__all_sync(0xffffffffu, mbar_try_wait(ss.mbar + b, par))) break;
+    }
+    __syncwarp();
+}
 
 constexpr int kMaxPasses = 1 << 20;
 constexpr int kRasterThreads = 128;   // persistent raster CTAs: 4 independent warps
@@ -683,9 +697,10 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
         for (int spins = 0;; spins++) {
             if (__all_sync(0xffffffffu, mbar_try_wait(ss.mbar + b, par))) break;
             if (spins >= kStageSpin) {
+                // buffer b stays pending: the kernel settles it at its end
                 ss.failed = true;
                 if (lane == 0 && A.status) atomicOr(A.status, 1 << DRK_ERR_TIMEOUT);
-                break;
+                return;
             }
         }
         ss.phase ^= 1u << b;
@@ -952,6 +967,8 @@ __global__ void __launch_bounds__(kRasterThreads, (BATCH || CAP >= 16) ? 4 : 5) 
                                      task, stage, ss, ring, ovf, kb, wc, rc);
         }
     }
+    // copies abandoned by a wait that ran out are waited for once more
+    if (ss.failed) stage_settle(ss);
     // the unused tail of the warp's last record chunk holds no record
     if (!BWD && !BATCH && A.rec_key)
         for (uint32_t q0 = rc.base; q0 < rc.end; q0 += 32)

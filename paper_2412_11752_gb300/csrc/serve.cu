@@ -191,9 +191,16 @@ void retire(drk_serve* S, std::unique_ptr<BatchInfo>* info) {
                 Request& r = it->second;
                 if (b->ok[i]) {
                     const unsigned long long bits = hc[(size_t)i * kCountersPer + 4] | batch_bits;
+                    // a failed launch, else the lowest device status bit set
+                    // (a capacity overflow, a stage wait that ran out)
+                    r.t.status = DRK_OK;
                     if (e != cudaSuccess) r.t.status = DRK_ERR_CUDA;
-                    else if (bits & (1ull << DRK_ERR_CAPACITY)) r.t.status = DRK_ERR_CAPACITY;
-                    else r.t.status = DRK_OK;
+                    else
+                        for (int sb = 1; sb < 8; sb++)
+                            if (bits & (1ull << sb)) {
+                                r.t.status = sb;
+                                break;
+                            }
                     // pairs per pixel of this scene, kept as the largest recent value
                     const BatchInfo& bi = *info[s];
                     SceneDev& sc = *S->scenes[bi.scene[i]];
