@@ -277,6 +277,16 @@ drk_status_t drk_get_stats(drk_ctx_t *ctx, drk_stats_t *out);
 drk_status_t drk_timing_enable(drk_ctx_t *ctx, int enable);
 drk_status_t drk_timing_read(drk_ctx_t *ctx, double *ms, int64_t *launches);
 
+/* Statistics of the forward raster (n_evals, n_geo_evals, n_contrib_evals,
+ * n_emitted and n_spills of drk_stats_t) are collected by default.  With
+ * enable = 0 the forward of later drk_render calls on this context runs a
+ * kernel without them (its per-lane counters cost the 1080p forward about
+ * 1.5 % of its time) and those five fields read 0; images, records and
+ * gradients are the same bit for bit.  n_visible, n_pairs, n_extra_passes,
+ * n_replay_evals and the status word are always kept.  Takes effect at the
+ * next render; no device work.  DRK_ERR_INVALID_ARG for a null context. */
+drk_status_t drk_stats_enable(drk_ctx_t *ctx, int enable);
+
 /* Measured arithmetic throughput of one GPU (operations per second): the
  * FP32 FMA pipe (an FMA counted as one operation) and the transcendental
  * unit for ex2.approx, rcp.approx and cos.approx, each from the library's

@@ -84,6 +84,7 @@ struct drk_ctx {
     unsigned int* rec_ctr = nullptr;          // record chunks the last recording forward took
     uint4* ovf = nullptr;                     // overflow columns of the raster's depth-order buffers
     size_t ovf_bytes = 0;
+    bool stats = true;                        // the forward raster collects its statistics
     drk_stats_t last{};
 };
 
@@ -474,7 +475,7 @@ drk_status_t drk_render(drk_ctx_t* ctx, const drk_params_t* params, const drk_ca
     }
     attach_ovf(ctx, opt, F.kmax, opt->kbuf_capacity, false, F.n_tiles, st, R);
     cudaEvent_t ev = tm.begin(st);
-    launch_raster(R, F.kmax, opt->kbuf_capacity, false, st);
+    launch_raster(R, F.kmax, opt->kbuf_capacity, false, ctx->stats, st);
     tm.end(ST_RASTER, ev, st);
     if ((s = check_launch()) != DRK_OK) return s;
 
@@ -618,7 +619,7 @@ drk_status_t drk_render_backward(drk_ctx_t* ctx, const drk_params_t* params, con
     launch_raster_backward_records(R, sslot, (uint32_t)nrec, F.kmax, st);
     tm.end(ST_RASTER_BWD, ev, st);
     ev = tm.begin(st);
-    launch_raster(R, F.kmax, state->cap, true, st);      // exact replay of the others
+    launch_raster(R, F.kmax, state->cap, true, true, st);   // exact replay of the others
     tm.end(ST_REPLAY, ev, st);
 
     PreArgs A;
@@ -644,6 +645,12 @@ drk_status_t drk_timing_enable(drk_ctx_t* ctx, int enable) {
         ctx->timer.cnt[i] = 0;
     }
     ctx->timer.on = enable != 0;
+    return DRK_OK;
+}
+
+drk_status_t drk_stats_enable(drk_ctx_t* ctx, int enable) {
+    if (!ctx) return fail(DRK_ERR_INVALID_ARG, "null context");
+    ctx->stats = enable != 0;
     return DRK_OK;
 }
 

@@ -148,7 +148,8 @@ void launch_tile_order(const uint2* ranges, int n_tiles, uint32_t* order, void* 
 // them by 26-bit key gives frame order, heaviest tile first within a frame
 void launch_batch_order_keys(const uint2* ranges, int n_tiles, int slot, uint32_t* keys, uint32_t* vals,
                              cudaStream_t st);
-void launch_raster(const RasterArgs& A, int kmax, int cap, bool bwd, cudaStream_t st);
+// stats: the forward keeps its per-render statistics (the replay always does)
+void launch_raster(const RasterArgs& A, int kmax, int cap, bool bwd, bool stats, cudaStream_t st);
 // warps the raster launch for n_tiles tiles runs (one overflow slot each),
 // and the bytes of the overflow columns of `slots` warps
 int raster_slots(int kmax, int cap, bool bwd, bool batch, int n_tiles);

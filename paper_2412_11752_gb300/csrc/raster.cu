@@ -459,13 +459,16 @@ __device__ __forceinline__ void take_record_chunk(const RasterArgs& A, RecChunk&
 // Per lane in 32 bits (a lane would need 2^32 evaluations in one launch to
 // wrap; the counters are statistics), summed over the warp in 32 bits and
 // added to the 64-bit device counters.
+// Only `passes` bounds the traversal; the others are statistics, kept
+// when the kernel is instantiated with STATS (their registers cost the
+// frame forward at 1080p about 1.5 % of its time).
 struct WarpCounters {
     uint32_t evals = 0, emit = 0, passes = 0, contrib = 0, geo = 0, spills = 0;
 };
 
 // One task of the forward (or replay) traversal: the 8 x 4 block `blk` of
 // `tile` in the frame (fc, rec, rgb, vals, keys, ranges, dq, out).
-template <int KMAX, int CAP, bool BWD, bool AUX>
+template <int KMAX, int CAP, bool BWD, bool AUX, bool STATS>
 __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& fc, const float* __restrict__ recp,
                                          const float4* __restrict__ rgbp, const uint32_t* __restrict__ valsp,
                                          const uint32_t* __restrict__ keysp, const uint2* __restrict__ rangesp,
@@ -621,7 +624,7 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
         }
         if (kk < lo || kk >= lost) return;
         if (!kb.full()) {
-            if (kb.n >= HeapSlots<CAP>::value) wc.spills++;
+            if (STATS && kb.n >= HeapSlots<CAP>::value) wc.spills++;
             kb.push(t, j, a);
         } else {
             const uint64_t d = kb.push_full(t, j, a);
@@ -658,12 +661,10 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
             }
             uint32_t rk = kNoSlot;
             if (want) rk = emit_front(slot);
-            if (rec_on) {
-                // records per primitive, one atomic per group of lanes that
-                // composited the same primitive in this round
-                const unsigned peers = __match_any_sync(0xffffffffu, rk);
-                if (rk != kNoSlot && lane == __ffs(peers) - 1) atomicAdd(A.rec_count + rk, (uint32_t)__popc(peers));
-            }
+            // records per primitive: one atomic per recorded lane (cheaper
+            // here than grouping equal primitives of the round with a
+            // match-any first)
+            if (rec_on && rk != kNoSlot) atomicAdd(A.rec_count + rk, 1u);
         }
         // nothing left below the smallest dropped key can come before thr
         if (go && ok) ok = !(lost != ~0ull && lt < thr);
@@ -770,7 +771,7 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
                     Geo gA{0.f, 0.f, 0.f, 0.f}, gB{0.f, 0.f, 0.f, 0.f};
                     bool geoA = false, geoB = false;
                     if (!pass_done) {
-                        wc.evals += two ? 2 : 1;
+                        if (STATS) wc.evals += two ? 2 : 1;
 #pragma unroll
                         for (int q = 0; q < R_GEO4; q++) {
                             const float4 v = sgA[q];
@@ -782,7 +783,7 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
                         geoB = two && eval_geometry(hB, pr, fc.near_plane, gB);
                     }
                     if (__any_sync(0xffffffffu, geoA || geoB)) {
-                        wc.geo += (geoA ? 1 : 0) + (geoB ? 1 : 0);
+                        if (STATS) wc.geo += (geoA ? 1 : 0) + (geoB ? 1 : 0);
 #pragma unroll
                         for (int q = R_GEO4; q < R_FIX4; q++) {
                             const float4 v = sgA[q];
@@ -796,11 +797,11 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
                         const bool okB = eval_kernel<KMAX, false>(hB, reinterpret_cast<const float*>(sgB), K, pr, gB,
                                                                   fc.alpha_min, fc.alpha_max, aB) && geoB;
                         if (okA) {
-                            wc.contrib++;
+                            if (STATS) wc.contrib++;
                             offer(gA.t, idxA, aA, key_of(gA.t, idxA));
                         }
                         if (okB) {
-                            wc.contrib++;
+                            if (STATS) wc.contrib++;
                             offer(gB.t, idxB, aB, key_of(gB.t, idxB));
                         }
                     }
@@ -813,7 +814,7 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
                     bool geo = false;
                     const float4* sg = stage + (buf * kChunk + jj) * HDR4;
                     if (!pass_done) {
-                        wc.evals++;
+                        if (STATS) wc.evals++;
     #pragma unroll
                         for (int q = 0; q < R_GEO4; q++) {
                             const float4 v = sg[q];
@@ -823,7 +824,7 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
                     }
                     if (__any_sync(0xffffffffu, geo)) {
                         if (geo) {
-                            wc.geo++;
+                            if (STATS) wc.geo++;
     #pragma unroll
                             for (int q = R_GEO4; q < R_FIX4; q++) {
                                 const float4 v = sg[q];
@@ -832,7 +833,7 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
                             float a;
                             if (eval_kernel<KMAX, false>(h, reinterpret_cast<const float*>(sg), K, pr, gm, fc.alpha_min,
                                                          fc.alpha_max, a)) {
-                                wc.contrib++;
+                                if (STATS) wc.contrib++;
                                 offer(gm.t, idx, a, key_of(gm.t, idx));
                                 if (ps.done) pass_done = true;
                             }
@@ -877,7 +878,7 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
                 for (int c = 0; c < 3; c++) A.out_normal[c * npix + pix] = aux_n[c];
         }
     }
-    wc.emit += (uint32_t)ps.n_emit;
+    if (STATS) wc.emit += (uint32_t)ps.n_emit;
 }
 
 // Forward traversal; with BWD it is the exact replay used by the backward of
@@ -898,7 +899,7 @@ __device__ __forceinline__ void run_task(const RasterArgs& A, const FrameConst& 
 // The register budget is that of the CTAs per SM the shared memory allows:
 // four with 16 or more heap slots (and for the batch variant, which keeps a
 // frame slot per task), five with 8.
-template <int KMAX, int CAP, bool BWD, bool BATCH, bool AUX = false>
+template <int KMAX, int CAP, bool BWD, bool BATCH, bool AUX = false, bool STATS = true>
 __global__ void __launch_bounds__(kRasterThreads, (BATCH || CAP >= 16) ? 4 : 5) raster_kernel(RasterArgs A) {
     constexpr int kWarps = kRasterThreads / 32;
     constexpr int HDR4 = Rec<KMAX>::HDR / 4;
@@ -949,7 +950,7 @@ __global__ void __launch_bounds__(kRasterThreads, (BATCH || CAP >= 16) ? 4 : 5) 
             __syncwarp();
             if (lane < kFcWords) reinterpret_cast<int*>(&fc_sh[warp])[lane] = reinterpret_cast<const int*>(&sl.fc)[lane];
             __syncwarp();
-            run_task<KMAX, CAP, BWD, false>(A, fc_sh[warp], sl.rec, sl.rgb, sl.vals, sl.keys, sl.ranges, sl.dq,
+            run_task<KMAX, CAP, BWD, false, STATS>(A, fc_sh[warp], sl.rec, sl.rgb, sl.vals, sl.keys, sl.ranges, sl.dq,
                                             sl.out_rgb, true, sl.K, tile & ((1 << 20) - 1), task, stage, ss, ring, ovf,
                                             kb, wc, rc);
             // the warp that finishes a frame's last task publishes it: its
@@ -963,7 +964,7 @@ __global__ void __launch_bounds__(kRasterThreads, (BATCH || CAP >= 16) ? 4 : 5) 
                 }
             }
         } else {
-            run_task<KMAX, CAP, BWD, AUX>(A, A.fc, A.rec, A.rgb, A.vals, A.keys, A.ranges, A.dq, A.out_rgb, false, A.K, tile,
+            run_task<KMAX, CAP, BWD, AUX, STATS>(A, A.fc, A.rec, A.rgb, A.vals, A.keys, A.ranges, A.dq, A.out_rgb, false, A.K, tile,
                                      task, stage, ss, ring, ovf, kb, wc, rc);
         }
     }
@@ -1178,39 +1179,40 @@ constexpr size_t raster_smem() {
 }
 
 // resident CTAs x SMs of one instantiation (computed once)
-template <int KMAX, int CAP, bool BWD, bool BATCH, bool AUX = false>
+template <int KMAX, int CAP, bool BWD, bool BATCH, bool AUX = false, bool STATS = true>
 static int raster_grid() {
     static int grid = 0;
     if (grid == 0) {
         constexpr size_t smem = raster_smem<KMAX, CAP>();
-        cudaFuncSetAttribute(raster_kernel<KMAX, CAP, BWD, BATCH, AUX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(raster_kernel<KMAX, CAP, BWD, BATCH, AUX, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raster_kernel<KMAX, CAP, BWD, BATCH, AUX>,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raster_kernel<KMAX, CAP, BWD, BATCH, AUX, STATS>,
                                                       kRasterThreads, smem);
         grid = sms * (per_sm > 0 ? per_sm : 1);
     }
     return grid;
 }
 
-template <int KMAX, int CAP, bool BWD, bool BATCH, bool AUX = false>
+template <int KMAX, int CAP, bool BWD, bool BATCH, bool AUX = false, bool STATS = true>
 static int raster_blocks(int n_tiles) {
     constexpr int kWarps = kRasterThreads / 32;
     const int n_tasks = n_tiles * 8;
-    return std::min(raster_grid<KMAX, CAP, BWD, BATCH, AUX>(), (n_tasks + kWarps - 1) / kWarps);
+    return std::min(raster_grid<KMAX, CAP, BWD, BATCH, AUX, STATS>(), (n_tasks + kWarps - 1) / kWarps);
 }
 
-template <int KMAX, int CAP, bool BWD, bool BATCH, bool AUX = false>
+template <int KMAX, int CAP, bool BWD, bool BATCH, bool AUX = false, bool STATS = true>
 static void launch_raster_t(const RasterArgs& A, int n_tiles, cudaStream_t st) {
-    // the depth/normal instantiation never has more resident warps than the
-    // plain one (same bounds, at least as many registers), so the overflow
-    // columns sized by raster_slots cover it; warps past them run without
-    const int blocks = raster_blocks<KMAX, CAP, BWD, BATCH, AUX>(n_tiles);
+    // the depth/normal and the statistics-free instantiations run at most
+    // as many resident warps as the plain one (the same bounds and shared
+    // memory), so the overflow columns sized by raster_slots cover them;
+    // warps past the columns would run without
+    const int blocks = raster_blocks<KMAX, CAP, BWD, BATCH, AUX, STATS>(n_tiles);
     if (blocks <= 0) return;
     cudaMemsetAsync(A.task_counter, 0, sizeof(unsigned int), st);
-    raster_kernel<KMAX, CAP, BWD, BATCH, AUX><<<blocks, kRasterThreads, raster_smem<KMAX, CAP>(), st>>>(A);
+    raster_kernel<KMAX, CAP, BWD, BATCH, AUX, STATS><<<blocks, kRasterThreads, raster_smem<KMAX, CAP>(), st>>>(A);
     note_launch();
 }
 
@@ -1235,16 +1237,17 @@ int raster_slots(int kmax, int cap, bool bwd, bool batch, int n_tiles) {
 
 size_t raster_ovf_bytes(int slots) { return (size_t)slots * kOvfCap * 32 * sizeof(uint4); }
 
-void launch_raster(const RasterArgs& A, int kmax, int cap, bool bwd, cudaStream_t st) {
+void launch_raster(const RasterArgs& A, int kmax, int cap, bool bwd, bool stats, cudaStream_t st) {
     const int n_tiles = A.fc.tiles_x * A.fc.tiles_y;
     if (n_tiles == 0) return;
     const bool aux = !bwd && (A.out_depth || A.out_normal);
-#define DRK_RASTER_CASE(KM, CP)                                                   \
-    if (kmax == KM && cap == CP) {                                                \
-        if (bwd) launch_raster_t<KM, CP, true, false>(A, n_tiles, st);            \
-        else if (aux) launch_raster_t<KM, CP, false, false, true>(A, n_tiles, st);\
-        else launch_raster_t<KM, CP, false, false>(A, n_tiles, st);               \
-        return;                                                                   \
+#define DRK_RASTER_CASE(KM, CP)                                                          \
+    if (kmax == KM && cap == CP) {                                                       \
+        if (bwd) launch_raster_t<KM, CP, true, false>(A, n_tiles, st);                   \
+        else if (aux) launch_raster_t<KM, CP, false, false, true>(A, n_tiles, st);       \
+        else if (stats) launch_raster_t<KM, CP, false, false>(A, n_tiles, st);           \
+        else launch_raster_t<KM, CP, false, false, false, false>(A, n_tiles, st);        \
+        return;                                                                          \
     }
     DRK_RASTER_CASE(8, 8)
     DRK_RASTER_CASE(8, 16)

@@ -123,6 +123,7 @@ def lib():
         L.drk_measure_pipes.argtypes = [C.c_int, C.POINTER(drk_pipe_peaks_t)]
         L.drk_measure_pipes.restype = C.c_int
         L.drk_timing_enable.argtypes = [vp, C.c_int]
+        L.drk_stats_enable.argtypes = [vp, C.c_int]
         L.drk_timing_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
         L.drk_launch_count.restype = C.c_int64
         L.drk_serve_create.argtypes = [C.c_int, C.c_size_t, C.c_int, C.POINTER(drk_options_t), C.POINTER(vp)]
@@ -146,7 +147,7 @@ def lib():
         for f in ("drk_activate", "drk_activate_backward", "drk_adam_step", "drk_mesh_to_drk"):
             getattr(L, f).restype = C.c_int
         for f in ("drk_ctx_create", "drk_render", "drk_render_backward", "drk_get_stats", "drk_sort_pairs",
-                  "drk_timing_enable", "drk_timing_read", "drk_serve_create", "drk_serve_add_scene",
+                  "drk_timing_enable", "drk_stats_enable", "drk_timing_read", "drk_serve_create", "drk_serve_add_scene",
                   "drk_serve_submit", "drk_serve_poll", "drk_serve_wait", "drk_serve_release",
                   "drk_serve_inject_alloc_failure", "drk_serve_destroy"):
             getattr(L, f).restype = C.c_int
@@ -242,6 +243,12 @@ class Context:
 
     def timing_enable(self, on: bool = True) -> None:
         _check(lib().drk_timing_enable(self.handle, 1 if on else 0))
+
+    def stats_enable(self, on: bool = True) -> None:
+        """Collect the forward raster's statistics (default) or not: without
+        them n_evals, n_geo_evals, n_contrib_evals, n_emitted and n_spills
+        read 0 and the forward runs slightly faster; images are identical."""
+        _check(lib().drk_stats_enable(self.handle, 1 if on else 0))
 
     def timing_read(self) -> dict:
         ms = (C.c_double * 8)()

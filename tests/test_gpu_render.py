@@ -4,7 +4,7 @@ import math
 import numpy as np
 import pytest
 
-from helpers import TOL_IMAGE, excluded, image_parity, oracle_options
+from helpers import TOL_IMAGE, excluded, image_parity, oracle_options, rel_err
 from oracle import drk_oracle as O
 from paper_2412_11752_gb300 import synth
 
@@ -81,6 +81,50 @@ def test_buffer_capacity_does_not_change_the_image(drk):
     assert seen[(8, 0)][0] > 0 and seen[(8, 0)][1] == 0      # spills, no extra pass
     assert seen[(8, 3)][0] > 0 and seen[(8, 3)][1] > 0       # column too small: both
     assert seen[(8, -1)][0] == 0 and seen[(8, -1)][1] > 0    # no column: passes only
+
+
+@pytest.mark.parametrize("cap", [8, 16])
+def test_statistics_switch_keeps_images_and_gradients(drk, cap):
+    # the forward without statistics (drk_stats_enable 0) renders the same
+    # image bit for bit and the backward over its records gives the same
+    # gradients (up to the order of float atomics); its five statistics
+    # read 0, and two renders with statistics count the same (8 shared
+    # heap slots make this scene spill; 16 is the default capacity)
+    scene = synth.scene_clustered(4000, 8, seed=2100, n_clusters=8)
+    cam = synth.camera_front(96, 64)
+    opt = drk.Options(kbuf_capacity=cap)
+    ds = drk.DeviceScene.from_scene(scene, "cuda")
+    dL = torch.from_numpy(np.random.default_rng(7).standard_normal((3, 64, 96)).astype(np.float32)).cuda()
+    ctx = drk.Context(0)
+    fields = ("n_evals", "n_geo_evals", "n_contrib_evals", "n_emitted", "n_spills")
+
+    def run(on):
+        ctx.stats_enable(on)
+        rgb, T, n, st = drk.drk_render(ds, cam, opt, ctx=ctx, need_state=True)
+        stats = ctx.stats()
+        g = drk.drk_render_backward(ds, cam, opt, st, dL, ctx=ctx)
+        torch.cuda.synchronize()
+        st.free()
+        return rgb.cpu().numpy(), T.cpu().numpy(), n.cpu().numpy(), {k: v.cpu().numpy() for k, v in g.items()}, stats
+
+    try:
+        a, b, c = run(True), run(False), run(True)
+    finally:
+        ctx.stats_enable(True)
+    for x in (b, c):
+        for i in range(3):
+            assert np.array_equal(x[i], a[i])
+        # two backward runs sum their float atomics in different orders, which
+        # moves single elements with heavy cancellation (quat) by more than
+        # 1e-4 of themselves; per tensor the difference stays near float
+        # rounding, while records that differed would move it by far more
+        for k, v in a[3].items():
+            assert rel_err(x[3][k], v) <= 5e-4, (k, rel_err(x[3][k], v))
+    assert all(a[4][f] == c[4][f] for f in fields), (a[4], c[4])
+    assert all(a[4][f] > 0 for f in fields if f != "n_spills" or cap == 8), a[4]
+    assert all(b[4][f] == 0 for f in fields), b[4]
+    assert b[4]["n_pairs"] == a[4]["n_pairs"] and b[4]["n_extra_passes"] == a[4]["n_extra_passes"]
+    ctx.close()
 
 
 def test_gaussian_special_case_k4(drk):
