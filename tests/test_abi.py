@@ -48,3 +48,15 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(drk, "_lib", None)
     with pytest.raises(RuntimeError):
         drk.lib()
+
+
+def test_context_calls_reject_null_arguments_before_any_cuda_call():
+    # the host-side argument checks come first, so they run without a GPU:
+    # each returns DRK_ERR_INVALID_ARG and leaves its message
+    from paper_2412_11752_gb300 import drk
+    L = drk.lib()
+    calls = (("drk_stats_enable", (None, 0)), ("drk_timing_enable", (None, 1)), ("drk_get_stats", (None, None)),
+             ("drk_ctx_create", (0, None)))
+    for name, args in calls:
+        assert getattr(L, name)(*args) == 1, name
+        assert L.drk_last_error(), name
