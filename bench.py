@@ -46,6 +46,9 @@ OPS_PER_EMIT_BWD = 190
 # depth, the reciprocal inside the polar angle, the cosine of Eq. 6 and
 # the exponentials of Eq. 8 and Eq. 10
 XU_PER_EVAL = 5
+# bytes the backward must read per composited contributor: its 32-byte
+# record sector and its 4-byte grouped slot index
+REC_BYTES_BWD = 36
 
 
 def parse():
@@ -154,6 +157,34 @@ def raster_traffic(workload: str):
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return float(t.group(1)) * 1e9 if h.hexdigest()[:16] == m.group(1) else None
+
+
+def records_roofline(n_records: int, ms: float, fma_ops: float, xu_s_per_unit: float, hbm_gbs: float,
+                     replayed: bool = False):
+    """The backward over the contributor records, reported like the forward
+    raster: per record the pair is evaluated again (OPS_PER_EVAL FP32 and
+    XU_PER_EVAL transcendental operations) and its gradient chained
+    (OPS_PER_EMIT_BWD more), against the measured FMA rate (fma_ops, per
+    second) and transcendental mix (xu_s_per_unit seconds per evaluation's
+    XU_PER_EVAL operations); and its REC_BYTES_BWD algorithmic bytes per
+    record against the measured copy rate.  n_records counts every
+    composited contributor, which includes those of tiles taken by the
+    exact replay when `replayed`.  None without records or time."""
+    if n_records <= 0 or ms <= 0.0 or fma_ops <= 0.0 or xu_s_per_unit <= 0.0 or hbm_gbs <= 0.0:
+        return None
+    s = ms / 1e3
+    ops = OPS_PER_EVAL + OPS_PER_EMIT_BWD
+    fma_peak = fma_ops / 1e12
+    achieved = n_records * ops / s / 1e12
+    xu_peak = XU_PER_EVAL / xu_s_per_unit / 1e12
+    xu_achieved = n_records * XU_PER_EVAL / s / 1e12
+    gbs = n_records * REC_BYTES_BWD / s / 1e9
+    return {"kernel": "raster_bwd_records", "bound": "alu", "achieved": achieved, "peak": fma_peak, "unit": "Top/s",
+            "frac": achieved / fma_peak, "ops_per_unit": ops, "units": int(n_records), "ms": ms,
+            "replayed_tiles": bool(replayed),
+            "xu": {"achieved": xu_achieved, "peak": xu_peak, "unit": "Top/s", "frac": xu_achieved / xu_peak,
+                   "ops_per_unit": XU_PER_EVAL},
+            "hbm": {"bytes_per_unit": REC_BYTES_BWD, "achieved_gbs": gbs, "peak_gbs": hbm_gbs, "frac": gbs / hbm_gbs}}
 
 
 def measured_peaks() -> dict:
@@ -365,6 +396,11 @@ def run_drk(args):
             ms_k = stage[k][0] / stage[k][1]
             gbs = b / (ms_k / 1e3) / 1e9
             hbm_stages[k] = {"bytes": b, "ms": ms_k, "achieved_gbs": gbs, "peak_gbs": hbm, "frac": gbs / hbm}
+    # the backward's records kernel beside the dominant kernel
+    bwd_roof = records_roofline(stats["n_emitted"], bwd_ms, pipes["fma_ops"], xu_s_per_unit, hbm,
+                                stats["n_replay_evals"] > 0)
+    if bwd_roof is not None:
+        roofline["backward"] = bwd_roof
 
     # ---- end to end through the public API with host buffers
     e2e = None
