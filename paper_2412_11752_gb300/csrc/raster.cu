@@ -18,9 +18,10 @@
 // (primitive, pixel, T_i, P_i) in the order it composites, which is the
 // front-to-back order the supplementary "Cache-Sorting" paragraph asks the
 // backward to follow; each record then carries its own T_i and P_i, so the
-// backward treats records independently: grouped by primitive, a warp
-// recomputes 32 of them and sums the gradients of equal primitives with
-// segmented shuffles before one global atomic per run and component.
+// backward treats records independently: grouped by primitive, each warp
+// recomputes a range of them 32 at a time, keeps per-lane partial sums of
+// the current primitive and adds them over the warp into one global
+// atomic per component only when the primitive changes.
 // Tiles whose records did not fit the pool use the replay kernel instead,
 // which re-runs the forward traversal exactly and accumulates with global
 // atomics.
