@@ -110,7 +110,7 @@ def test_statistics_switch_keeps_images_and_gradients(drk, cap):
     try:
         a, b, c = run(True), run(False), run(True)
     finally:
-        ctx.stats_enable(True)
+        ctx.close()
     for x in (b, c):
         for i in range(3):
             assert np.array_equal(x[i], a[i])
@@ -124,7 +124,6 @@ def test_statistics_switch_keeps_images_and_gradients(drk, cap):
     assert all(a[4][f] > 0 for f in fields if f != "n_spills" or cap == 8), a[4]
     assert all(b[4][f] == 0 for f in fields), b[4]
     assert b[4]["n_pairs"] == a[4]["n_pairs"] and b[4]["n_extra_passes"] == a[4]["n_extra_passes"]
-    ctx.close()
 
 
 def test_gaussian_special_case_k4(drk):
