@@ -23,3 +23,15 @@ def test_records_roofline_counts_the_backward_like_the_forward():
 def test_records_roofline_is_absent_without_records_or_time():
     assert bench.records_roofline(0, 1.0, 1e12, 1e-12, 1.0) is None
     assert bench.records_roofline(10, 0.0, 1e12, 1e-12, 1.0) is None
+
+
+def test_raster_traffic_only_while_the_captured_source_matches(tmp_path, monkeypatch):
+    # the committed summary's traffic applies to the raster sources it was
+    # captured on; with the same sources it is reported, after any change
+    # it is null
+    assert bench.raster_traffic("clustered-100k-1080p") > 1e9
+    changed = tmp_path / "raster.cu"
+    changed.write_text("// another kernel\n")
+    monkeypatch.setattr(bench, "RASTER_SOURCES", (str(changed),) + tuple(bench.RASTER_SOURCES[1:]))
+    assert bench.raster_traffic("clustered-100k-1080p") is None
+    assert bench.raster_traffic("no-such-workload") is None
