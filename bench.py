@@ -160,7 +160,7 @@ def raster_traffic(workload: str):
 
 
 def records_roofline(n_records: int, ms: float, fma_ops: float, xu_s_per_unit: float, hbm_gbs: float,
-                     replayed: bool = False):
+                     replayed: bool = False, hbm_basis: str = ""):
     """The backward over the contributor records, reported like the forward
     raster: per record the pair is evaluated again (OPS_PER_EVAL FP32 and
     XU_PER_EVAL transcendental operations) and its gradient chained
@@ -184,7 +184,8 @@ def records_roofline(n_records: int, ms: float, fma_ops: float, xu_s_per_unit: f
             "replayed_tiles": bool(replayed),
             "xu": {"achieved": xu_achieved, "peak": xu_peak, "unit": "Top/s", "frac": xu_achieved / xu_peak,
                    "ops_per_unit": XU_PER_EVAL},
-            "hbm": {"bytes_per_unit": REC_BYTES_BWD, "achieved_gbs": gbs, "peak_gbs": hbm_gbs, "frac": gbs / hbm_gbs}}
+            "hbm": {"bytes_per_unit": REC_BYTES_BWD, "achieved_gbs": gbs, "peak_gbs": hbm_gbs, "frac": gbs / hbm_gbs,
+                    "peak_basis": hbm_basis}}
 
 
 def measured_peaks() -> dict:
@@ -193,6 +194,16 @@ def measured_peaks() -> dict:
             return json.load(fh)
     except Exception:
         return {}
+
+
+def hbm_peak() -> tuple[float, str]:
+    """The HBM denominator and its basis: the copy rate measured on this
+    pool's GPUs when MEASURED_PEAKS.json holds it, else an earlier GB300
+    measurement of 6.8 TB/s."""
+    v = measured_peaks().get("hbm_gbs")
+    if v:
+        return float(v), "hbm_gbs of MEASURED_PEAKS.json (of measured)"
+    return 6800.0, "6800 GB/s from an earlier GB300 measurement (of fallback)"
 
 
 def dist_setup():
@@ -376,7 +387,7 @@ def run_drk(args):
                 "measured_pipes_tops": {k: v / 1e12 for k, v in pipes.items() if k.endswith("_ops")},
                 "load_clock_mhz": sm_load}
     # HBM-bound stages: algorithmic bytes per launch over their event times
-    hbm = float(peaks.get("hbm_gbs") or 6800.0)
+    hbm, hbm_basis = hbm_peak()
     P, N, K = stats["n_pairs"], scene.n, scene.K
     rec_b = 4 * (24 + 4 * (8 if K <= 8 else 16))
     bnd_b = 4 * (((10 + (8 if K <= 8 else 16) + 3) + 3) // 4 * 4)
@@ -395,10 +406,11 @@ def run_drk(args):
         if stage.get(k, (0, 0))[1]:
             ms_k = stage[k][0] / stage[k][1]
             gbs = b / (ms_k / 1e3) / 1e9
-            hbm_stages[k] = {"bytes": b, "ms": ms_k, "achieved_gbs": gbs, "peak_gbs": hbm, "frac": gbs / hbm}
+            hbm_stages[k] = {"bytes": b, "ms": ms_k, "achieved_gbs": gbs, "peak_gbs": hbm, "frac": gbs / hbm,
+                             "peak_basis": hbm_basis}
     # the backward's records kernel beside the dominant kernel
     bwd_roof = records_roofline(stats["n_emitted"], bwd_ms, pipes["fma_ops"], xu_s_per_unit, hbm,
-                                stats["n_replay_evals"] > 0)
+                                stats["n_replay_evals"] > 0, hbm_basis)
     if bwd_roof is not None:
         roofline["backward"] = bwd_roof
 
@@ -566,7 +578,7 @@ def train_bench(args):
     # arrays written once more (quat, K scales, K angles, eta, tau, opacity)
     floats = 3 + 4 + 2 * K + 3 + ncol
     adam_bytes = n * (28 * floats + 4 * (7 + 2 * K))
-    peak = float(measured_peaks().get("hbm_gbs") or 6800.0)
+    peak, peak_basis = hbm_peak()
     achieved = adam_bytes / (adam_ms / 1e3) / 1e9
     print(json.dumps({"metric": "training steps/s (render + backward + fused Adam) at 1080p/100k DRK",
                       "value": 1e3 / ms, "unit": "steps/s", "ms_per_step": ms, "mpix_s": H * W / ms / 1e3,
@@ -576,7 +588,7 @@ def train_bench(args):
                                  "l2": "flushed between timed steps (256 MiB write)"},
                       "adam": {"ms": adam_ms, "bytes_per_launch": adam_bytes,
                                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                                            "frac": achieved / peak, "peak_basis": "hbm_gbs of MEASURED_PEAKS.json"}},
+                                            "frac": achieved / peak, "peak_basis": peak_basis}},
                       "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
                       "gpu_launches_adam_per_step": 1}), flush=True)
     return 0
@@ -628,7 +640,7 @@ def mesh_bench(args):
     # and the colour read; mu, quat, scale, theta, eta, tau, opacity, colour
     # and status written
     bytes_face = 4 * 3 + 3 * 12 + 12 + 4 * (3 + 4 + 3 + 3 + 1 + 1 + 1 + 3) + 4
-    peak = float(measured_peaks().get("hbm_gbs") or 6800.0)
+    peak, peak_basis = hbm_peak()
     res = {}
     imgs = {}
     for name, opt, aux in (("exact", drk.Options(), False), ("exact_depth_normal", drk.Options(), True),
@@ -662,7 +674,7 @@ def mesh_bench(args):
                                   "roofline": {"bound": "hbm", "achieved": nf * bytes_face / (conv_ms / 1e3) / 1e9,
                                                "peak": peak, "unit": "GB/s",
                                                "frac": nf * bytes_face / (conv_ms / 1e3) / 1e9 / peak,
-                                               "bytes_per_face": bytes_face}},
+                                               "peak_basis": peak_basis, "bytes_per_face": bytes_face}},
                       "render": res}), flush=True)
     return 0
 

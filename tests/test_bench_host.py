@@ -35,3 +35,11 @@ def test_raster_traffic_only_while_the_captured_source_matches(tmp_path, monkeyp
     monkeypatch.setattr(bench, "RASTER_SOURCES", (str(changed),) + tuple(bench.RASTER_SOURCES[1:]))
     assert bench.raster_traffic("clustered-100k-1080p") is None
     assert bench.raster_traffic("no-such-workload") is None
+
+
+def test_hbm_peak_says_which_denominator_it_is(monkeypatch):
+    monkeypatch.setattr(bench, "measured_peaks", lambda: {"hbm_gbs": 6783.5})
+    assert bench.hbm_peak() == (6783.5, "hbm_gbs of MEASURED_PEAKS.json (of measured)")
+    monkeypatch.setattr(bench, "measured_peaks", lambda: {})
+    v, basis = bench.hbm_peak()
+    assert v == 6800.0 and basis.endswith("(of fallback)")
