@@ -218,18 +218,31 @@ void drk_ctx_destroy(drk_ctx_t *ctx);
  * The call reads the pair count back to the host once (a stream sync) to
  * size the sort; everything else is asynchronous.  Returns
  * DRK_ERR_INVALID_ARG for bad sizes or options, DRK_ERR_OOM if scratch
- * cannot grow, DRK_ERR_CUDA on a launch failure. */
+ * cannot grow, DRK_ERR_CUDA on a launch failure.  Conditions found on the
+ * device (a bounded wait that ran out, a capacity bound) do not change the
+ * return value: they surface as drk_stats_t.status of drk_get_stats. */
 drk_status_t drk_render(drk_ctx_t *ctx, const drk_params_t *params, const drk_camera_t *cam,
                         const drk_options_t *opt, const drk_image_t *out, drk_state_t **state,
                         void *stream);
 
-/* Reverse mode of drk_render for the same params, cam and opt and the
- * state it produced: grads <- d(sum dL_drgb * rgb)/d(params).  dL_drgb is a
- * device 3 x H x W array.  grads arrays are overwritten.  Asynchronous. */
+/* Reverse mode of drk_render (Eq. 1 and Eq. 4 - Eq. 10, taken front to
+ * back as the supplementary "Cache-Sorting" paragraph describes) for the
+ * same params, cam and opt and the state it produced:
+ * grads <- d(sum dL_drgb * rgb)/d(params), with respect to the activated
+ * parameters.  dL_drgb is a device 3 x H x W array; grads holds device
+ * arrays of the parameters' shapes, overwritten.  The state stays owned by
+ * the caller and may be used again.  The call reads the forward's record
+ * count back once (a stream sync) to size the grouping of the records;
+ * everything else is asynchronous.  Returns DRK_ERR_INVALID_ARG when
+ * params, cam or opt do not match the state, for the cache-sorting order
+ * (it has no backward) or for a null gradient array; DRK_ERR_OOM or
+ * DRK_ERR_CUDA as drk_render does. */
 drk_status_t drk_render_backward(drk_ctx_t *ctx, const drk_params_t *params, const drk_camera_t *cam,
                                  const drk_options_t *opt, const drk_state_t *state,
                                  const float *dL_drgb, const drk_params_grad_t *grads, void *stream);
 
+/* Frees a state of drk_render (stream-ordered on the stream of its
+ * render); NULL is a no-op. */
 void drk_state_free(drk_state_t *state);
 
 /* Stable ascending sort of n (key, value) pairs by the low key_bits bits of
@@ -262,7 +275,10 @@ drk_status_t drk_sort_pairs(drk_ctx_t *ctx, uint32_t *keys, uint32_t *vals, int6
  * a launch fails (message in drk_last_error). */
 drk_status_t drk_sort_pairs_static(uint32_t *keys, uint32_t *vals, int64_t n, int key_bits, void *stream);
 
-/* Synchronises the stream of the last render and copies its counters. */
+/* Synchronises the stream of the last render and copies its counters into
+ * *out (host).  out->status is the lowest device status bit the last
+ * render or backward set (DRK_OK if none).  DRK_ERR_INVALID_ARG for a null
+ * argument, DRK_ERR_CUDA if the copy fails. */
 drk_status_t drk_get_stats(drk_ctx_t *ctx, drk_stats_t *out);
 
 /* Stage timing with CUDA events recorded on the caller's stream around each
